@@ -1,0 +1,351 @@
+"""Benchmark of voxel-grid decimation on GB300 (one JSON line on stdout).
+
+Workload: the fused map cloud -- 50,000,000 FP32 points (70 % on planes/box surfaces in a
+40 x 40 x 10 m volume with 5 mm noise, 30 % uniform clutter, 2 % NaN, globally
+shuffled), origin = cloud minimum, leaf 0.02 m.  One step = one vg_downsample call over
+the whole cloud (origin, keys, radix sort, segmented reduction + compaction).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 (under torchrun) runs one independent replica per GPU (the path has no exchange
+step) and reports the points of all ranks over the slowest rank's time.
+--impl reference times the CPU oracle (FP64 std::map, one core) on a bounded sample of
+the same workload, as the reference arm.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N_POINTS = 50_000_000
+LEAF = 0.02
+WORKLOAD = "fused map cloud, 50M xyz f32 points, 40x40x10 m, leaf 0.02 m, origin = cloud min"
+ORACLE_SAMPLE = 1_000_000     # cpu_baseline: first 1M points of the same cloud
+REFERENCE_SAMPLE = 250_000    # --impl reference: points per step
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="vg", choices=["vg", "reference"])
+    p.add_argument("--n", type=int, default=N_POINTS)
+    p.add_argument("--leaf", type=float, default=LEAF)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.gpu = gpu_index
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        if not getattr(self, "lines", None):
+            return None
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except (ValueError, IndexError):
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2102_11084_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel: str, units: float):
+    """DRAM bytes per launch from the committed ncu summary, if it matches the source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if d.get("source_hash") != kernel_source_hash():
+        return None
+    k = d.get("kernels", {}).get(kernel)
+    if not k:
+        return None
+    return float(k["bytes_per_unit"]) * units
+
+
+# --------------------------------------------------------------------------------------
+def run_reference(args, rank, world):
+    """Reference arm: the CPU oracle on bounded samples of the same workload."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_2102_11084_gb300 import synth
+    xyz = synth.fused_map(args.n, seed=0)
+    sample = np.ascontiguousarray(xyz[:REFERENCE_SAMPLE])
+    for _ in range(args.warmup):
+        oracle.downsample(sample, args.leaf)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.downsample(sample, args.leaf)
+        times.append(time.perf_counter() - t0)
+    ms = 1000 * statistics.mean(times)
+    value = REFERENCE_SAMPLE / (ms / 1000)
+    sample_desc = f"first {REFERENCE_SAMPLE} points of the workload cloud per step, 1 thread"
+    print(json.dumps({
+        "impl": "reference", "metric": "points/s", "value": value, "unit": "points/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "leaf_m": args.leaf},
+        "cpu_baseline": {"value": value, "unit": "points/s", "cores": 1, "kind": "oracle",
+                         "sample": sample_desc},
+        "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def cpu_baseline(xyz, leaf):
+    import oracle
+    sample = np.ascontiguousarray(xyz[:ORACLE_SAMPLE])
+    t0 = time.perf_counter()
+    oracle.downsample(sample, leaf)
+    dt = time.perf_counter() - t0
+    return {"value": ORACLE_SAMPLE / dt, "unit": "points/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {ORACLE_SAMPLE} points of the workload cloud (same leaf, origin = "
+                      f"sample min), single-threaded std::map FP64 oracle, {dt:.1f} s",
+            "host_cores_available": os.cpu_count()}
+
+
+def run_vg(args, rank, world, local):
+    import torch
+    import torch.distributed as dist
+    from paper_2102_11084_gb300 import synth, vg
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    xyz_np = synth.fused_map(args.n, seed=rank)
+    n = xyz_np.shape[0]
+    xyz_host = torch.from_numpy(xyz_np).pin_memory()
+    xyz = xyz_host.to(dev)
+    buf = vg.alloc_buffers(n, dev)
+    stream = torch.cuda.current_stream(dev)
+
+    # stage events (profiling hook of the C ABI): one set per timed step
+    n_stages = int(vg.lib().vg_set_stage_events(None, 0))
+    import ctypes
+
+    def call():
+        vg.downsample_into(xyz, args.leaf, buf, origin_from_min=True, stream=stream)
+
+    for _ in range(args.warmup):
+        call()
+    torch.cuda.synchronize()
+    err = int(buf.error.item())
+    if err:
+        raise vg.VGError(err, "warm-up")
+
+    ev_sets = [[torch.cuda.Event(enable_timing=True) for _ in range(n_stages + 1)]
+               for _ in range(args.steps)]
+    # create the underlying CUDA events
+    for s in ev_sets:
+        for e in s:
+            e.record(stream)
+    torch.cuda.synchronize()
+    arrs = [(ctypes.c_void_p * (n_stages + 1))(*[ctypes.c_void_p(e.cuda_event) for e in s])
+            for s in ev_sets]
+
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        start.record(stream)
+        for k in range(args.steps):
+            vg.lib().vg_set_stage_events(arrs[k], n_stages + 1)
+            call()
+        stop.record(stream)
+        torch.cuda.synchronize()
+    vg.lib().vg_set_stage_events(None, 0)
+    ms = start.elapsed_time(stop) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+        ms = float(t.item())
+    err = int(buf.error.item())
+    if err:
+        raise vg.VGError(err, "timed steps")
+    V = int(buf.num_voxels.item())
+    nvalid = int(np.isfinite(xyz_np).all(axis=1).sum())
+
+    # per-stage device times (ms, mean over steps)
+    stage_names = ["origin", "keys"] + [f"sort_pass{p}" for p in range(8)] + ["segreduce"]
+    stage_ms = np.zeros(n_stages)
+    for s in ev_sets:
+        for i in range(n_stages):
+            stage_ms[i] += s[i].elapsed_time(s[i + 1])
+    stage_ms /= args.steps
+    passes = int(np.ceil(max(1, int(buf.keys[V - 1].item()).bit_length()) / 8)) if V else 1
+    # algorithmic bytes per launch of each kernel
+    algo = {
+        "origin": 12.0 * n,
+        "keys": 12.0 * n + 8.0 * n,
+        "sort_pass": 24.0 * nvalid,
+        "segreduce": (8 + 4 + 12) * nvalid + 16.0 * V,
+    }
+    sort_ms = stage_ms[2:2 + passes]
+    kern = {
+        "origin": (stage_ms[0], algo["origin"], 1),
+        "keys": (stage_ms[1], algo["keys"], 1),
+        "sort_pass": (float(sort_ms.mean()), algo["sort_pass"], passes),
+        "segreduce": (stage_ms[10], algo["segreduce"], 1),
+    }
+    dom = max(kern, key=lambda k: kern[k][0] * kern[k][2])
+    peaks, peak_src = measured_peaks()
+    peak = float(peaks["hbm_gbs"])
+    d_ms, d_bytes, _ = kern[dom]
+    achieved = d_bytes / (d_ms / 1000) / 1e9
+    traffic = profiled_traffic(dom, {"origin": n, "keys": n, "sort_pass": nvalid,
+                                     "segreduce": nvalid}[dom])
+    path_bytes = 12.0 * n + 16.0 * V
+    path_gbs = path_bytes / (ms / 1000) / 1e9
+
+    # end to end: pinned host cloud in, key/centroid/count rows out, through the C ABI
+    keys_h = torch.empty(n, dtype=torch.int64).pin_memory()
+    cent_h = torch.empty((n, 3), dtype=torch.float32).pin_memory()
+    cnt_h = torch.empty(n, dtype=torch.int32).pin_memory()
+    nv_h = torch.empty(1, dtype=torch.int64).pin_memory()
+    e2e_steps = max(1, min(args.steps, 5))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    d2h = 0
+    for _ in range(e2e_steps):
+        xyz.copy_(xyz_host, non_blocking=True)
+        call()
+        nv_h.copy_(buf.num_voxels, non_blocking=True)
+        stream.synchronize()
+        v = int(nv_h.item())
+        keys_h[:v].copy_(buf.keys[:v], non_blocking=True)
+        cent_h[:v].copy_(buf.centroids[:v], non_blocking=True)
+        cnt_h[:v].copy_(buf.counts[:v], non_blocking=True)
+        stream.synchronize()
+        d2h = 8 + v * (8 + 12 + 4)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    cpu = None if args.no_cpu_baseline else cpu_baseline(xyz_np, args.leaf)
+    launches_per_step = 1 + 1 + 8 + 1
+    out = {
+        "metric": "points/s", "value": world * n / (ms / 1000), "unit": "points/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "points": n, "valid_points": nvalid, "voxels": V,
+                   "leaf_m": args.leaf, "method": "sort", "parallelism": f"replicas x{world}",
+                   "l2": "inputs (600 MB) larger than L2 (129 MB); no flush"},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": f"hbm_gbs of MEASURED_PEAKS.json ({peak_src})",
+                     "algorithmic_bytes_per_launch": d_bytes, "ms_per_launch": d_ms},
+        "roofline_path": {"bytes_per_step": path_bytes, "achieved": path_gbs, "peak": peak,
+                          "unit": "GB/s", "frac": path_gbs / peak,
+                          "definition": "12 B per input point + 16 B per output voxel"},
+        "stages_ms": {nm: float(v) for nm, v in zip(stage_names, stage_ms)},
+        "sort_passes": passes,
+        "cpu_baseline": cpu,
+        "e2e": {"value": world * n / e2e_s, "unit": "points/s", "h2d_bytes_per_step": 12 * n,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_vg(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

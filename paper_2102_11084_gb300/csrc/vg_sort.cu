@@ -1,0 +1,230 @@
+// Step a3 (sort path): stable LSD radix sort of the voxel keys with the point index as
+// payload, one kernel per 8-bit digit ("onesweep": per-tile digit ranks, a chained scan
+// with decoupled look-back for the tile's offset inside each digit bucket, and a
+// locally-sorted, coalesced scatter).
+//
+// arXiv 2102.11084 Sec. II-C / Algorithm 1 sorts the (cell, point) table "tabla_subdiv"
+// with a radix sort so that the points of every cell become contiguous.  This kernel is
+// that sort, restated for sm_103a:
+//   * only the significant digits are sorted: the number of passes comes from the
+//     largest valid key (found by the key kernel), read on the device, so launched
+//     passes beyond it return at once and the data stays in the right buffer;
+//   * pass 0 reads the raw per-point keys, drops invalid rows (sentinel keys) and
+//     generates the payload index itself, so compaction costs nothing extra;
+//   * every pass also histograms the next digit, so no separate upsweep pass exists;
+//   * tile ids come from an atomic ticket (a waiting tile only waits on tiles that have
+//     already started), and every wait is bounded: after the limit the kernel records
+//     a timeout status and carries on, so a fault can never hang the GPU.
+#include "vg_device.cuh"
+#include "vg_internal.h"
+
+namespace vg {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr uint64_t kSentinel = ~0ull;
+
+// Exclusive scans of two values over a 256-thread block; also returns the totals.
+__device__ __forceinline__ void block_excl_scan2(uint32_t a, uint32_t b, uint32_t* ea,
+                                                 uint32_t* eb, uint32_t* ta, uint32_t* tb,
+                                                 uint32_t (*tmp)[2]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t ia = a, ib = b;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const uint32_t ya = __shfl_up_sync(kFull, ia, off);
+    const uint32_t yb = __shfl_up_sync(kFull, ib, off);
+    if (lane >= off) {
+      ia += ya;
+      ib += yb;
+    }
+  }
+  if (lane == 31) {
+    tmp[warp][0] = ia;
+    tmp[warp][1] = ib;
+  }
+  __syncthreads();
+  uint32_t wa = 0, wb = 0, sa = 0, sb = 0;
+#pragma unroll
+  for (int w = 0; w < kSortThreads / 32; ++w) {
+    if (w < warp) {
+      wa += tmp[w][0];
+      wb += tmp[w][1];
+    }
+    sa += tmp[w][0];
+    sb += tmp[w][1];
+  }
+  *ea = wa + ia - a;
+  *eb = wb + ib - b;
+  *ta = sa;
+  *tb = sb;
+}
+
+__global__ __launch_bounds__(kSortThreads, 2) void onesweep_kernel(
+    const uint64_t* __restrict__ keys_in, const uint32_t* __restrict__ idx_in,
+    uint64_t* __restrict__ keys_out, uint32_t* __restrict__ idx_out, State* st,
+    uint32_t* lb_cur, uint32_t* lb_next, int pass, int64_t n_host, uint32_t spin_limit,
+    int* err) {
+  __shared__ uint32_t warp_hist[kSortThreads / 32][kRadix];
+  __shared__ uint32_t digit_start[kRadix];
+  __shared__ uint32_t gbase[kRadix];
+  __shared__ uint32_t next_hist[kRadix];
+  __shared__ uint32_t scan_tmp[kSortThreads / 32][2];
+  __shared__ uint64_t sbuf[kSortTile];
+  __shared__ uint8_t sdig[kSortTile];
+  __shared__ int s_tile;
+  __shared__ uint32_t s_tile_n;
+
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  if (t == 0) s_tile = static_cast<int>(atomicAdd(&st->tile_ctr[pass], 1u));
+  __syncthreads();
+  const int tile = s_tile;
+  // The next pass uses the other status region; every tile clears its own row of it.
+  lb_next[size_t(tile) * kRadix + t] = 0;
+
+  const int passes = max(1, sort_passes(st->maxkey));
+  if (pass >= passes) return;
+  const int64_t n_items = pass == 0 ? n_host : int64_t(st->nvalid);
+  const int64_t tile_base = int64_t(tile) * kSortTile;
+  if (tile_base >= n_items) return;
+  const int shift = pass * kRadixBits;
+
+  // ---- load (warp-striped: item j of lane l is tile_base + warp*512 + j*32 + l) ----
+  uint64_t key[kSortItems];
+  uint32_t pay[kSortItems];
+  uint32_t vmask = 0;
+#pragma unroll
+  for (int j = 0; j < kSortItems; ++j) {
+    const int64_t i = tile_base + warp * (32 * kSortItems) + j * 32 + lane;
+    const bool in = i < n_items;
+    key[j] = in ? __ldcs(keys_in + i) : kSentinel;
+    const bool ok = in && (pass > 0 || key[j] != kSentinel);
+    vmask |= uint32_t(ok) << j;
+    pay[j] = (pass == 0) ? static_cast<uint32_t>(i) : (in ? __ldcs(idx_in + i) : 0u);
+  }
+  for (int d = lane; d < kRadix; d += 32) warp_hist[warp][d] = 0;
+  next_hist[t] = 0;
+  __syncwarp();
+
+  // ---- stable rank of every item among the same digit within its warp ----
+  const uint32_t lt = (1u << lane) - 1u;
+  uint32_t rank[kSortItems];
+#pragma unroll
+  for (int j = 0; j < kSortItems; ++j) {
+    const bool ok = (vmask >> j) & 1u;
+    const uint32_t d = static_cast<uint32_t>(key[j] >> shift) & (kRadix - 1);
+    uint32_t peers = __ballot_sync(kFull, ok);
+#pragma unroll
+    for (int b = 0; b < kRadixBits; ++b) {
+      const bool bit = (d >> b) & 1u;
+      const uint32_t bal = __ballot_sync(kFull, bit);
+      peers &= bit ? bal : ~bal;
+    }
+    const uint32_t lower = peers & lt;
+    uint32_t old = 0;
+    if (ok) old = warp_hist[warp][d];
+    __syncwarp();
+    if (ok && lower == 0) warp_hist[warp][d] = old + __popc(peers);
+    __syncwarp();
+    rank[j] = old + __popc(lower);
+  }
+  __syncthreads();
+
+  // ---- per digit (thread t = digit t): offsets of the warps, tile count, scans ----
+  uint32_t run = 0;
+#pragma unroll
+  for (int w = 0; w < kSortThreads / 32; ++w) {
+    const uint32_t c = warp_hist[w][t];
+    warp_hist[w][t] = run;
+    run += c;
+  }
+  const uint32_t tile_count = run;
+  uint32_t local_excl, global_excl, tile_total, global_total;
+  block_excl_scan2(tile_count, st->hist[pass][t], &local_excl, &global_excl, &tile_total,
+                   &global_total, scan_tmp);
+
+  // ---- chained scan over tiles, one digit per thread ----
+  uint32_t excl = 0;
+  uint32_t* my = lb_cur + size_t(tile) * kRadix + t;
+  if (tile == 0) {
+    st_relaxed(my, kFlagPrefix | tile_count);
+  } else {
+    st_relaxed(my, kFlagAggregate | tile_count);
+    int j = tile - 1;
+    uint32_t spins = 0;
+    while (j >= 0) {
+      const uint32_t s = ld_relaxed(lb_cur + size_t(j) * kRadix + t);
+      const uint32_t f = s & ~kValueMask;
+      if (f == 0) {
+        if (++spins > spin_limit) {
+          set_error(err, 6 /* VG_ERR_TIMEOUT */);
+          break;
+        }
+        if (spins > 64) __nanosleep(64);
+        continue;
+      }
+      excl += s & kValueMask;
+      if (f == kFlagPrefix) break;
+      --j;
+    }
+    st_relaxed(my, kFlagPrefix | ((excl + tile_count) & kValueMask));
+  }
+  digit_start[t] = local_excl;
+  gbase[t] = global_excl + excl;
+  if (t == 0) s_tile_n = tile_total;
+  __syncthreads();
+
+  // ---- keys: locally sorted in shared memory, then written digit run by digit run ----
+#pragma unroll
+  for (int j = 0; j < kSortItems; ++j) {
+    if ((vmask >> j) & 1u) {
+      const uint32_t d = static_cast<uint32_t>(key[j] >> shift) & (kRadix - 1);
+      rank[j] += digit_start[d] + warp_hist[warp][d];
+      sbuf[rank[j]] = key[j];
+    }
+  }
+  __syncthreads();
+  const uint32_t tile_n = s_tile_n;
+  const bool has_next = shift + kRadixBits < 64;
+  for (uint32_t i = t; i < tile_n; i += kSortThreads) {
+    const uint64_t k = sbuf[i];
+    const uint32_t d = static_cast<uint32_t>(k >> shift) & (kRadix - 1);
+    sdig[i] = static_cast<uint8_t>(d);
+    __stcg(keys_out + gbase[d] + (i - digit_start[d]), k);
+    if (has_next) atomicAdd(&next_hist[static_cast<uint32_t>(k >> (shift + kRadixBits)) & (kRadix - 1)], 1u);
+  }
+  __syncthreads();
+  uint32_t* sbuf32 = reinterpret_cast<uint32_t*>(sbuf);
+#pragma unroll
+  for (int j = 0; j < kSortItems; ++j)
+    if ((vmask >> j) & 1u) sbuf32[rank[j]] = pay[j];
+  __syncthreads();
+  for (uint32_t i = t; i < tile_n; i += kSortThreads) {
+    const uint32_t d = sdig[i];
+    __stcg(idx_out + gbase[d] + (i - digit_start[d]), sbuf32[i]);
+  }
+  if (has_next && pass + 1 < kMaxPasses && next_hist[t])
+    atomicAdd(&st->hist[pass + 1][t], next_hist[t]);
+}
+
+}  // namespace
+
+cudaError_t launch_sort_pass(State* st, uint64_t* keys0, uint32_t* idx0, uint64_t* keys1,
+                             uint32_t* idx1, uint32_t* lb_a, uint32_t* lb_b, int64_t n_max,
+                             int pass, uint32_t spin_limit, int* err, cudaStream_t stream) {
+  if (n_max == 0) return cudaSuccess;
+  const int tiles = static_cast<int>(ceil_div(n_max, kSortTile));
+  const bool even = (pass & 1) == 0;
+  // pass p reads buffer (p odd ? 1 : 0) and writes the other; pass 0 reads raw keys.
+  const uint64_t* kin = even ? keys0 : keys1;
+  const uint32_t* iin = even ? idx0 : idx1;
+  uint64_t* kout = even ? keys1 : keys0;
+  uint32_t* iout = even ? idx1 : idx0;
+  uint32_t* cur = even ? lb_a : lb_b;
+  uint32_t* nxt = even ? lb_b : lb_a;
+  onesweep_kernel<<<tiles, kSortThreads, 0, stream>>>(kin, pass == 0 ? nullptr : iin, kout, iout,
+                                                      st, cur, nxt, pass, n_max, spin_limit, err);
+  return cudaGetLastError();
+}
+
+}  // namespace vg

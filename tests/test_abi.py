@@ -1,0 +1,81 @@
+"""The C ABI library loads and exports every declared symbol (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2102_11084_gb300 as vgpkg
+from paper_2102_11084_gb300 import build as vgbuild
+from paper_2102_11084_gb300 import vg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    vgbuild.build()
+
+
+def declared_symbols():
+    names = []
+    inc = os.path.join(ROOT, "include")
+    for f in sorted(os.listdir(inc)):
+        if f.endswith(".h"):
+            txt = open(os.path.join(inc, f)).read()
+            names += re.findall(r"VG_API\s+[\w\s\*]+?\b(vg_\w+)\s*\(", txt)
+    return names
+
+
+def test_every_declared_symbol_is_exported():
+    names = declared_symbols()
+    assert "vg_downsample" in names
+    h = ctypes.CDLL(vg.LIB_PATH)
+    missing = [n for n in names if not hasattr(h, n)]
+    assert not missing, missing
+
+
+def test_binding_names_match_header():
+    names = set(declared_symbols())
+    assert set(vg._SIGS) <= names
+
+
+def test_status_strings():
+    assert vg.status_string(0) == "ok"
+    for s in vg.Status:
+        assert vg.status_string(int(s))
+    assert vgpkg.version() >= 100
+
+
+def test_workspace_query():
+    assert vg.workspace_bytes(0) > 0
+    a, b = vg.workspace_bytes(1000), vg.workspace_bytes(1_000_000)
+    assert b > a > 0
+    assert vg.lib().vg_downsample_workspace_bytes(-1, 0) == 0
+
+
+def _call(n=0, leaf=0.1, flags=0, ws=None, wsb=0, origin=8):
+    L = vg.lib()
+    nv = 16
+    return L.vg_downsample(None, n, origin, ctypes.c_float(leaf), None, None, None, 0, nv, None,
+                           None, ws, wsb, flags, None)
+
+
+def test_argument_errors_return_before_any_launch():
+    assert _call(n=-1) == vg.Status.INVALID_ARG
+    assert _call(leaf=0.0) == vg.Status.INVALID_ARG
+    assert _call(leaf=float("nan")) == vg.Status.INVALID_ARG
+    assert _call(leaf=float("inf")) == vg.Status.INVALID_ARG
+    assert _call(flags=1 << 20) == vg.Status.INVALID_ARG
+    assert _call(origin=None) == vg.Status.INVALID_ARG
+    assert _call(n=vg.MAX_POINTS + 1) == vg.Status.INVALID_ARG
+    assert _call(n=5) == vg.Status.INVALID_ARG          # xyz null with n > 0
+    assert _call(origin=2) == vg.Status.ALIGN
+    assert _call(ws=None, wsb=0) == vg.Status.WORKSPACE
+    assert _call(ws=256, wsb=16) == vg.Status.WORKSPACE
+
+
+def test_no_cpu_fallback():
+    import torch
+    with pytest.raises(TypeError):
+        vgpkg.downsample(torch.zeros((4, 3)), 0.1)
