@@ -114,6 +114,38 @@ VG_API vg_status vg_downsample(const float* xyz, int64_t n, float* origin, float
                         int32_t* out_error, void* workspace, size_t workspace_bytes,
                         int flags, vg_stream_t stream);
 
+/* Largest cloud vg_downsample_noalloc accepts (2^20 points: a 1280 x 720 frame fits). */
+#define VG_NOALLOC_MAX_POINTS 1048576LL
+
+/*
+ * vg_downsample_noalloc -- vg_downsample without a caller workspace, for callers that
+ * cannot call cudaMalloc: code that runs where allocating is not allowed or not possible,
+ * such as a real-time sensor callback that must never block (cudaMalloc can synchronise
+ * the device), or a host program whose device memory is owned by another allocator and
+ * that cannot hand out scratch.  The paper has no counterpart of this entry point; it
+ * exists only for such callers.
+ *
+ * Arguments are those of vg_downsample minus workspace/workspace_bytes; the caller still
+ * passes (and owns) the input cloud and all outputs.  The scratch is a static device
+ * array of vg_downsample_noalloc_scratch_bytes() bytes (about 25 MB, the workspace of
+ * VG_NOALLOC_MAX_POINTS points) that every GPU loading the library keeps until the
+ * process exits.  The call allocates nothing.
+ *   * n > VG_NOALLOC_MAX_POINTS is rejected with VG_ERR_INVALID_ARG before any launch.
+ *   * The first call on a device looks up the array's device address (once per device,
+ *     with that device current); make that first call before any stream capture.
+ *   * All calls on a device share the one array; it keeps the last call's contents and
+ *     every call clears what must start at zero.  Calls whose work overlaps on the GPU
+ *     (different streams, or different host threads) race on it: serialise them.
+ */
+VG_API vg_status vg_downsample_noalloc(const float* xyz, int64_t n, float* origin, float leaf,
+                                       uint64_t* out_keys, float* out_centroids,
+                                       uint32_t* out_counts, int64_t cap,
+                                       int64_t* out_num_voxels, int32_t* out_point_to_voxel,
+                                       int32_t* out_error, int flags, vg_stream_t stream);
+
+/* Bytes of the static scratch array behind vg_downsample_noalloc. */
+VG_API size_t vg_downsample_noalloc_scratch_bytes(void);
+
 /* Profiling hook.  When `events` is non-NULL, every later vg_downsample call records
  * events[0] on its stream before its first kernel and events[k] after stage k, for
  * k = 1 .. min(max_events - 1, number of stages); NULL turns it off.  The events are

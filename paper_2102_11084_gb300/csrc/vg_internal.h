@@ -63,8 +63,8 @@ struct alignas(16) SegStatus {
   long long pad3;
 };
 
-inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
-inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+constexpr int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+constexpr size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 // Workspace layout of the sort path for n points.
 struct SortLayout {
@@ -72,7 +72,32 @@ struct SortLayout {
   size_t zero_bytes;  // bytes from `state` that must be zero at call start
   int64_t sort_tiles, seg_tiles;
 };
-SortLayout sort_layout(int64_t n);
+constexpr SortLayout sort_layout(int64_t n) {
+  SortLayout L{};
+  const int64_t nn = n < 1 ? 1 : n;
+  L.sort_tiles = ceil_div(nn, kSortTile);
+  L.seg_tiles = ceil_div(nn, kSegTile);
+  size_t off = 0;
+  L.state = off;
+  off = align_up(off + sizeof(State), 256);
+  L.lb_a = off;
+  off = align_up(off + size_t(L.sort_tiles) * kRadix * sizeof(uint32_t), 256);
+  L.seg_lb = off;
+  off = align_up(off + size_t(L.seg_tiles) * sizeof(SegStatus), 256);
+  L.zero_bytes = off;  // state, pass-0 status rows and segment status: zeroed per call
+  L.lb_b = off;
+  off = align_up(off + size_t(L.sort_tiles) * kRadix * sizeof(uint32_t), 256);
+  L.keys0 = off;
+  off = align_up(off + size_t(nn) * sizeof(uint64_t), 256);
+  L.keys1 = off;
+  off = align_up(off + size_t(nn) * sizeof(uint64_t), 256);
+  L.idx0 = off;
+  off = align_up(off + size_t(nn) * sizeof(uint32_t), 256);
+  L.idx1 = off;
+  off = align_up(off + size_t(nn) * sizeof(uint32_t), 256);
+  L.total = off;
+  return L;
+}
 
 int num_sms();
 

@@ -53,6 +53,11 @@ _SIGS = {
                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                        ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p], ctypes.c_int),
     "vg_debug_set_spin_limit": ([ctypes.c_uint32], None),
+    "vg_downsample_noalloc": ([ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_float,
+                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                               ctypes.c_void_p], ctypes.c_int),
+    "vg_downsample_noalloc_scratch_bytes": ([], ctypes.c_size_t),
 }
 
 
@@ -194,6 +199,39 @@ def downsample(xyz: torch.Tensor, leaf: float, origin: Optional[torch.Tensor] = 
     v = int(buf.num_voxels.item())
     return Decimation(buf.keys[:v], buf.centroids[:v], buf.counts[:v], buf.origin,
                       buf.point_to_voxel[:n] if point_to_voxel else None)
+
+
+NOALLOC_MAX_POINTS = 1 << 20
+
+
+def downsample_noalloc(xyz: torch.Tensor, leaf: float, origin: Optional[torch.Tensor] = None, *,
+                       method="sort", point_to_voxel: bool = False,
+                       stream: Optional[torch.cuda.Stream] = None) -> Decimation:
+    """vg_downsample_noalloc: decimation whose scratch is the library's static device
+    array instead of a workspace (for callers that cannot allocate device memory; the
+    outputs here are still torch tensors).  At most NOALLOC_MAX_POINTS points; calls
+    that overlap on the GPU race on the shared scratch."""
+    xyz = _cuda_cloud(xyz)
+    n = xyz.shape[0]
+    dev = xyz.device
+    org = (torch.zeros(3, dtype=torch.float32, device=dev) if origin is None else
+           torch.as_tensor(origin, dtype=torch.float32, device=dev).reshape(3).contiguous())
+    cap = max(n, 1)
+    keys = torch.empty(cap, dtype=torch.int64, device=dev)
+    cents = torch.empty((cap, 3), dtype=torch.float32, device=dev)
+    counts = torch.empty(cap, dtype=torch.int32, device=dev)
+    nv = torch.zeros(1, dtype=torch.int64, device=dev)
+    err = torch.zeros(1, dtype=torch.int32, device=dev)
+    p2v = torch.empty(cap, dtype=torch.int32, device=dev) if point_to_voxel else None
+    flags = method_flag(method) | (ORIGIN_FROM_MIN if origin is None else 0)
+    st = lib().vg_downsample_noalloc(
+        _ptr(xyz), n, _ptr(org), ctypes.c_float(leaf), _ptr(keys), _ptr(cents), _ptr(counts), n,
+        _ptr(nv), _ptr(p2v), _ptr(err), flags, _stream_ptr(stream))
+    _check(st, "vg_downsample_noalloc")
+    (stream or torch.cuda.current_stream()).synchronize()
+    _check(int(err.item()), "vg_downsample_noalloc (device)")
+    v = int(nv.item())
+    return Decimation(keys[:v], cents[:v], counts[:v], org, p2v[:n] if point_to_voxel else None)
 
 
 def set_spin_limit(limit: int) -> None:
