@@ -68,8 +68,17 @@ typedef enum {
 /* flags */
 #define VG_ORIGIN_FROM_MIN 1 /* compute origin = per-axis min of the valid points and
                                 write it to `origin` (else `origin` is read)            */
-#define VG_METHOD_AUTO 0     /* let the library choose the grouping method             */
-#define VG_METHOD_SORT 16    /* radix sort + segmented reduction                       */
+#define VG_METHOD_AUTO 0     /* the library's default grouping method (currently SORT)  */
+#define VG_METHOD_SORT 16    /* radix sort of every point + segmented reduction        */
+#define VG_METHOD_HASH 32    /* hash-table accumulation + radix sort of the voxels     */
+#define VG_METHOD_MASK 48
+#define VG_USE_GRAPH 64      /* vg_downsample_batch: capture / replay a CUDA graph      */
+#define VG_GRID_SHIFT 8      /* vg_downsample_frames: blocks per SM of the streaming    */
+#define VG_GRID_MASK (0xff << VG_GRID_SHIFT) /* kernels (0 = default 8)                */
+
+/* Largest number of frames of one batched call, and of pyramid levels. */
+#define VG_MAX_FRAMES 1024
+#define VG_MAX_LEVELS 8
 
 /* Largest number of points one call accepts (2^30 - 1). */
 #define VG_MAX_POINTS 1073741823LL
@@ -105,7 +114,9 @@ VG_API size_t vg_downsample_workspace_bytes(int64_t n_points, int flags);
  *   out_error      int32 scalar or NULL: device error word (see conventions).
  *   workspace      scratch of at least vg_downsample_workspace_bytes(n, flags) bytes,
  *                  256-byte aligned; its contents on entry do not matter.
- *   flags          VG_ORIGIN_FROM_MIN | one VG_METHOD_*.
+ *   flags          VG_ORIGIN_FROM_MIN | one VG_METHOD_*.  SORT and HASH give identical
+ *                  results; HASH needs more workspace and wins when voxels hold many
+ *                  points.
  *   stream         CUDA stream for every launch.
  */
 VG_API vg_status vg_downsample(const float* xyz, int64_t n, float* origin, float leaf,
@@ -113,6 +124,100 @@ VG_API vg_status vg_downsample(const float* xyz, int64_t n, float* origin, float
                         int64_t cap, int64_t* out_num_voxels, int32_t* out_point_to_voxel,
                         int32_t* out_error, void* workspace, size_t workspace_bytes,
                         int flags, vg_stream_t stream);
+
+/*
+ * Batched frames -- step a8: many clouds of uneven size in one call.  Every frame is
+ * decimated exactly as vg_downsample would decimate it alone (same keys, counts and
+ * centroid bits); all frames share the launches and one radix sort (frame id above the
+ * voxel key).  The paper distributes the subdivisions of space over every CUDA processor
+ * (Sec. II-C, grid sized to the processor count).
+ *
+ *   xyz               [n_total,3] float32, the frames concatenated.
+ *   frame_offsets     int64 [n_frames+1] (device): frame f is rows [off[f], off[f+1]);
+ *                     off[0] = 0, non-decreasing, off[n_frames] = n_total (checked on the
+ *                     device: VG_ERR_INVALID_ARG).  1 <= n_frames <= VG_MAX_FRAMES.
+ *   origins           float32 [n_frames,3] (device): read, or written with each frame's
+ *                     minimum when flags has VG_ORIGIN_FROM_MIN.
+ *   leaves            float32 [n_frames] (device): each frame's leaf (finite, > 0).
+ *   out_keys/out_centroids/out_counts  rows of all frames, frame by frame, each frame in
+ *                     ascending key order; keys are the frames' own voxel keys.
+ *   out_frame_offsets int64 [n_frames+1] (device): frame f's rows are
+ *                     [out[f], out[f+1]); out[n_frames] = total voxels.
+ *   out_point_to_voxel int32 [n_total] or NULL: global output row of each point, or -1.
+ * The per-frame key field plus the frame id must fit in 63 bits (VG_ERR_RANGE otherwise).
+ */
+VG_API size_t vg_batch_workspace_bytes(int64_t n_total, int n_frames, int flags);
+VG_API vg_status vg_downsample_frames(const float* xyz, int64_t n_total,
+                                      const int64_t* frame_offsets, int n_frames,
+                                      float* origins, const float* leaves, uint64_t* out_keys,
+                                      float* out_centroids, uint32_t* out_counts, int64_t cap,
+                                      int64_t* out_frame_offsets, int32_t* out_point_to_voxel,
+                                      int32_t* out_error, void* workspace,
+                                      size_t workspace_bytes, int flags, vg_stream_t stream);
+
+/*
+ * Batch plan: owns a workspace for up to max_points points in max_frames frames
+ * (allocated here, once), the grouping method and grid size, and a CUDA graph of the
+ * batched launch sequence.  vg_downsample_batch takes the arguments of
+ * vg_downsample_frames without the workspace; with VG_USE_GRAPH (non-NULL stream
+ * required) the first call captures the sequence and later calls with the same pointers,
+ * sizes and flags replay it with one cudaGraphLaunch.  A plan is not thread-safe and its
+ * workspace is shared by its calls: calls that overlap on the GPU race.
+ * vg_plan_tune times both methods x streaming grids {4,8,16} blocks/SM on the given
+ * batch (`reps` replays each, host-synchronising) and keeps the fastest; out_ms (6
+ * floats or NULL) receives sort@4,8,16 then hash@4,8,16 in ms per batch.
+ */
+typedef struct vg_plan vg_plan;
+VG_API vg_status vg_plan_create(vg_plan** plan, int max_frames, int64_t max_points, int flags);
+VG_API vg_status vg_plan_destroy(vg_plan* plan);
+VG_API vg_status vg_plan_configure(vg_plan* plan, int method, int grid_per_sm);
+VG_API vg_status vg_plan_get(const vg_plan* plan, int* method, int* grid_per_sm,
+                             size_t* workspace_bytes);
+VG_API vg_status vg_downsample_batch(vg_plan* plan, const float* xyz, int64_t n_total,
+                                     const int64_t* frame_offsets, int n_frames, float* origins,
+                                     const float* leaves, uint64_t* out_keys,
+                                     float* out_centroids, uint32_t* out_counts, int64_t cap,
+                                     int64_t* out_frame_offsets, int32_t* out_point_to_voxel,
+                                     int32_t* out_error, int flags, vg_stream_t stream);
+VG_API vg_status vg_plan_tune(vg_plan* plan, const float* xyz, int64_t n_total,
+                              const int64_t* frame_offsets, int n_frames, float* origins,
+                              const float* leaves, uint64_t* out_keys, float* out_centroids,
+                              uint32_t* out_counts, int64_t cap, int64_t* out_frame_offsets,
+                              int32_t* out_error, int flags, int reps, vg_stream_t stream,
+                              float* out_ms);
+
+/*
+ * vg_pyramid -- step a6: the count-weighted octree pyramid ("iterative reduction with an
+ * ordered subdivision of space", abstract and Sec. II-C; octree cells split in eight,
+ * Sec. I).  Level 0 is vg_downsample at `leaf`; level k+1 merges level k by key >> 3
+ * (edge doubles), n' = sum n, centroid' = count-weighted mean.  Levels are written one
+ * after another into the outputs: level k is rows [off[k], off[k+1]) of out_keys /
+ * out_centroids / out_counts, with out_level_offsets int64 [levels+1] (device).  Keys and
+ * counts of level k equal vg_downsample at leaf 2^k * leaf exactly; centroids agree within
+ * the library's tolerance.  cap_total >= levels * n always suffices.  Single cloud,
+ * sort method, 1 <= levels <= VG_MAX_LEVELS.  point_to_voxel refers to level 0.
+ */
+VG_API size_t vg_pyramid_workspace_bytes(int64_t n_points, int levels, int flags);
+VG_API vg_status vg_pyramid(const float* xyz, int64_t n, float* origin, float leaf, int levels,
+                            uint64_t* out_keys, float* out_centroids, uint32_t* out_counts,
+                            int64_t cap_total, int64_t* out_level_offsets,
+                            int32_t* out_point_to_voxel, int32_t* out_error, void* workspace,
+                            size_t workspace_bytes, int flags, vg_stream_t stream);
+
+/*
+ * vg_downsample_backward -- step a7: gradient of a loss of the centroids with respect to
+ * the input points.  A centroid is the mean of its n members, so
+ * grad_xyz[i] = grad_centroids[v(i)] / counts[v(i)] for a valid point i (v = point_to_voxel
+ * from the forward call) and 0 for an invalid one (v = -1); keys are piecewise constant and
+ * carry no gradient.  (The paper has no training pass; this differentiates its decimation.)
+ *   grad_centroids float32 [num_voxels,3], counts uint32 [num_voxels],
+ *   point_to_voxel int32 [n], grad_xyz float32 [n,3] (written, every row), out_error int32
+ *   scalar: VG_ERR_INVALID_ARG if an entry of point_to_voxel is outside [-1, num_voxels).
+ */
+VG_API vg_status vg_downsample_backward(const float* grad_centroids, const uint32_t* counts,
+                                        const int32_t* point_to_voxel, int64_t n,
+                                        int64_t num_voxels, float* grad_xyz, int32_t* out_error,
+                                        vg_stream_t stream);
 
 /* Largest cloud vg_downsample_noalloc accepts (2^20 points: a 1280 x 720 frame fits). */
 #define VG_NOALLOC_MAX_POINTS 1048576LL
@@ -150,9 +255,17 @@ VG_API size_t vg_downsample_noalloc_scratch_bytes(void);
  * events[0] on its stream before its first kernel and events[k] after stage k, for
  * k = 1 .. min(max_events - 1, number of stages); NULL turns it off.  The events are
  * cudaEvent_t handles owned by the caller.  Stages of the sort path, in order: origin
- * (recorded even when the origin is given), keys, 8 radix passes, segmented reduction.
- * Returns the number of stages of the sort path (11). */
+ * (recorded even when the origin is given), keys, 8 radix passes, segmented reduction;
+ * of the hash path: origin, insert, compaction, 8 radix passes, finalize, point-to-voxel.
+ * Returns the largest number of events a call records (16). */
 VG_API int vg_set_stage_events(void** events, int max_events);
+
+/* Test of the bounded waits: runs one chained-scan wait on four device words
+ * (scratch_words, caller-owned) that nothing publishes, with a limit of `limit` polls
+ * (1 .. 2^22); the wait gives up and *out_error becomes VG_ERR_TIMEOUT.  No hang, no
+ * fault: this is how a lost predecessor is reported. */
+VG_API vg_status vg_debug_wait_timeout(uint32_t* scratch_words, uint32_t limit,
+                                       int32_t* out_error, vg_stream_t stream);
 
 /* Test hook: limit of every chained-scan wait in later calls (0 restores the default
  * of about a second).  A wait that reaches it records VG_ERR_TIMEOUT and returns. */

@@ -1,10 +1,12 @@
 // C ABI entry points of libvg.so (declared in include/vg.h): argument checks, workspace
-// layout and the launch sequence of each call.  No allocation happens here.
+// layouts and the launch sequence of each call.  No allocation happens here (the plan
+// object in vg_plan.cu is the only owner of device memory in the library).
 #include <atomic>
 #include <cmath>
 #include <cstring>
 
 #include "../../include/vg.h"
+#include "vg_api_internal.h"
 #include "vg_internal.h"
 
 namespace vg {
@@ -13,14 +15,9 @@ namespace {
 std::atomic<uint32_t> g_spin_limit{0};
 void** g_events = nullptr;
 int g_max_events = 0;
-constexpr int kSortStages = 3 + kMaxPasses;
-
-// Records profiling event k on `stream` when the stage-event hook is on.
-void mark(int k, cudaStream_t stream) {
-  if (g_events && k < g_max_events && g_events[k])
-    cudaEventRecord(static_cast<cudaEvent_t>(g_events[k]), stream);
-}
+bool g_events_paused = false;
 int g_sms[64] = {0};
+constexpr int kMaxStages = 16;
 }  // namespace
 
 uint32_t spin_limit() {
@@ -40,17 +37,169 @@ int num_sms() {
   return g_sms[dev];
 }
 
-}  // namespace vg
-
-using namespace vg;
+void pause_stage_events(bool paused) { g_events_paused = paused; }
 
 namespace {
+
+// Records profiling event k on `stream` when the stage-event hook is on.
+void mark(int k, cudaStream_t stream) {
+  if (!g_events_paused && g_events && k < g_max_events && g_events[k])
+    cudaEventRecord(static_cast<cudaEvent_t>(g_events[k]), stream);
+}
 
 bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
 vg_status cuda_status(cudaError_t e) { return e == cudaSuccess ? VG_OK : VG_ERR_CUDA; }
 
+int grid_per_sm_of(int flags) { return (flags >> VG_GRID_SHIFT) & 0xff; }
+
+int method_of(int flags) {
+  const int m = flags & VG_METHOD_MASK;
+  return m == VG_METHOD_HASH ? VG_METHOD_HASH : VG_METHOD_SORT;
+}
+
 }  // namespace
+
+size_t frames_workspace_bytes(int64_t n, int frames, int flags) {
+  if (n < 0 || frames < 1) return 0;
+  return method_of(flags) == VG_METHOD_HASH ? hash_layout(n, frames).total
+                                            : sort_layout(n, frames).total;
+}
+
+vg_status check_outputs(int64_t n, const float* xyz, uint64_t* out_keys, float* out_centroids,
+                        uint32_t* out_counts, int64_t cap, const int64_t* num_voxels,
+                        const int32_t* p2v, const int32_t* out_error, const void* workspace) {
+  if (n < 0 || n > kMaxPoints || cap < 0) return VG_ERR_INVALID_ARG;
+  if (n > 0 && !xyz) return VG_ERR_INVALID_ARG;
+  if (cap > 0 && (!out_keys || !out_centroids || !out_counts)) return VG_ERR_INVALID_ARG;
+  if (!aligned(xyz, 4) || !aligned(out_keys, 8) || !aligned(out_centroids, 4) ||
+      !aligned(out_counts, 4) || !aligned(num_voxels, 8) || !aligned(p2v, 4) ||
+      !aligned(out_error, 4) || !aligned(workspace, 256))
+    return VG_ERR_ALIGN;
+  return VG_OK;
+}
+
+// The launch sequence shared by every decimation entry point.
+vg_status run_frames(const float* xyz, const FramesArg& fr, bool from_min, const SegOut& out,
+                     int32_t* out_error, void* workspace, size_t workspace_bytes, int flags,
+                     cudaStream_t stream) {
+  const int64_t n = fr.n;
+  const int F = fr.nframes;
+  const int method = method_of(flags);
+  const size_t need = frames_workspace_bytes(n, F, flags);
+  if (!workspace || workspace_bytes < need) return VG_ERR_WORKSPACE;
+  char* ws = static_cast<char*>(workspace);
+  const uint32_t spins = spin_limit();
+  const bool have_extent = from_min || F > 1;
+  int stage = 0;
+
+  if (method == VG_METHOD_SORT) {
+    const SortLayout L = sort_layout(n, F);
+    State* st = reinterpret_cast<State*>(ws + L.state);
+    FrameState* fs = reinterpret_cast<FrameState*>(ws + L.frames);
+    uint64_t* keys0 = reinterpret_cast<uint64_t*>(ws + L.keys0);
+    uint64_t* keys1 = reinterpret_cast<uint64_t*>(ws + L.keys1);
+    uint32_t* idx0 = reinterpret_cast<uint32_t*>(ws + L.idx0);
+    uint32_t* idx1 = reinterpret_cast<uint32_t*>(ws + L.idx1);
+    uint32_t* lb_a = reinterpret_cast<uint32_t*>(ws + L.lb_a);
+    uint32_t* lb_b = reinterpret_cast<uint32_t*>(ws + L.lb_b);
+    SegStatus* seg_lb = reinterpret_cast<SegStatus*>(ws + L.seg_lb);
+    int* err = out_error ? reinterpret_cast<int*>(out_error) : &st->error;
+
+    cudaError_t e = cudaMemsetAsync(ws, 0, L.zero_bytes, stream);
+    if (e == cudaSuccess && out_error) e = cudaMemsetAsync(out_error, 0, sizeof(int32_t), stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(out.num_voxels, 0, sizeof(int64_t), stream);
+    if (e == cudaSuccess && out.frame_offsets)
+      e = cudaMemsetAsync(out.frame_offsets, 0, size_t(F + 1) * sizeof(int64_t), stream);
+    if (e == cudaSuccess && out.p2v && n > 0)
+      e = cudaMemsetAsync(out.p2v, 0xff, size_t(n) * sizeof(int32_t), stream);
+    mark(stage++, stream);
+    if (e == cudaSuccess && have_extent) e = launch_origin(xyz, fr, st, fs, err, stream);
+    mark(stage++, stream);
+    if (e == cudaSuccess) e = launch_keys(xyz, fr, have_extent, st, fs, keys0, err, stream);
+    mark(stage++, stream);
+    for (int p = 0; p < kMaxPasses && e == cudaSuccess; ++p) {
+      e = launch_sort_pass(st, keys0, idx0, keys1, idx1, lb_a, lb_b, n, p, false, spins, err,
+                           stream);
+      mark(stage++, stream);
+    }
+    if (e == cudaSuccess)
+      e = launch_segreduce(st, fs, F, keys0, idx0, keys1, idx1, xyz, seg_lb, n, out, spins, err,
+                           stream);
+    mark(stage++, stream);
+    return cuda_status(e);
+  }
+
+  // hash path
+  const HashLayout L = hash_layout(n, F);
+  State* st = reinterpret_cast<State*>(ws + L.state);
+  FrameState* fs = reinterpret_cast<FrameState*>(ws + L.frames);
+  uint64_t* keys0 = reinterpret_cast<uint64_t*>(ws + L.keys0);
+  uint64_t* keys1 = reinterpret_cast<uint64_t*>(ws + L.keys1);
+  uint32_t* idx0 = reinterpret_cast<uint32_t*>(ws + L.idx0);
+  uint32_t* idx1 = reinterpret_cast<uint32_t*>(ws + L.idx1);
+  uint32_t* lb_a = reinterpret_cast<uint32_t*>(ws + L.lb_a);
+  uint32_t* lb_b = reinterpret_cast<uint32_t*>(ws + L.lb_b);
+  HashTable tab{reinterpret_cast<unsigned long long*>(ws + L.tkeys),
+                reinterpret_cast<HashAcc*>(ws + L.tacc), static_cast<uint32_t>(L.slots - 1)};
+  uint32_t* slot_rank = out.p2v ? reinterpret_cast<uint32_t*>(ws + L.slot_rank) : nullptr;
+  uint32_t* point_slot = out.p2v ? reinterpret_cast<uint32_t*>(ws + L.point_slot) : nullptr;
+  int* err = out_error ? reinterpret_cast<int*>(out_error) : &st->error;
+
+  cudaError_t e = cudaMemsetAsync(ws, 0, L.zero_bytes, stream);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(tab.keys, 0xff, size_t(L.slots) * sizeof(unsigned long long), stream);
+  if (e == cudaSuccess && out_error) e = cudaMemsetAsync(out_error, 0, sizeof(int32_t), stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(out.num_voxels, 0, sizeof(int64_t), stream);
+  if (e == cudaSuccess && out.frame_offsets)
+    e = cudaMemsetAsync(out.frame_offsets, 0, size_t(F + 1) * sizeof(int64_t), stream);
+  mark(stage++, stream);
+  if (e == cudaSuccess && have_extent) e = launch_origin(xyz, fr, st, fs, err, stream);
+  mark(stage++, stream);
+  if (e == cudaSuccess)
+    e = launch_hash_insert(xyz, fr, have_extent, st, fs, tab, point_slot, spins, err, stream);
+  mark(stage++, stream);
+  if (e == cudaSuccess) e = launch_hash_compact(tab, st, keys0, idx0, stream);
+  mark(stage++, stream);
+  for (int p = 0; p < kMaxPasses && e == cudaSuccess; ++p) {
+    e = launch_sort_pass(st, keys0, idx0, keys1, idx1, lb_a, lb_b, n, p, true, spins, err, stream);
+    mark(stage++, stream);
+  }
+  if (e == cudaSuccess)
+    e = launch_hash_finalize(st, fs, F, keys0, idx0, keys1, idx1, tab, slot_rank, n, out, err,
+                             stream);
+  mark(stage++, stream);
+  if (e == cudaSuccess && out.p2v) e = launch_hash_p2v(point_slot, slot_rank, n, out.p2v, stream);
+  mark(stage++, stream);
+  return cuda_status(e);
+}
+
+// Pyramid workspace: the sort path's, then two fixed-point sum buffers and the merge
+// chained-scan status of every level.
+struct PyramidLayout {
+  size_t base, sums_a, sums_b, merge_lb, total;
+  int64_t merge_tiles;
+};
+
+PyramidLayout pyramid_layout(int64_t n, int levels) {
+  PyramidLayout L{};
+  const int64_t nn = n < 1 ? 1 : n;
+  L.base = sort_layout(n, 1).total;
+  size_t off = L.base;
+  L.sums_a = off;
+  off = align_up(off + size_t(nn) * 3 * sizeof(long long), 256);
+  L.sums_b = off;
+  off = align_up(off + size_t(nn) * 3 * sizeof(long long), 256);
+  L.merge_tiles = ceil_div(nn, kMergeTile);
+  L.merge_lb = off;
+  off = align_up(off + size_t(levels) * size_t(L.merge_tiles) * sizeof(uint32_t), 256);
+  L.total = off;
+  return L;
+}
+
+}  // namespace vg
+
+using namespace vg;
 
 extern "C" {
 
@@ -73,69 +222,149 @@ int vg_version(void) { return 100; }
 int vg_set_stage_events(void** events, int max_events) {
   g_events = events;
   g_max_events = events ? max_events : 0;
-  return kSortStages;
+  return kMaxStages;
 }
 
 void vg_debug_set_spin_limit(uint32_t limit) {
   g_spin_limit.store(limit, std::memory_order_relaxed);
 }
 
+vg_status vg_debug_wait_timeout(uint32_t* scratch_words, uint32_t limit, int32_t* out_error,
+                                vg_stream_t stream_) {
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+  if (!scratch_words || !out_error || limit == 0 || limit > kDefaultSpinLimit)
+    return VG_ERR_INVALID_ARG;
+  if (!aligned(scratch_words, 4) || !aligned(out_error, 4)) return VG_ERR_ALIGN;
+  cudaError_t e = cudaMemsetAsync(scratch_words, 0, 4 * sizeof(uint32_t), stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(out_error, 0, sizeof(int32_t), stream);
+  if (e == cudaSuccess)
+    e = launch_debug_wait(scratch_words, 3, limit, reinterpret_cast<int*>(out_error), stream);
+  return cuda_status(e);
+}
+
 size_t vg_downsample_workspace_bytes(int64_t n_points, int flags) {
-  (void)flags;
-  if (n_points < 0) return 0;
-  return sort_layout(n_points).total;
+  return frames_workspace_bytes(n_points, 1, flags);
+}
+
+size_t vg_batch_workspace_bytes(int64_t n_total, int n_frames, int flags) {
+  if (n_frames < 1 || n_frames > kMaxFrames) return 0;
+  return frames_workspace_bytes(n_total, n_frames, flags);
 }
 
 vg_status vg_downsample(const float* xyz, int64_t n, float* origin, float leaf,
                         uint64_t* out_keys, float* out_centroids, uint32_t* out_counts,
                         int64_t cap, int64_t* out_num_voxels, int32_t* out_point_to_voxel,
                         int32_t* out_error, void* workspace, size_t workspace_bytes, int flags,
-                        vg_stream_t stream_) {
-  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
-  if (n < 0 || n > kMaxPoints || cap < 0) return VG_ERR_INVALID_ARG;
+                        vg_stream_t stream) {
   if (!(leaf > 0.0f) || !std::isfinite(leaf)) return VG_ERR_INVALID_ARG;
-  if ((flags & ~(VG_ORIGIN_FROM_MIN | VG_METHOD_SORT)) != 0) return VG_ERR_INVALID_ARG;
-  if (!origin || !out_num_voxels || (n > 0 && !xyz)) return VG_ERR_INVALID_ARG;
-  if (cap > 0 && (!out_keys || !out_centroids || !out_counts)) return VG_ERR_INVALID_ARG;
-  if (!aligned(xyz, 4) || !aligned(origin, 4) || !aligned(out_keys, 8) ||
-      !aligned(out_centroids, 4) || !aligned(out_counts, 4) || !aligned(out_num_voxels, 8) ||
-      !aligned(out_point_to_voxel, 4) || !aligned(out_error, 4) || !aligned(workspace, 256))
-    return VG_ERR_ALIGN;
-  const SortLayout L = sort_layout(n);
-  if (!workspace || workspace_bytes < L.total) return VG_ERR_WORKSPACE;
+  if ((flags & ~(VG_ORIGIN_FROM_MIN | VG_METHOD_MASK)) != 0) return VG_ERR_INVALID_ARG;
+  if ((flags & VG_METHOD_MASK) == VG_METHOD_MASK) return VG_ERR_INVALID_ARG;
+  if (!origin || !out_num_voxels) return VG_ERR_INVALID_ARG;
+  vg_status s = check_outputs(n, xyz, out_keys, out_centroids, out_counts, cap, out_num_voxels,
+                              out_point_to_voxel, out_error, workspace);
+  if (s != VG_OK) return s;
+  if (!aligned(origin, 4)) return VG_ERR_ALIGN;
+  const bool from_min = (flags & VG_ORIGIN_FROM_MIN) != 0;
+  FramesArg fr{nullptr, 1, n, from_min ? nullptr : origin, from_min ? origin : nullptr, nullptr, leaf, 0};
+  SegOut out{out_keys, out_centroids, out_counts, nullptr, cap, out_num_voxels, nullptr,
+             out_point_to_voxel};
+  return run_frames(xyz, fr, from_min, out, out_error, workspace, workspace_bytes, flags,
+                    reinterpret_cast<cudaStream_t>(stream));
+}
 
+vg_status vg_downsample_frames(const float* xyz, int64_t n_total, const int64_t* frame_offsets,
+                               int n_frames, float* origins, const float* leaves,
+                               uint64_t* out_keys, float* out_centroids, uint32_t* out_counts,
+                               int64_t cap, int64_t* out_frame_offsets,
+                               int32_t* out_point_to_voxel, int32_t* out_error, void* workspace,
+                               size_t workspace_bytes, int flags, vg_stream_t stream) {
+  if (n_frames < 1 || n_frames > kMaxFrames) return VG_ERR_INVALID_ARG;
+  if ((flags & ~(VG_ORIGIN_FROM_MIN | VG_METHOD_MASK | VG_GRID_MASK)) != 0)
+    return VG_ERR_INVALID_ARG;
+  if ((flags & VG_METHOD_MASK) == VG_METHOD_MASK) return VG_ERR_INVALID_ARG;
+  if (!frame_offsets || !origins || !leaves || !out_frame_offsets) return VG_ERR_INVALID_ARG;
+  vg_status s = check_outputs(n_total, xyz, out_keys, out_centroids, out_counts, cap,
+                              out_frame_offsets, out_point_to_voxel, out_error, workspace);
+  if (s != VG_OK) return s;
+  if (!aligned(frame_offsets, 8) || !aligned(origins, 4) || !aligned(leaves, 4))
+    return VG_ERR_ALIGN;
+  const bool from_min = (flags & VG_ORIGIN_FROM_MIN) != 0;
+  FramesArg fr{frame_offsets, n_frames, n_total, from_min ? nullptr : origins,
+               from_min ? origins : nullptr, leaves, 0.0f, grid_per_sm_of(flags)};
+  // V lands in out_frame_offsets[n_frames]; the segmented reduction also writes it there.
+  SegOut out{out_keys, out_centroids, out_counts, nullptr, cap, out_frame_offsets + n_frames,
+             out_frame_offsets, out_point_to_voxel};
+  return run_frames(xyz, fr, from_min, out, out_error, workspace, workspace_bytes, flags,
+                    reinterpret_cast<cudaStream_t>(stream));
+}
+
+size_t vg_pyramid_workspace_bytes(int64_t n_points, int levels, int flags) {
+  (void)flags;
+  if (n_points < 0 || levels < 1 || levels > kMaxLevels) return 0;
+  return pyramid_layout(n_points, levels).total;
+}
+
+vg_status vg_pyramid(const float* xyz, int64_t n, float* origin, float leaf, int levels,
+                     uint64_t* out_keys, float* out_centroids, uint32_t* out_counts,
+                     int64_t cap_total, int64_t* out_level_offsets, int32_t* out_point_to_voxel,
+                     int32_t* out_error, void* workspace, size_t workspace_bytes, int flags,
+                     vg_stream_t stream_) {
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+  if (!(leaf > 0.0f) || !std::isfinite(leaf)) return VG_ERR_INVALID_ARG;
+  if (levels < 1 || levels > kMaxLevels) return VG_ERR_INVALID_ARG;
+  if ((flags & ~VG_ORIGIN_FROM_MIN) != 0) return VG_ERR_INVALID_ARG;
+  if (!origin || !out_level_offsets) return VG_ERR_INVALID_ARG;
+  if (!std::isfinite(leaf * float(1u << (levels - 1)))) return VG_ERR_INVALID_ARG;
+  vg_status s = check_outputs(n, xyz, out_keys, out_centroids, out_counts, cap_total,
+                              out_level_offsets, out_point_to_voxel, out_error, workspace);
+  if (s != VG_OK) return s;
+  if (!aligned(origin, 4)) return VG_ERR_ALIGN;
+  const PyramidLayout P = pyramid_layout(n, levels);
+  if (!workspace || workspace_bytes < P.total) return VG_ERR_WORKSPACE;
   char* ws = static_cast<char*>(workspace);
+  const SortLayout L = sort_layout(n, 1);
   State* st = reinterpret_cast<State*>(ws + L.state);
-  uint64_t* keys0 = reinterpret_cast<uint64_t*>(ws + L.keys0);
-  uint64_t* keys1 = reinterpret_cast<uint64_t*>(ws + L.keys1);
-  uint32_t* idx0 = reinterpret_cast<uint32_t*>(ws + L.idx0);
-  uint32_t* idx1 = reinterpret_cast<uint32_t*>(ws + L.idx1);
-  uint32_t* lb_a = reinterpret_cast<uint32_t*>(ws + L.lb_a);
-  uint32_t* lb_b = reinterpret_cast<uint32_t*>(ws + L.lb_b);
-  SegStatus* seg_lb = reinterpret_cast<SegStatus*>(ws + L.seg_lb);
+  const FrameState* fs = reinterpret_cast<const FrameState*>(ws + L.frames);
+  long long* sums[2] = {reinterpret_cast<long long*>(ws + P.sums_a),
+                        reinterpret_cast<long long*>(ws + P.sums_b)};
+  uint32_t* merge_lb = reinterpret_cast<uint32_t*>(ws + P.merge_lb);
   int* err = out_error ? reinterpret_cast<int*>(out_error) : &st->error;
-  const uint32_t spins = spin_limit();
   const bool from_min = (flags & VG_ORIGIN_FROM_MIN) != 0;
 
-  cudaError_t e = cudaMemsetAsync(ws, 0, L.zero_bytes, stream);
-  if (e == cudaSuccess && out_error) e = cudaMemsetAsync(out_error, 0, sizeof(int32_t), stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(out_num_voxels, 0, sizeof(int64_t), stream);
-  if (e == cudaSuccess && out_point_to_voxel && n > 0)
-    e = cudaMemsetAsync(out_point_to_voxel, 0xff, size_t(n) * sizeof(int32_t), stream);
-  mark(0, stream);
-  if (e == cudaSuccess && from_min) e = launch_origin(xyz, n, st, stream);
-  mark(1, stream);
-  if (e == cudaSuccess) e = launch_keys(xyz, n, origin, from_min, leaf, st, keys0, err, stream);
-  mark(2, stream);
-  for (int p = 0; p < kMaxPasses && e == cudaSuccess; ++p) {
-    e = launch_sort_pass(st, keys0, idx0, keys1, idx1, lb_a, lb_b, n, p, spins, err, stream);
-    mark(3 + p, stream);
-  }
+  cudaError_t e = cudaMemsetAsync(out_level_offsets, 0, size_t(levels + 1) * sizeof(int64_t), stream);
   if (e == cudaSuccess)
-    e = launch_segreduce(st, keys0, idx0, keys1, idx1, xyz, leaf, seg_lb, n, out_keys,
-                         out_centroids, out_counts, cap, out_num_voxels, out_point_to_voxel,
-                         spins, err, stream);
-  mark(3 + kMaxPasses, stream);
+    e = cudaMemsetAsync(merge_lb, 0, size_t(levels) * size_t(P.merge_tiles) * sizeof(uint32_t),
+                        stream);
+  if (e != cudaSuccess) return VG_ERR_CUDA;
+  FramesArg fr{nullptr, 1, n, from_min ? nullptr : origin, from_min ? origin : nullptr, nullptr, leaf, 0};
+  SegOut out{out_keys, out_centroids, out_counts, sums[0], cap_total, out_level_offsets + 1,
+             nullptr, out_point_to_voxel};
+  s = run_frames(xyz, fr, from_min, out, out_error, workspace, L.total, VG_METHOD_SORT, stream);
+  if (s != VG_OK) return s;
+  const uint32_t spins = spin_limit();
+  for (int k = 1; k < levels && e == cudaSuccess; ++k)
+    e = launch_pyramid_merge(st, fs, k, out_keys, out_centroids, out_counts, sums[(k - 1) & 1],
+                             sums[k & 1], out_level_offsets, cap_total,
+                             merge_lb + size_t(k - 1) * size_t(P.merge_tiles), n, spins, err,
+                             stream);
+  return cuda_status(e);
+}
+
+vg_status vg_downsample_backward(const float* grad_centroids, const uint32_t* counts,
+                                 const int32_t* point_to_voxel, int64_t n, int64_t num_voxels,
+                                 float* grad_xyz, int32_t* out_error, vg_stream_t stream_) {
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+  if (n < 0 || num_voxels < 0 || n > kMaxPoints) return VG_ERR_INVALID_ARG;
+  if (n > 0 && (!point_to_voxel || !grad_xyz || !out_error)) return VG_ERR_INVALID_ARG;
+  if (num_voxels > 0 && (!grad_centroids || !counts)) return VG_ERR_INVALID_ARG;
+  if (!aligned(grad_centroids, 4) || !aligned(counts, 4) || !aligned(point_to_voxel, 4) ||
+      !aligned(grad_xyz, 4) || !aligned(out_error, 4))
+    return VG_ERR_ALIGN;
+  if (n == 0) return VG_OK;
+  cudaError_t e = cudaMemsetAsync(out_error, 0, sizeof(int32_t), stream);
+  if (e == cudaSuccess)
+    e = launch_backward(grad_centroids, counts, point_to_voxel, n, num_voxels, grad_xyz,
+                        reinterpret_cast<int*>(out_error), stream);
   return cuda_status(e);
 }
 

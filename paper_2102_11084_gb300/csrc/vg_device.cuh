@@ -3,12 +3,14 @@
 // Voxel key (arXiv 2102.11084 Sec. II-C, ordered subdivision of space): per axis, in
 // IEEE binary32 with round-to-nearest and no contraction, i = floor(fl(fl(p-o)/leaf)),
 // 0 <= i < 2^21; the key interleaves bit b of ix, iy, iz into bits 3b, 3b+1, 3b+2.
+// Batched calls put the frame id above a key_shift-bit key field, so one sort orders
+// every frame's voxels at once.
 //
 // Centroid accumulator (not fixed by the paper): each point contributes the offset from
 // its voxel corner c = fl(o + fl(i*leaf)), quantised to a signed integer in units of
 // leaf/2^20; sums are int64, so any summation order gives the same bits.  The centroid is
-// c + (sum/n)/2^20*leaf evaluated in binary32.  Every path (sort, hash, batch, pyramid)
-// uses exactly these functions, so their outputs agree bit for bit.
+// c + (sum/n)/2^20*leaf evaluated in binary32.  Every path (sort, hash, batch, pyramid
+// level 0) uses exactly these functions, so their outputs agree bit for bit.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -17,8 +19,10 @@
 
 namespace vg {
 
+constexpr unsigned kFullMask = 0xffffffffu;
 constexpr float kAxisLimitF = 2097152.0f;   // 2^21
 constexpr float kQuantScale = 1048576.0f;   // 2^20 units per leaf
+constexpr uint64_t kKeySentinel = ~0ull;    // invalid point
 
 // ---- error word -------------------------------------------------------------------
 // The first error code wins; later ones are dropped.
@@ -66,8 +70,8 @@ __device__ __forceinline__ uint64_t morton3(uint32_t ix, uint32_t iy, uint32_t i
   return spread3(ix) | (spread3(iy) << 1) | (spread3(iz) << 2);
 }
 
-// Key of a point, or false if the point is invalid / out of range (*range_bad set for
-// the latter).
+// Morton key of a point, or false if the point is invalid / out of range (*range_bad
+// set for the latter).
 __device__ __forceinline__ bool point_key(float x, float y, float z, const float o[3],
                                           float leaf, uint64_t* key, bool* range_bad) {
   if (!point_valid(x, y, z)) return false;
@@ -80,6 +84,18 @@ __device__ __forceinline__ bool point_key(float x, float y, float z, const float
   }
   *key = morton3(ix, iy, iz);
   return true;
+}
+
+// Split a sort key into (frame, per-frame voxel key).  key_shift == 64: one frame.
+__device__ __forceinline__ uint32_t key_frame(uint64_t key, uint32_t key_shift) {
+  return key_shift >= 64 ? 0u : static_cast<uint32_t>(key >> key_shift);
+}
+__device__ __forceinline__ uint64_t key_local(uint64_t key, uint32_t key_shift) {
+  return key_shift >= 64 ? key : (key & ((1ull << key_shift) - 1ull));
+}
+__device__ __forceinline__ uint64_t key_compose(uint32_t frame, uint64_t local,
+                                                uint32_t key_shift) {
+  return key_shift >= 64 ? local : ((uint64_t(frame) << key_shift) | local);
 }
 
 // ---- fixed-point centroid accumulator ------------------------------------------------
@@ -115,22 +131,22 @@ __device__ __forceinline__ int quant_offset(float p, float c, float inv_unit) {
   return __float2int_rn(__fmul_rn(__fsub_rn(p, c), inv_unit));
 }
 
-// Offsets of point (x,y,z) from the corner of voxel `key`, as one accumulator entry.
-__device__ __forceinline__ Acc point_acc(uint64_t key, float x, float y, float z,
+// Offsets of point (x,y,z) from the corner of voxel `local` (a per-frame Morton key).
+__device__ __forceinline__ Acc point_acc(uint64_t local, float x, float y, float z,
                                          const float o[3], float leaf, float inv_unit) {
   Acc a;
   a.n = 1;
-  a.s[0] = quant_offset(x, voxel_corner(compact3(key), o[0], leaf), inv_unit);
-  a.s[1] = quant_offset(y, voxel_corner(compact3(key >> 1), o[1], leaf), inv_unit);
-  a.s[2] = quant_offset(z, voxel_corner(compact3(key >> 2), o[2], leaf), inv_unit);
+  a.s[0] = quant_offset(x, voxel_corner(compact3(local), o[0], leaf), inv_unit);
+  a.s[1] = quant_offset(y, voxel_corner(compact3(local >> 1), o[1], leaf), inv_unit);
+  a.s[2] = quant_offset(z, voxel_corner(compact3(local >> 2), o[2], leaf), inv_unit);
   return a;
 }
 
-// Centroid of voxel `key` from its accumulator (n >= 1).
-__device__ __forceinline__ void acc_centroid(uint64_t key, const Acc& a, const float o[3],
+// Centroid of voxel `local` from a sum S in units of leaf/2^20 relative to its corner.
+__device__ __forceinline__ void acc_centroid(uint64_t local, const Acc& a, const float o[3],
                                              float leaf, float inv_unit, float out[3]) {
   const float fn = __uint2float_rn(a.n);
-  const uint32_t ii[3] = {compact3(key), compact3(key >> 1), compact3(key >> 2)};
+  const uint32_t ii[3] = {compact3(local), compact3(local >> 1), compact3(local >> 2)};
 #pragma unroll
   for (int ax = 0; ax < 3; ++ax) {
     const float c = voxel_corner(ii[ax], o[ax], leaf);
@@ -155,8 +171,16 @@ __device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
+__device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
 __device__ __forceinline__ void st_release(uint32_t* p, uint32_t v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_release64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 __device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
   uint32_t v;
@@ -172,6 +196,141 @@ __device__ __forceinline__ int sort_passes(unsigned long long maxkey) {
   if (maxkey == 0) return 0;
   const int bits = 64 - __clzll(static_cast<long long>(maxkey));
   return (bits + kRadixBits - 1) / kRadixBits;
+}
+
+// Bounded chained-scan wait on a tile status word (flag | 30-bit value).  Returns the
+// exclusive prefix of tile `tile`'s value over tiles 0..tile-1.
+__device__ __forceinline__ uint32_t lookback_u32(const uint32_t* status, size_t stride,
+                                                 int tile, uint32_t spin_limit, int* err) {
+  uint32_t excl = 0;
+  int j = tile - 1;
+  uint32_t spins = 0;
+  while (j >= 0) {
+    const uint32_t s = ld_relaxed(status + size_t(j) * stride);
+    const uint32_t f = s & ~kValueMask;
+    if (f == 0) {
+      if (++spins > spin_limit) {
+        set_error(err, kErrTimeout);
+        break;
+      }
+      if (spins > 64) __nanosleep(64);
+      continue;
+    }
+    excl += s & kValueMask;
+    if (f == kFlagPrefix) break;
+    --j;
+  }
+  return excl;
+}
+
+// ---- block-wide helpers (256 threads) -------------------------------------------------
+// Exclusive scan of one u32 per thread; *total receives the block sum.  `tmp` holds
+// blockDim/32 words of shared memory.  Contains __syncthreads.
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* total,
+                                                    uint32_t* tmp) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  uint32_t inc = v;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const uint32_t y = __shfl_up_sync(kFullMask, inc, off);
+    if (lane >= off) inc += y;
+  }
+  __syncthreads();
+  if (lane == 31) tmp[warp] = inc;
+  __syncthreads();
+  uint32_t before = 0, all = 0;
+  for (int w = 0; w < nw; ++w) {
+    const uint32_t x = tmp[w];
+    if (w < warp) before += x;
+    all += x;
+  }
+  *total = all;
+  return before + inc - v;
+}
+
+// ---- frame decomposition (chunks of kChunk points inside one frame) -----------------------
+// Loads the frame offsets into s_off[0..F] and the chunk prefix into s_cstart[0..F];
+// returns the number of chunks.  Bad offsets (not starting at 0, not ending at n, or
+// decreasing) record kErrInvalidArg and yield zero chunks.  Contains __syncthreads.
+__device__ __forceinline__ uint32_t build_chunk_map(const FramesArg& fr, int64_t* s_off,
+                                                    uint32_t* s_cstart, uint32_t* tmp,
+                                                    int* err) {
+  const int F = fr.nframes;
+  for (int f = threadIdx.x; f <= F; f += blockDim.x)
+    s_off[f] = fr.offsets ? fr.offsets[f] : (f == 0 ? 0 : fr.n);
+  __syncthreads();
+  // chunk counts of the frames owned by this thread: frames [4t, 4t+4)
+  constexpr int kPer = kMaxFrames / kStreamThreads;
+  uint32_t c[kPer];
+  uint32_t mine = 0;
+  bool bad = false;
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    const int f = threadIdx.x * kPer + k;
+    c[k] = 0;
+    if (f < F) {
+      const int64_t a = s_off[f], b = s_off[f + 1];
+      if (b < a || a < 0 || b > fr.n) bad = true;
+      else c[k] = static_cast<uint32_t>(ceil_div(b - a, kChunk));
+    }
+    mine += c[k];
+  }
+  if (threadIdx.x == 0 && (s_off[0] != 0 || s_off[F] != fr.n)) bad = true;
+  const int any_bad = __syncthreads_or(bad);
+  uint32_t total;
+  uint32_t run = block_excl_scan(any_bad ? 0u : mine, &total, tmp);
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    const int f = threadIdx.x * kPer + k;
+    if (f <= F) s_cstart[f] = run;
+    if (!any_bad) run += c[k];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) s_cstart[F] = any_bad ? 0u : total;
+  if (any_bad && threadIdx.x == 0 && blockIdx.x == 0) set_error(err, kErrInvalidArg);
+  __syncthreads();
+  return any_bad ? 0u : total;
+}
+
+// Frame holding chunk c (largest f with s_cstart[f] <= c, skipping empty frames).
+__device__ __forceinline__ int chunk_frame(const uint32_t* s_cstart, int F, uint32_t c) {
+  int lo = 0, hi = F - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (s_cstart[mid] <= c) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Loads points p0..p0+3 (x,y,z interleaved) into v[12]; rows at or beyond `end` are NaN.
+__device__ __forceinline__ void load4(const float* __restrict__ xyz, int64_t p0, int64_t end,
+                                      bool vec, float v[12]) {
+  if (vec && p0 + 4 <= end) {
+    const float4* q = reinterpret_cast<const float4*>(xyz + 3 * p0);
+    const float4 a = __ldcs(q), b = __ldcs(q + 1), c = __ldcs(q + 2);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    v[8] = c.x; v[9] = c.y; v[10] = c.z; v[11] = c.w;
+  } else {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const bool in = p0 + j < end;
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+        v[3 * j + a] = in ? __ldcs(xyz + 3 * (p0 + j) + a) : __int_as_float(0x7fc00000);
+    }
+  }
+}
+
+// 64-bit mixer (the MurmurHash3 finaliser) for the voxel hash table.
+__device__ __forceinline__ uint64_t hash64(uint64_t x) {
+  x ^= x >> 33;
+  x *= 0xff51afd7ed558ccdull;
+  x ^= x >> 33;
+  x *= 0xc4ceb9fe1a85ec53ull;
+  x ^= x >> 33;
+  return x;
 }
 
 }  // namespace vg

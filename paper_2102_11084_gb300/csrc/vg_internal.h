@@ -19,9 +19,14 @@ constexpr int kSegThreads = 256;
 constexpr int kSegItems = 8;
 constexpr int kSegTile = kSegThreads * kSegItems;
 
-// Streaming kernels (origin, keys): 256 threads, 4 points per thread per iteration.
+// Streaming kernels (origin, keys, hash insert): 256 threads, 4 points per thread; the
+// cloud is cut into chunks of 1024 points that never cross a frame boundary.
 constexpr int kStreamThreads = 256;
 constexpr int kStreamPoints = 4;
+constexpr int kChunk = kStreamThreads * kStreamPoints;
+
+// Frames per batched call.
+constexpr int kMaxFrames = 1024;
 
 // Chained-scan status flags (top two bits of a 32-bit status word).
 constexpr uint32_t kFlagAggregate = 1u << 30;
@@ -34,18 +39,31 @@ constexpr int64_t kMaxPoints = (int64_t(1) << 30) - 1;
 // Default spin limit of a chained-scan wait before it gives up with a timeout status.
 constexpr uint32_t kDefaultSpinLimit = 1u << 22;
 
+// Status codes shared with include/vg.h (device side).
+constexpr int kErrInvalidArg = 1;
+constexpr int kErrRange = 3;
+constexpr int kErrCapacity = 4;
+constexpr int kErrTimeout = 6;
+
+// Per-frame device state (workspace, zeroed by every call).
+struct FrameState {
+  uint32_t ord_min_inv[3];  // max of ~ordered(x) over valid points: the min, via atomicMax
+  uint32_t ord_max[3];      // max of ordered(x) over valid points
+  float origin[3];          // origin used for the frame
+  float leaf;               // leaf used for the frame
+  uint32_t pad[2];
+};
+
 // Per-call device state, at the start of the workspace.  Zeroed by the call.
 struct alignas(256) State {
-  uint32_t ord_min_inv[3];   // max over valid points of ~ordered(x): min via atomicMax
-  uint32_t pad0;
-  float origin[3];           // origin used by the call
-  uint32_t pad1;
-  unsigned long long maxkey; // largest valid key
-  uint32_t nvalid;           // number of valid points (compacted key count)
-  uint32_t pad3;
-  uint32_t tile_ctr[kMaxPasses + 4];
-  int32_t error;             // internal error word when the caller passes none
-  uint32_t pad2[3];
+  unsigned long long maxkey;  // largest sort key
+  uint32_t nvalid;            // number of valid points
+  uint32_t nitems;            // number of entries the radix sort orders
+  uint32_t key_shift;         // bits of the per-frame key field (frame id above it)
+  uint32_t nframes;
+  uint32_t nchunks;           // chunks of the frame decomposition
+  int32_t error;              // internal error word when the caller passes none
+  uint32_t tile_ctr[kMaxPasses + 8];
   uint32_t hist[kMaxPasses][kRadix];
 };
 
@@ -63,28 +81,50 @@ struct alignas(16) SegStatus {
   long long pad3;
 };
 
+// Frames of one call.  A single cloud is one frame [0, n) with offsets == nullptr.
+struct FramesArg {
+  const int64_t* offsets;  // device [F+1], or nullptr for one frame
+  int nframes;
+  int64_t n;               // total points
+  const float* origin_in;  // device [F,3] origins to use, or nullptr: per-frame minimum
+  float* origin_out;       // device [F,3] receives the minimum (when origin_in == nullptr)
+  const float* leaves;     // device [F] per-frame leaves, or nullptr: `leaf` for all
+  float leaf;
+  int grid_per_sm;         // blocks per SM of the streaming kernels (0 = default 8)
+};
+
+// Grid of the streaming kernels: one block per chunk, at most grid_per_sm blocks per SM.
+int stream_grid(const FramesArg& fr);
+
 constexpr int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 constexpr size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-// Workspace layout of the sort path for n points.
+// Upper bound of the chunk count of n points in F frames.
+constexpr int64_t max_chunks(int64_t n, int frames) { return ceil_div(n, kChunk) + frames; }
+
+// Workspace layout of the sort path for n points in `frames` frames.
 struct SortLayout {
-  size_t state, keys0, keys1, idx0, idx1, lb_a, lb_b, seg_lb, total;
+  size_t state, frames, keys0, keys1, idx0, idx1, lb_a, lb_b, seg_lb, total;
   size_t zero_bytes;  // bytes from `state` that must be zero at call start
   int64_t sort_tiles, seg_tiles;
 };
-constexpr SortLayout sort_layout(int64_t n) {
+
+constexpr SortLayout sort_layout(int64_t n, int frames = 1) {
   SortLayout L{};
   const int64_t nn = n < 1 ? 1 : n;
+  const int64_t ff = frames < 1 ? 1 : frames;
   L.sort_tiles = ceil_div(nn, kSortTile);
   L.seg_tiles = ceil_div(nn, kSegTile);
   size_t off = 0;
   L.state = off;
   off = align_up(off + sizeof(State), 256);
+  L.frames = off;
+  off = align_up(off + size_t(ff) * sizeof(FrameState), 256);
   L.lb_a = off;
   off = align_up(off + size_t(L.sort_tiles) * kRadix * sizeof(uint32_t), 256);
   L.seg_lb = off;
   off = align_up(off + size_t(L.seg_tiles) * sizeof(SegStatus), 256);
-  L.zero_bytes = off;  // state, pass-0 status rows and segment status: zeroed per call
+  L.zero_bytes = off;  // state, frames, pass-0 status rows and segment status
   L.lb_b = off;
   off = align_up(off + size_t(L.sort_tiles) * kRadix * sizeof(uint32_t), 256);
   L.keys0 = off;
@@ -100,21 +140,131 @@ constexpr SortLayout sort_layout(int64_t n) {
 }
 
 int num_sms();
-
 uint32_t spin_limit();
 
 // Launchers (all asynchronous on `stream`).
-cudaError_t launch_origin(const float* xyz, int64_t n, State* st, cudaStream_t stream);
-cudaError_t launch_keys(const float* xyz, int64_t n, float* origin_user, bool from_min,
-                        float leaf, State* st, uint64_t* keys, int* err, cudaStream_t stream);
+// a1: per-frame min (and max) of the valid points into FrameState.
+cudaError_t launch_origin(const float* xyz, const FramesArg& fr, State* st, FrameState* fs,
+                          int* err, cudaStream_t stream);
+// a2: per-point sort keys (frame id above a key_shift-bit Morton field; ~0 = invalid).
+cudaError_t launch_keys(const float* xyz, const FramesArg& fr, bool have_extent, State* st,
+                        FrameState* fs, uint64_t* keys, int* err, cudaStream_t stream);
+// a3: one radix pass.  compact_input: pass 0 reads st->nitems compacted keys with their
+// payload from idx0 (hash path) instead of n raw keys with an implicit index.
 cudaError_t launch_sort_pass(State* st, uint64_t* keys0, uint32_t* idx0, uint64_t* keys1,
                              uint32_t* idx1, uint32_t* lb_a, uint32_t* lb_b, int64_t n_max,
-                             int pass, uint32_t spin_limit, int* err, cudaStream_t stream);
-cudaError_t launch_segreduce(State* st, const uint64_t* keys0, const uint32_t* idx0,
-                             const uint64_t* keys1, const uint32_t* idx1, const float* xyz,
-                             float leaf, SegStatus* lb, int64_t n_max, uint64_t* out_keys,
-                             float* out_centroids, uint32_t* out_counts, int64_t cap,
-                             int64_t* out_num_voxels, int32_t* out_p2v, uint32_t spin_limit,
-                             int* err, cudaStream_t stream);
+                             int pass, bool compact_input, uint32_t spin_limit, int* err,
+                             cudaStream_t stream);
+// a4 + a5: reduce-by-key of the sorted table into key-ordered voxels.
+struct SegOut {
+  uint64_t* keys;
+  float* centroids;
+  uint32_t* counts;
+  long long* sums;         // optional [cap,3] fixed-point sums (pyramid input)
+  int64_t cap;
+  int64_t* num_voxels;
+  int64_t* frame_offsets;  // optional [F+1] per-frame output offsets
+  int32_t* p2v;
+};
+cudaError_t launch_segreduce(State* st, const FrameState* fs, int nframes,
+                             const uint64_t* keys0, const uint32_t* idx0, const uint64_t* keys1,
+                             const uint32_t* idx1, const float* xyz, SegStatus* lb,
+                             int64_t n_max, const SegOut& out, uint32_t spin_limit, int* err,
+                             cudaStream_t stream);
+
+// ---- hash path ----
+struct alignas(32) HashAcc {
+  uint32_t n;
+  uint32_t pad;
+  long long s[3];
+};
+struct HashTable {
+  unsigned long long* keys;  // [H], ~0 = empty
+  HashAcc* acc;              // [H]
+  uint32_t mask;             // H - 1, H a power of two
+};
+
+// Slot count of the hash table for n points: a power of two >= 2n (never fills).
+constexpr int64_t hash_slots(int64_t n) {
+  int64_t h = 1024;
+  while (h < 2 * n) h <<= 1;
+  return h;
+}
+
+struct HashLayout {
+  size_t state, frames, lb_a, zero_bytes, lb_b, keys0, keys1, idx0, idx1, tkeys, tacc, slot_rank,
+      point_slot, total;
+  int64_t slots, sort_tiles;
+};
+
+constexpr HashLayout hash_layout(int64_t n, int frames = 1) {
+  HashLayout L{};
+  const int64_t nn = n < 1 ? 1 : n;
+  const int64_t ff = frames < 1 ? 1 : frames;
+  L.slots = hash_slots(nn);
+  L.sort_tiles = ceil_div(nn, kSortTile);
+  size_t off = 0;
+  L.state = off;
+  off = align_up(off + sizeof(State), 256);
+  L.frames = off;
+  off = align_up(off + size_t(ff) * sizeof(FrameState), 256);
+  L.lb_a = off;
+  off = align_up(off + size_t(L.sort_tiles) * kRadix * sizeof(uint32_t), 256);
+  L.zero_bytes = off;
+  L.lb_b = off;
+  off = align_up(off + size_t(L.sort_tiles) * kRadix * sizeof(uint32_t), 256);
+  L.keys0 = off;
+  off = align_up(off + size_t(nn) * sizeof(uint64_t), 256);
+  L.keys1 = off;
+  off = align_up(off + size_t(nn) * sizeof(uint64_t), 256);
+  L.idx0 = off;
+  off = align_up(off + size_t(nn) * sizeof(uint32_t), 256);
+  L.idx1 = off;
+  off = align_up(off + size_t(nn) * sizeof(uint32_t), 256);
+  L.tkeys = off;
+  off = align_up(off + size_t(L.slots) * sizeof(unsigned long long), 256);
+  L.tacc = off;
+  off = align_up(off + size_t(L.slots) * sizeof(HashAcc), 256);
+  L.slot_rank = off;
+  off = align_up(off + size_t(L.slots) * sizeof(uint32_t), 256);
+  L.point_slot = off;
+  off = align_up(off + size_t(nn) * sizeof(uint32_t), 256);
+  L.total = off;
+  return L;
+}
+
+cudaError_t launch_hash_insert(const float* xyz, const FramesArg& fr, bool have_extent, State* st,
+                               FrameState* fs, const HashTable& tab, uint32_t* point_slot,
+                               uint32_t spin_limit, int* err, cudaStream_t stream);
+cudaError_t launch_hash_compact(const HashTable& tab, State* st, uint64_t* keys, uint32_t* slots,
+                                cudaStream_t stream);
+cudaError_t launch_hash_finalize(const State* st, const FrameState* fs, int nframes,
+                                 const uint64_t* keys0, const uint32_t* idx0,
+                                 const uint64_t* keys1, const uint32_t* idx1,
+                                 const HashTable& tab, uint32_t* slot_rank, int64_t n_max,
+                                 const SegOut& out, int* err, cudaStream_t stream);
+cudaError_t launch_hash_p2v(const uint32_t* point_slot, const uint32_t* slot_rank, int64_t n,
+                            int32_t* p2v, cudaStream_t stream);
+
+// ---- pyramid ----
+constexpr int kMaxLevels = 8;
+constexpr int kMergeThreads = 256;
+constexpr int kMergeItems = 8;
+constexpr int kMergeTile = kMergeThreads * kMergeItems;
+// Merges pyramid level k-1 (rows [off[k-1], off[k])) into level k (written from off[k]).
+cudaError_t launch_pyramid_merge(State* st, const FrameState* fs, int level, uint64_t* keys,
+                                 float* centroids, uint32_t* counts, const long long* sums_in,
+                                 long long* sums_out, int64_t* level_offsets, int64_t cap,
+                                 uint32_t* lb, int64_t n_max, uint32_t spin_limit, int* err,
+                                 cudaStream_t stream);
+
+// Test: a bounded chained-scan wait on words nobody sets (records kErrTimeout).
+cudaError_t launch_debug_wait(const uint32_t* status, int tile, uint32_t limit, int* err,
+                              cudaStream_t stream);
+
+// ---- backward ----
+cudaError_t launch_backward(const float* grad_centroids, const uint32_t* counts,
+                            const int32_t* p2v, int64_t n, int64_t num_voxels, float* grad_xyz,
+                            int* err, cudaStream_t stream);
 
 }  // namespace vg

@@ -1,140 +1,154 @@
-// Steps a1 (origin = cloud minimum) and a2 (voxel key per point).
+// Steps a1 (origin = per-frame cloud minimum) and a2 (sort key per point).
 //
 // arXiv 2102.11084 Sec. II-C normalises each point and classifies it into one cell of an
-// ordered subdivision of space ("buscar subdiv" / "actualizar tabla_subdiv" of
-// Algorithm 1); here the cell is the voxel of an unbounded lattice with a caller-chosen
-// origin and leaf, keyed by a 63-bit Morton code.  Both kernels stream the xyz array
-// once with 16-byte loads (4 points = 3 float4 per lane) and are HBM-bound.
+// ordered subdivision of space (the classification and table update of Algorithm 1);
+// here the cell is the voxel of an unbounded lattice with a caller-chosen origin and
+// leaf, keyed by a 63-bit Morton code.  Both kernels stream xyz once with 16-byte loads
+// (4 points = 3 float4 per lane) over chunks of 1024 points that never cross a frame,
+// each block walking a contiguous run of chunks; they are HBM-bound.
 #include "vg_device.cuh"
 #include "vg_internal.h"
+#include "vg_stream.cuh"
 
 namespace vg {
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
-constexpr uint64_t kSentinel = ~0ull;
-
-// Loads points p0..p0+3 (x,y,z interleaved) into v[12]; rows at or beyond n are NaN.
-template <bool kVec>
-__device__ __forceinline__ void load4(const float* __restrict__ xyz, int64_t p0, int64_t n,
-                                      float v[12]) {
-  if (kVec && p0 + 4 <= n) {
-    const float4* q = reinterpret_cast<const float4*>(xyz + 3 * p0);
-    const float4 a = __ldcs(q), b = __ldcs(q + 1), c = __ldcs(q + 2);
-    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
-    v[8] = c.x; v[9] = c.y; v[10] = c.z; v[11] = c.w;
-  } else {
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const bool in = p0 + j < n;
-#pragma unroll
-      for (int a = 0; a < 3; ++a) v[3 * j + a] = in ? __ldcs(xyz + 3 * (p0 + j) + a) : __int_as_float(0x7fc00000);
-    }
-  }
-}
-
-// a1: per-axis minimum over the valid points, folded into st->ord_min_inv with atomicMax
-// on ~ordered(x) (so that a zeroed word means "no valid point").
-template <bool kVec>
-__global__ __launch_bounds__(kStreamThreads) void origin_kernel(const float* __restrict__ xyz,
-                                                                int64_t n, State* st) {
-  float mn[3] = {INFINITY, INFINITY, INFINITY};
-  const int64_t stride = int64_t(gridDim.x) * kStreamThreads * kStreamPoints;
-  for (int64_t p0 = (int64_t(blockIdx.x) * kStreamThreads + threadIdx.x) * kStreamPoints; p0 < n;
-       p0 += stride) {
-    float v[12];
-    load4<kVec>(xyz, p0, n, v);
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      if (point_valid(v[3 * j], v[3 * j + 1], v[3 * j + 2])) {
-#pragma unroll
-        for (int a = 0; a < 3; ++a) mn[a] = fminf(mn[a], v[3 * j + a]);
-      }
-    }
-  }
-  __shared__ float red[kStreamThreads / 32][3];
+// Reduces per-thread min/max over the block and folds them into frame f's state.
+__device__ __forceinline__ void flush_extent(float mn[3], float mx[3], FrameState* fs, int f,
+                                             float (*red)[6]) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
 #pragma unroll
-    for (int off = 16; off; off >>= 1) mn[a] = fminf(mn[a], __shfl_xor_sync(kFull, mn[a], off));
-    if (lane == 0) red[warp][a] = mn[a];
+    for (int off = 16; off; off >>= 1) {
+      mn[a] = fminf(mn[a], __shfl_xor_sync(kFullMask, mn[a], off));
+      mx[a] = fmaxf(mx[a], __shfl_xor_sync(kFullMask, mx[a], off));
+    }
+  }
+  __syncthreads();
+  if (lane == 0) {
+    for (int a = 0; a < 3; ++a) {
+      red[warp][a] = mn[a];
+      red[warp][3 + a] = mx[a];
+    }
   }
   __syncthreads();
   if (threadIdx.x < 3) {
-    float m = INFINITY;
-    for (int w = 0; w < kStreamThreads / 32; ++w) m = fminf(m, red[w][threadIdx.x]);
-    if (m != INFINITY) atomicMax(&st->ord_min_inv[threadIdx.x], ~float_to_ordered(m));
+    const int a = threadIdx.x;
+    float m = INFINITY, M = -INFINITY;
+    for (int w = 0; w < kStreamThreads / 32; ++w) {
+      m = fminf(m, red[w][a]);
+      M = fmaxf(M, red[w][3 + a]);
+    }
+    if (m != INFINITY) {
+      atomicMax(&fs[f].ord_min_inv[a], ~float_to_ordered(m));
+      atomicMax(&fs[f].ord_max[a], float_to_ordered(M));
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    mn[a] = INFINITY;
+    mx[a] = -INFINITY;
   }
 }
 
-// a2: key per point (kSentinel for invalid or out-of-range rows), plus the digit-0
-// histogram of the valid keys, the number of valid points and the largest valid key.
-// Each warp handles 128 consecutive points per iteration (4 per lane).
-template <bool kVec>
-__global__ __launch_bounds__(kStreamThreads) void key_kernel(
-    const float* __restrict__ xyz, int64_t n, float* origin_user, int from_min, float leaf,
-    State* st, uint64_t* __restrict__ keys, int* err) {
-  __shared__ float so[3];
-  __shared__ uint32_t hist[kRadix];
-  __shared__ uint32_t wcount[kStreamThreads / 32];
-  __shared__ unsigned long long wmax[kStreamThreads / 32];
-  if (threadIdx.x < 3) {
-    float o;
-    if (from_min) {
-      const uint32_t u = st->ord_min_inv[threadIdx.x];
-      o = (u == 0) ? 0.0f : ordered_to_float(~u);
-    } else {
-      o = origin_user[threadIdx.x];
+// a1: per-frame minimum and maximum over the valid points.
+__global__ __launch_bounds__(kStreamThreads) void origin_kernel(const float* __restrict__ xyz,
+                                                                FramesArg fr, FrameState* fs,
+                                                                int* err) {
+  __shared__ ChunkSmem sm;
+  __shared__ float red[kStreamThreads / 32][6];
+  const uint32_t T = build_chunk_map(fr, sm.off, sm.cstart, sm.tmp, err);
+  uint32_t c0, c1;
+  block_range(T, &c0, &c1);
+  const bool xyz_vec = (reinterpret_cast<uintptr_t>(xyz) & 15) == 0;
+  float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+  int cur = -1;
+  for (uint32_t c = c0; c < c1; ++c) {
+    const int f = chunk_frame(sm.cstart, fr.nframes, c);
+    if (f != cur) {
+      if (cur >= 0) flush_extent(mn, mx, fs, cur, red);
+      cur = f;
     }
-    so[threadIdx.x] = o;
-    if (blockIdx.x == 0) {
-      st->origin[threadIdx.x] = o;
-      if (from_min) origin_user[threadIdx.x] = o;
+    const int64_t start = sm.off[f] + int64_t(c - sm.cstart[f]) * kChunk;
+    const int64_t end = min(start + kChunk, sm.off[f + 1]);
+    const int64_t p0 = start + int64_t(threadIdx.x) * kStreamPoints;
+    float v[12];
+    load4(xyz, p0, end, xyz_vec && (start & 3) == 0, v);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (point_valid(v[3 * j], v[3 * j + 1], v[3 * j + 2])) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          mn[a] = fminf(mn[a], v[3 * j + a]);
+          mx[a] = fmaxf(mx[a], v[3 * j + a]);
+        }
+      }
     }
   }
-  for (int d = threadIdx.x; d < kRadix; d += kStreamThreads) hist[d] = 0;
-  __syncthreads();
-  const float o[3] = {so[0], so[1], so[2]};
+  if (cur >= 0) flush_extent(mn, mx, fs, cur, red);
+}
 
+// a2: sort key per point (kKeySentinel for invalid or out-of-range rows), plus the
+// digit-0 histogram of the valid keys, the number of valid points and the largest key.
+// Block 0 also publishes every frame's origin and leaf (and the minimum to the caller
+// when the origin is computed) and the key shift.
+__global__ __launch_bounds__(kStreamThreads) void key_kernel(
+    const float* __restrict__ xyz, FramesArg fr, int have_extent, State* st, FrameState* fs,
+    uint64_t* __restrict__ keys, int* err) {
+  __shared__ ChunkSmem sm;
+  __shared__ uint32_t hist[kRadix];
+  __shared__ unsigned long long wmax[kStreamThreads / 32];
+  __shared__ uint32_t wcount[kStreamThreads / 32];
+  const int F = fr.nframes;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t warp_global = int64_t(blockIdx.x) * (kStreamThreads / 32) + warp;
-  const int64_t warp_stride = int64_t(gridDim.x) * (kStreamThreads / 32) * 32 * kStreamPoints;
+  for (int d = threadIdx.x; d < kRadix; d += kStreamThreads) hist[d] = 0;
+  const uint32_t T = build_chunk_map(fr, sm.off, sm.cstart, sm.tmp, err);
+  const uint32_t key_shift = frame_prologue(fr, have_extent != 0, st, fs, T, sm, err);
+  uint32_t c0, c1;
+  block_range(T, &c0, &c1);
+  const bool xyz_vec = (reinterpret_cast<uintptr_t>(xyz) & 15) == 0;
+  const bool key_vec = (reinterpret_cast<uintptr_t>(keys) & 15) == 0;
   uint32_t nvalid = 0;
   unsigned long long kmax = 0;
   bool range_bad = false;
-  for (int64_t w0 = warp_global * 32 * kStreamPoints; w0 < n; w0 += warp_stride) {
-    const int64_t p0 = w0 + int64_t(lane) * kStreamPoints;
+  for (uint32_t c = c0; c < c1; ++c) {
+    const int f = chunk_frame(sm.cstart, F, c);
+    const int64_t start = sm.off[f] + int64_t(c - sm.cstart[f]) * kChunk;
+    const int64_t end = min(start + kChunk, sm.off[f + 1]);
+    const int64_t p0 = start + int64_t(threadIdx.x) * kStreamPoints;
+    const bool vec = (start & 3) == 0;
     float v[12];
-    load4<kVec>(xyz, p0, n, v);
+    load4(xyz, p0, end, xyz_vec && vec, v);
+    const float o[3] = {sm.org[f][0], sm.org[f][1], sm.org[f][2]};
+    const float leaf = sm.leaf[f];
     uint64_t k[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      uint64_t key;
-      const bool ok = point_key(v[3 * j], v[3 * j + 1], v[3 * j + 2], o, leaf, &key, &range_bad);
-      k[j] = ok ? key : kSentinel;
+      uint64_t local;
+      const bool ok = point_key(v[3 * j], v[3 * j + 1], v[3 * j + 2], o, leaf, &local, &range_bad);
+      k[j] = ok ? key_compose(static_cast<uint32_t>(f), local, key_shift) : kKeySentinel;
       if (ok) {
         ++nvalid;
-        kmax = key > kmax ? key : kmax;
-        atomicAdd(&hist[key & (kRadix - 1)], 1u);
+        kmax = k[j] > kmax ? k[j] : kmax;
+        atomicAdd(&hist[k[j] & (kRadix - 1)], 1u);
       }
     }
-    if (kVec && p0 + 4 <= n) {
+    if (key_vec && vec && p0 + 4 <= end) {
       ulonglong2* dst = reinterpret_cast<ulonglong2*>(keys + p0);
       __stcg(dst, make_ulonglong2(k[0], k[1]));
       __stcg(dst + 1, make_ulonglong2(k[2], k[3]));
     } else {
 #pragma unroll
       for (int j = 0; j < 4; ++j)
-        if (p0 + j < n) keys[p0 + j] = k[j];
+        if (p0 + j < end) keys[p0 + j] = k[j];
     }
   }
-  if (__any_sync(kFull, range_bad) && lane == 0) set_error(err, 3 /* VG_ERR_RANGE */);
+  if (__any_sync(kFullMask, range_bad) && lane == 0) set_error(err, kErrRange);
 #pragma unroll
   for (int off = 16; off; off >>= 1) {
-    nvalid += __shfl_xor_sync(kFull, nvalid, off);
-    const unsigned long long other = __shfl_xor_sync(kFull, kmax, off);
+    nvalid += __shfl_xor_sync(kFullMask, nvalid, off);
+    const unsigned long long other = __shfl_xor_sync(kFullMask, kmax, off);
     kmax = other > kmax ? other : kmax;
   }
   if (lane == 0) {
@@ -143,14 +157,15 @@ __global__ __launch_bounds__(kStreamThreads) void key_kernel(
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    uint32_t c = 0;
+    uint32_t cnt = 0;
     unsigned long long m = 0;
     for (int w = 0; w < kStreamThreads / 32; ++w) {
-      c += wcount[w];
+      cnt += wcount[w];
       m = wmax[w] > m ? wmax[w] : m;
     }
-    if (c) {
-      atomicAdd(&st->nvalid, c);
+    if (cnt) {
+      atomicAdd(&st->nvalid, cnt);
+      atomicAdd(&st->nitems, cnt);
       atomicMax(&st->maxkey, m);
     }
   }
@@ -158,36 +173,27 @@ __global__ __launch_bounds__(kStreamThreads) void key_kernel(
     if (hist[d]) atomicAdd(&st->hist[0][d], hist[d]);
 }
 
-int stream_grid(int64_t n) {
-  const int64_t per_block = int64_t(kStreamThreads) * kStreamPoints;
-  const int64_t want = ceil_div(n, per_block);
-  const int64_t cap = int64_t(num_sms()) * 8;
+}  // namespace
+
+int stream_grid(const FramesArg& fr) {
+  const int64_t want = max_chunks(fr.n, fr.nframes);
+  const int64_t cap = int64_t(num_sms()) * (fr.grid_per_sm > 0 ? fr.grid_per_sm : 8);
   return static_cast<int>(want < 1 ? 1 : (want < cap ? want : cap));
 }
 
-}  // namespace
-
-cudaError_t launch_origin(const float* xyz, int64_t n, State* st, cudaStream_t stream) {
-  if (n == 0) return cudaSuccess;
-  const bool vec = (reinterpret_cast<uintptr_t>(xyz) & 15) == 0;
-  if (vec)
-    origin_kernel<true><<<stream_grid(n), kStreamThreads, 0, stream>>>(xyz, n, st);
-  else
-    origin_kernel<false><<<stream_grid(n), kStreamThreads, 0, stream>>>(xyz, n, st);
+cudaError_t launch_origin(const float* xyz, const FramesArg& fr, State* st, FrameState* fs,
+                          int* err, cudaStream_t stream) {
+  (void)st;
+  if (fr.n == 0) return cudaSuccess;
+  origin_kernel<<<stream_grid(fr), kStreamThreads, 0, stream>>>(xyz, fr, fs, err);
   return cudaGetLastError();
 }
 
-cudaError_t launch_keys(const float* xyz, int64_t n, float* origin_user, bool from_min, float leaf,
-                        State* st, uint64_t* keys, int* err, cudaStream_t stream) {
-  const bool vec = (reinterpret_cast<uintptr_t>(xyz) & 15) == 0 &&
-                   (reinterpret_cast<uintptr_t>(keys) & 15) == 0;
-  // One block even for n == 0: it publishes the origin the call used.
-  if (vec)
-    key_kernel<true><<<stream_grid(n), kStreamThreads, 0, stream>>>(xyz, n, origin_user,
-                                                                    from_min, leaf, st, keys, err);
-  else
-    key_kernel<false><<<stream_grid(n), kStreamThreads, 0, stream>>>(xyz, n, origin_user,
-                                                                     from_min, leaf, st, keys, err);
+cudaError_t launch_keys(const float* xyz, const FramesArg& fr, bool have_extent, State* st,
+                        FrameState* fs, uint64_t* keys, int* err, cudaStream_t stream) {
+  // Always at least one block: it publishes the origins and leaves the call used.
+  key_kernel<<<stream_grid(fr), kStreamThreads, 0, stream>>>(
+      xyz, fr, have_extent ? 1 : 0, st, fs, keys, err);
   return cudaGetLastError();
 }
 

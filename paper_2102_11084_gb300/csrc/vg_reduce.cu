@@ -20,7 +20,7 @@
 namespace vg {
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
+constexpr unsigned kFull = kFullMask;
 
 // A segmented-scan value: number of run heads, and the partial sums of the run that is
 // open at the end of the segment.
@@ -58,29 +58,44 @@ __device__ __forceinline__ Seg seg_shfl_up(const Seg& s, int off) {
   return r;
 }
 
+// Writes voxel v (sort key `key`, sums `a`) and its centroid.
 __device__ __forceinline__ void emit_voxel(uint32_t v, uint64_t key, const Acc& a,
-                                           const float o[3], float leaf, float inv_unit,
-                                           uint64_t* out_keys, float* out_centroids,
-                                           uint32_t* out_counts, int64_t cap, int* err) {
-  if (int64_t(v) >= cap) {
-    set_error(err, 4 /* VG_ERR_CAPACITY */);
+                                           const FrameState* fs, uint32_t key_shift,
+                                           const SegOut& out, int* err) {
+  if (int64_t(v) >= out.cap) {
+    set_error(err, kErrCapacity);
     return;
   }
+  const uint32_t f = key_frame(key, key_shift);
+  const uint64_t local = key_local(key, key_shift);
+  const float o[3] = {fs[f].origin[0], fs[f].origin[1], fs[f].origin[2]};
+  const float leaf = fs[f].leaf;
   float c[3];
-  acc_centroid(key, a, o, leaf, inv_unit, c);
-  out_keys[v] = key;
-  out_counts[v] = a.n;
-  out_centroids[3 * size_t(v)] = c[0];
-  out_centroids[3 * size_t(v) + 1] = c[1];
-  out_centroids[3 * size_t(v) + 2] = c[2];
+  acc_centroid(local, a, o, leaf, quant_inv_unit(leaf), c);
+  out.keys[v] = local;
+  out.counts[v] = a.n;
+  out.centroids[3 * size_t(v)] = c[0];
+  out.centroids[3 * size_t(v) + 1] = c[1];
+  out.centroids[3 * size_t(v) + 2] = c[2];
+  if (out.sums) {
+    out.sums[3 * size_t(v)] = a.s[0];
+    out.sums[3 * size_t(v) + 1] = a.s[1];
+    out.sums[3 * size_t(v) + 2] = a.s[2];
+  }
 }
 
-__global__ __launch_bounds__(kSegThreads) void segreduce_kernel(
-    State* st, const uint64_t* __restrict__ keys0, const uint32_t* __restrict__ idx0,
+// Output offsets of frames (f_prev, f_new] start at voxel v.
+__device__ __forceinline__ void mark_frames(int64_t* fo, uint32_t f_prev, uint32_t f_new,
+                                            uint32_t v) {
+  if (!fo) return;
+  for (uint32_t f = f_prev + 1; f <= f_new; ++f) fo[f] = v;
+}
+
+__global__ __launch_bounds__(kSegThreads, 2) void segreduce_kernel(
+    State* st, const FrameState* __restrict__ fs, int nframes,
+    const uint64_t* __restrict__ keys0, const uint32_t* __restrict__ idx0,
     const uint64_t* __restrict__ keys1, const uint32_t* __restrict__ idx1,
-    const float* __restrict__ xyz, float leaf, SegStatus* lb, uint64_t* __restrict__ out_keys,
-    float* __restrict__ out_centroids, uint32_t* __restrict__ out_counts, int64_t cap,
-    int64_t* out_num_voxels, int32_t* __restrict__ out_p2v, uint32_t spin_limit, int* err) {
+    const float* __restrict__ xyz, SegStatus* lb, SegOut out, uint32_t spin_limit, int* err) {
   __shared__ uint64_t skeys[kSegTile];
   __shared__ uint32_t sidx[kSegTile];
   __shared__ Seg wtot[kSegThreads / 32];
@@ -92,15 +107,14 @@ __global__ __launch_bounds__(kSegThreads) void segreduce_kernel(
   if (t == 0) s_tile = static_cast<int>(atomicAdd(&st->tile_ctr[kMaxPasses], 1u));
   __syncthreads();
   const int tile = s_tile;
-  const int64_t nvalid = st->nvalid;
+  const int64_t nitems = st->nitems;
   const int64_t base = int64_t(tile) * kSegTile;
-  if (base >= nvalid) return;
+  if (base >= nitems) return;
+  const uint32_t key_shift = st->key_shift;
   const int passes = max(1, sort_passes(st->maxkey));
   const uint64_t* K = (passes & 1) ? keys1 : keys0;
   const uint32_t* I = (passes & 1) ? idx1 : idx0;
-  const int cnt = static_cast<int>(nvalid - base < kSegTile ? nvalid - base : kSegTile);
-  const float o[3] = {st->origin[0], st->origin[1], st->origin[2]};
-  const float inv_unit = quant_inv_unit(leaf);
+  const int cnt = static_cast<int>(nitems - base < kSegTile ? nitems - base : kSegTile);
 
   for (int i = t; i < cnt; i += kSegThreads) {
     skeys[i] = __ldcs(K + base + i);
@@ -126,8 +140,12 @@ __global__ __launch_bounds__(kSegThreads) void segreduce_kernel(
       const uint64_t pk = j == 0 ? prev0 : k[j - 1];
       const bool head = (base + li == 0) || (k[j] != pk);
       headmask |= uint32_t(head) << j;
+      const uint32_t f = key_frame(k[j], key_shift);
+      const float o[3] = {fs[f].origin[0], fs[f].origin[1], fs[f].origin[2]};
+      const float leaf = fs[f].leaf;
       const float* p = xyz + 3 * size_t(pi[j]);
-      const Acc a = point_acc(k[j], __ldg(p), __ldg(p + 1), __ldg(p + 2), o, leaf, inv_unit);
+      const Acc a = point_acc(key_local(k[j], key_shift), __ldg(p), __ldg(p + 1), __ldg(p + 2),
+                              o, leaf, quant_inv_unit(leaf));
       q[j][0] = static_cast<int>(a.s[0]);
       q[j][1] = static_cast<int>(a.s[1]);
       q[j][2] = static_cast<int>(a.s[2]);
@@ -178,7 +196,7 @@ __global__ __launch_bounds__(kSegThreads) void segreduce_kernel(
         const uint32_t f = ld_acquire(&other->flag);
         if (f == 0) {
           if (++spins > spin_limit) {
-            set_error(err, 6 /* VG_ERR_TIMEOUT */);
+            set_error(err, kErrTimeout);
             break;
           }
           if (spins > 64) __nanosleep(64);
@@ -224,7 +242,8 @@ __global__ __launch_bounds__(kSegThreads) void segreduce_kernel(
     if ((headmask >> j) & 1u) {
       if (gi > 0) {
         const uint64_t pk = j == 0 ? prev0 : k[j - 1];
-        emit_voxel(H - 1, pk, run, o, leaf, inv_unit, out_keys, out_centroids, out_counts, cap, err);
+        emit_voxel(H - 1, pk, run, fs, key_shift, out, err);
+        mark_frames(out.frame_offsets, key_frame(pk, key_shift), key_frame(k[j], key_shift), H);
       }
       H += 1;
       run = acc_zero();
@@ -233,27 +252,26 @@ __global__ __launch_bounds__(kSegThreads) void segreduce_kernel(
     run.s[0] += q[j][0];
     run.s[1] += q[j][1];
     run.s[2] += q[j][2];
-    if (out_p2v) out_p2v[pi[j]] = static_cast<int32_t>(H - 1);
-    if (gi == nvalid - 1) {
-      emit_voxel(H - 1, k[j], run, o, leaf, inv_unit, out_keys, out_centroids, out_counts, cap, err);
-      *out_num_voxels = H;
+    if (out.p2v) out.p2v[pi[j]] = static_cast<int32_t>(H - 1);
+    if (gi == nitems - 1) {
+      emit_voxel(H - 1, k[j], run, fs, key_shift, out, err);
+      *out.num_voxels = H;
+      mark_frames(out.frame_offsets, key_frame(k[j], key_shift), uint32_t(nframes), H);
     }
   }
 }
 
 }  // namespace
 
-cudaError_t launch_segreduce(State* st, const uint64_t* keys0, const uint32_t* idx0,
-                             const uint64_t* keys1, const uint32_t* idx1, const float* xyz,
-                             float leaf, SegStatus* lb, int64_t n_max, uint64_t* out_keys,
-                             float* out_centroids, uint32_t* out_counts, int64_t cap,
-                             int64_t* out_num_voxels, int32_t* out_p2v, uint32_t spin_limit,
-                             int* err, cudaStream_t stream) {
+cudaError_t launch_segreduce(State* st, const FrameState* fs, int nframes,
+                             const uint64_t* keys0, const uint32_t* idx0, const uint64_t* keys1,
+                             const uint32_t* idx1, const float* xyz, SegStatus* lb,
+                             int64_t n_max, const SegOut& out, uint32_t spin_limit, int* err,
+                             cudaStream_t stream) {
   if (n_max == 0) return cudaSuccess;
   const int tiles = static_cast<int>(ceil_div(n_max, kSegTile));
-  segreduce_kernel<<<tiles, kSegThreads, 0, stream>>>(st, keys0, idx0, keys1, idx1, xyz, leaf, lb,
-                                                      out_keys, out_centroids, out_counts, cap,
-                                                      out_num_voxels, out_p2v, spin_limit, err);
+  segreduce_kernel<<<tiles, kSegThreads, 0, stream>>>(st, fs, nframes, keys0, idx0, keys1, idx1,
+                                                      xyz, lb, out, spin_limit, err);
   return cudaGetLastError();
 }
 

@@ -22,7 +22,7 @@ namespace vg {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr uint64_t kSentinel = ~0ull;
+constexpr uint64_t kSentinel = kKeySentinel;
 
 // Exclusive scans of two values over a 256-thread block; also returns the totals.
 __device__ __forceinline__ void block_excl_scan2(uint32_t a, uint32_t b, uint32_t* ea,
@@ -63,8 +63,8 @@ __device__ __forceinline__ void block_excl_scan2(uint32_t a, uint32_t b, uint32_
 __global__ __launch_bounds__(kSortThreads, 2) void onesweep_kernel(
     const uint64_t* __restrict__ keys_in, const uint32_t* __restrict__ idx_in,
     uint64_t* __restrict__ keys_out, uint32_t* __restrict__ idx_out, State* st,
-    uint32_t* lb_cur, uint32_t* lb_next, int pass, int64_t n_host, uint32_t spin_limit,
-    int* err) {
+    uint32_t* lb_cur, uint32_t* lb_next, int pass, int64_t n_host, int compact_input,
+    uint32_t spin_limit, int* err) {
   __shared__ uint32_t warp_hist[kSortThreads / 32][kRadix];
   __shared__ uint32_t digit_start[kRadix];
   __shared__ uint32_t gbase[kRadix];
@@ -84,7 +84,10 @@ __global__ __launch_bounds__(kSortThreads, 2) void onesweep_kernel(
 
   const int passes = max(1, sort_passes(st->maxkey));
   if (pass >= passes) return;
-  const int64_t n_items = pass == 0 ? n_host : int64_t(st->nvalid);
+  // Pass 0 of the sort path reads all n raw keys (invalid rows hold the sentinel and are
+  // dropped); every other pass, and pass 0 of compacted input, reads st->nitems entries.
+  const bool raw = pass == 0 && !compact_input;
+  const int64_t n_items = raw ? n_host : int64_t(st->nitems);
   const int64_t tile_base = int64_t(tile) * kSortTile;
   if (tile_base >= n_items) return;
   const int shift = pass * kRadixBits;
@@ -98,9 +101,9 @@ __global__ __launch_bounds__(kSortThreads, 2) void onesweep_kernel(
     const int64_t i = tile_base + warp * (32 * kSortItems) + j * 32 + lane;
     const bool in = i < n_items;
     key[j] = in ? __ldcs(keys_in + i) : kSentinel;
-    const bool ok = in && (pass > 0 || key[j] != kSentinel);
+    const bool ok = in && (!raw || key[j] != kSentinel);
     vmask |= uint32_t(ok) << j;
-    pay[j] = (pass == 0) ? static_cast<uint32_t>(i) : (in ? __ldcs(idx_in + i) : 0u);
+    pay[j] = raw ? static_cast<uint32_t>(i) : (in ? __ldcs(idx_in + i) : 0u);
   }
   for (int d = lane; d < kRadix; d += 32) warp_hist[warp][d] = 0;
   next_hist[t] = 0;
@@ -157,7 +160,7 @@ __global__ __launch_bounds__(kSortThreads, 2) void onesweep_kernel(
       const uint32_t f = s & ~kValueMask;
       if (f == 0) {
         if (++spins > spin_limit) {
-          set_error(err, 6 /* VG_ERR_TIMEOUT */);
+          set_error(err, kErrTimeout);
           break;
         }
         if (spins > 64) __nanosleep(64);
@@ -207,11 +210,24 @@ __global__ __launch_bounds__(kSortThreads, 2) void onesweep_kernel(
     atomicAdd(&st->hist[pass + 1][t], next_hist[t]);
 }
 
+// Test kernel: one chained-scan wait of tile `tile` on status words nobody publishes; it
+// must give up after `limit` polls and record kErrTimeout.
+__global__ void debug_wait_kernel(const uint32_t* status, int tile, uint32_t limit, int* err) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) (void)lookback_u32(status, 1, tile, limit, err);
+}
+
 }  // namespace
+
+cudaError_t launch_debug_wait(const uint32_t* status, int tile, uint32_t limit, int* err,
+                              cudaStream_t stream) {
+  debug_wait_kernel<<<1, 32, 0, stream>>>(status, tile, limit, err);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_sort_pass(State* st, uint64_t* keys0, uint32_t* idx0, uint64_t* keys1,
                              uint32_t* idx1, uint32_t* lb_a, uint32_t* lb_b, int64_t n_max,
-                             int pass, uint32_t spin_limit, int* err, cudaStream_t stream) {
+                             int pass, bool compact_input, uint32_t spin_limit, int* err,
+                             cudaStream_t stream) {
   if (n_max == 0) return cudaSuccess;
   const int tiles = static_cast<int>(ceil_div(n_max, kSortTile));
   const bool even = (pass & 1) == 0;
@@ -222,8 +238,10 @@ cudaError_t launch_sort_pass(State* st, uint64_t* keys0, uint32_t* idx0, uint64_
   uint32_t* iout = even ? idx1 : idx0;
   uint32_t* cur = even ? lb_a : lb_b;
   uint32_t* nxt = even ? lb_b : lb_a;
-  onesweep_kernel<<<tiles, kSortThreads, 0, stream>>>(kin, pass == 0 ? nullptr : iin, kout, iout,
-                                                      st, cur, nxt, pass, n_max, spin_limit, err);
+  const bool raw = pass == 0 && !compact_input;
+  onesweep_kernel<<<tiles, kSortThreads, 0, stream>>>(kin, raw ? nullptr : iin, kout, iout, st,
+                                                      cur, nxt, pass, n_max,
+                                                      compact_input ? 1 : 0, spin_limit, err);
   return cudaGetLastError();
 }
 

@@ -23,8 +23,13 @@ _LIB = None
 ORIGIN_FROM_MIN = 1
 METHOD_AUTO = 0
 METHOD_SORT = 16
-_METHODS = {"auto": METHOD_AUTO, "sort": METHOD_SORT}
+METHOD_HASH = 32
+USE_GRAPH = 64
+GRID_SHIFT = 8
+_METHODS = {"auto": METHOD_AUTO, "sort": METHOD_SORT, "hash": METHOD_HASH}
 MAX_POINTS = (1 << 30) - 1
+MAX_FRAMES = 1024
+MAX_LEVELS = 8
 
 
 class Status(IntEnum):
@@ -58,6 +63,38 @@ _SIGS = {
                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                ctypes.c_void_p], ctypes.c_int),
     "vg_downsample_noalloc_scratch_bytes": ([], ctypes.c_size_t),
+    "vg_set_stage_events": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
+    "vg_debug_wait_timeout": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p],
+                              ctypes.c_int),
+    "vg_batch_workspace_bytes": ([ctypes.c_int64, ctypes.c_int, ctypes.c_int], ctypes.c_size_t),
+    "vg_downsample_frames": ([ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int,
+                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                              ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int,
+                              ctypes.c_void_p], ctypes.c_int),
+    "vg_plan_create": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_int], ctypes.c_int),
+    "vg_plan_destroy": ([ctypes.c_void_p], ctypes.c_int),
+    "vg_plan_configure": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+    "vg_plan_get": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+                    ctypes.c_int),
+    "vg_downsample_batch": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                             ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p],
+                            ctypes.c_int),
+    "vg_plan_tune": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                      ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                      ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                      ctypes.c_void_p], ctypes.c_int),
+    "vg_pyramid_workspace_bytes": ([ctypes.c_int64, ctypes.c_int, ctypes.c_int], ctypes.c_size_t),
+    "vg_pyramid": ([ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_float, ctypes.c_int,
+                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                    ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p], ctypes.c_int),
+    "vg_downsample_backward": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+                               ctypes.c_int),
 }
 
 
@@ -232,6 +269,214 @@ def downsample_noalloc(xyz: torch.Tensor, leaf: float, origin: Optional[torch.Te
     _check(int(err.item()), "vg_downsample_noalloc (device)")
     v = int(nv.item())
     return Decimation(keys[:v], cents[:v], counts[:v], org, p2v[:n] if point_to_voxel else None)
+
+
+# ---- batched frames (step a8) -------------------------------------------------------
+class Frames(NamedTuple):
+    """Outputs of a batched call: frame f's voxels are rows offsets[f]:offsets[f+1]."""
+    keys: torch.Tensor            # int64 view of uint64 per-frame keys [V_total]
+    centroids: torch.Tensor       # float32 [V_total, 3]
+    counts: torch.Tensor          # int32 [V_total]
+    offsets: list                 # host list of F+1 row offsets
+    origins: torch.Tensor         # float32 [F, 3]
+    point_to_voxel: Optional[torch.Tensor]  # int32 [N_total], global rows
+
+    def frame(self, f: int) -> Decimation:
+        a, b = self.offsets[f], self.offsets[f + 1]
+        return Decimation(self.keys[a:b], self.centroids[a:b], self.counts[a:b], self.origins[f],
+                          None)
+
+
+def _frame_inputs(frames, leaves, origins, device):
+    """Concatenate a list of [N_f,3] clouds (or take (xyz, offsets) as given)."""
+    if isinstance(frames, (list, tuple)):
+        sizes = [int(f.shape[0]) for f in frames]
+        xyz = torch.cat([f.to(device=device, dtype=torch.float32) for f in frames]).contiguous() \
+            if frames else torch.zeros((0, 3), dtype=torch.float32, device=device)
+        offs = [0]
+        for n in sizes:
+            offs.append(offs[-1] + n)
+    else:
+        xyz, offs = frames
+        offs = [int(v) for v in offs]
+    F = len(offs) - 1
+    off_t = torch.tensor(offs, dtype=torch.int64, device=device)
+    lv = torch.as_tensor(leaves, dtype=torch.float32).reshape(F).to(device)
+    og = (torch.zeros((F, 3), dtype=torch.float32, device=device) if origins is None else
+          torch.as_tensor(origins, dtype=torch.float32).reshape(F, 3).to(device).contiguous())
+    return _cuda_cloud(xyz), off_t, F, lv, og
+
+
+def downsample_frames(frames, leaves, origins=None, *, method="sort", point_to_voxel=False,
+                      grid_per_sm: int = 0, stream: Optional[torch.cuda.Stream] = None) -> Frames:
+    """vg_downsample_frames: every frame decimated as it would be alone, in one call.
+
+    ``frames`` is a list of float32 [N_f, 3] CUDA tensors or a tuple (xyz [N,3], offsets).
+    ``origins`` None means each frame's minimum.  Synchronises once to read the offsets.
+    """
+    dev = (frames[0].device if isinstance(frames, (list, tuple)) and frames else
+           (frames[0].device if not isinstance(frames, (list, tuple)) else torch.device("cuda")))
+    xyz, off_t, F, lv, og = _frame_inputs(frames, leaves, origins, dev)
+    n = xyz.shape[0]
+    flags = method_flag(method) | (ORIGIN_FROM_MIN if origins is None else 0) | \
+        (int(grid_per_sm) << GRID_SHIFT)
+    cap = max(n, 1)
+    keys = torch.empty(cap, dtype=torch.int64, device=dev)
+    cents = torch.empty((cap, 3), dtype=torch.float32, device=dev)
+    counts = torch.empty(cap, dtype=torch.int32, device=dev)
+    out_off = torch.zeros(F + 1, dtype=torch.int64, device=dev)
+    err = torch.zeros(1, dtype=torch.int32, device=dev)
+    p2v = torch.empty(cap, dtype=torch.int32, device=dev) if point_to_voxel else None
+    ws = torch.empty(max(int(lib().vg_batch_workspace_bytes(n, F, flags)), 256), dtype=torch.uint8,
+                     device=dev)
+    st = lib().vg_downsample_frames(
+        _ptr(xyz), n, _ptr(off_t), F, _ptr(og), _ptr(lv), _ptr(keys), _ptr(cents), _ptr(counts), n,
+        _ptr(out_off), _ptr(p2v), _ptr(err), _ptr(ws), ws.numel(), flags, _stream_ptr(stream))
+    _check(st, "vg_downsample_frames")
+    (stream or torch.cuda.current_stream()).synchronize()
+    _check(int(err.item()), "vg_downsample_frames (device)")
+    offs = out_off.cpu().tolist()
+    v = offs[-1]
+    return Frames(keys[:v], cents[:v], counts[:v], offs, og, p2v[:n] if point_to_voxel else None)
+
+
+class Plan:
+    """A batch plan (vg_plan): owned workspace, tuned method/grid, CUDA-graph replay."""
+
+    def __init__(self, max_frames: int, max_points: int, method="sort"):
+        h = ctypes.c_void_p()
+        _check(lib().vg_plan_create(ctypes.byref(h), int(max_frames), int(max_points),
+                                    method_flag(method)), "vg_plan_create")
+        self._h = h
+        self.max_frames = int(max_frames)
+        self.max_points = int(max_points)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().vg_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def configure(self, method, grid_per_sm: int = 0):
+        _check(lib().vg_plan_configure(self._h, method_flag(method), int(grid_per_sm)),
+               "vg_plan_configure")
+
+    def get(self):
+        m, g, w = ctypes.c_int(), ctypes.c_int(), ctypes.c_size_t()
+        _check(lib().vg_plan_get(self._h, ctypes.byref(m), ctypes.byref(g), ctypes.byref(w)),
+               "vg_plan_get")
+        return {"method": {METHOD_SORT: "sort", METHOD_HASH: "hash"}[m.value],
+                "grid_per_sm": g.value, "workspace_bytes": w.value}
+
+    def run(self, xyz, frame_offsets, n_frames, origins, leaves, out_keys, out_centroids,
+            out_counts, out_frame_offsets, out_error, *, origin_from_min=True, graph=True,
+            point_to_voxel=None, stream: Optional[torch.cuda.Stream] = None):
+        """vg_downsample_batch into preallocated device tensors (no host sync)."""
+        flags = (ORIGIN_FROM_MIN if origin_from_min else 0) | (USE_GRAPH if graph else 0)
+        st = lib().vg_downsample_batch(
+            self._h, _ptr(xyz), xyz.shape[0], _ptr(frame_offsets), int(n_frames), _ptr(origins),
+            _ptr(leaves), _ptr(out_keys), _ptr(out_centroids), _ptr(out_counts),
+            out_keys.shape[0], _ptr(out_frame_offsets), _ptr(point_to_voxel), _ptr(out_error),
+            flags, _stream_ptr(stream))
+        _check(st, "vg_downsample_batch")
+
+    def tune(self, xyz, frame_offsets, n_frames, origins, leaves, out_keys, out_centroids,
+             out_counts, out_frame_offsets, out_error, *, origin_from_min=True, reps=5,
+             stream: Optional[torch.cuda.Stream] = None):
+        """vg_plan_tune: time sort/hash x grids {4,8,16}; keeps the fastest."""
+        ms = (ctypes.c_float * 6)()
+        flags = ORIGIN_FROM_MIN if origin_from_min else 0
+        st = lib().vg_plan_tune(
+            self._h, _ptr(xyz), xyz.shape[0], _ptr(frame_offsets), int(n_frames), _ptr(origins),
+            _ptr(leaves), _ptr(out_keys), _ptr(out_centroids), _ptr(out_counts),
+            out_keys.shape[0], _ptr(out_frame_offsets), _ptr(out_error), flags, int(reps),
+            _stream_ptr(stream), ms)
+        _check(st, "vg_plan_tune")
+        names = [f"{m}@{g}" for m in ("sort", "hash") for g in (4, 8, 16)]
+        return dict(zip(names, list(ms)))
+
+
+# ---- pyramid (step a6) -----------------------------------------------------------------
+def pyramid(xyz: torch.Tensor, leaf: float, levels: int, origin: Optional[torch.Tensor] = None,
+            *, point_to_voxel: bool = False, stream: Optional[torch.cuda.Stream] = None) -> list:
+    """vg_pyramid: level 0 = decimation at ``leaf``, level k+1 = merge of level k by key>>3.
+
+    Returns a list of ``levels`` Decimation tuples (point_to_voxel only on level 0).
+    """
+    xyz = _cuda_cloud(xyz)
+    n = xyz.shape[0]
+    dev = xyz.device
+    org = (torch.zeros(3, dtype=torch.float32, device=dev) if origin is None else
+           torch.as_tensor(origin, dtype=torch.float32, device=dev).reshape(3).contiguous())
+    cap = max(n * levels, 1)
+    keys = torch.empty(cap, dtype=torch.int64, device=dev)
+    cents = torch.empty((cap, 3), dtype=torch.float32, device=dev)
+    counts = torch.empty(cap, dtype=torch.int32, device=dev)
+    loff = torch.zeros(levels + 1, dtype=torch.int64, device=dev)
+    err = torch.zeros(1, dtype=torch.int32, device=dev)
+    p2v = torch.empty(max(n, 1), dtype=torch.int32, device=dev) if point_to_voxel else None
+    flags = ORIGIN_FROM_MIN if origin is None else 0
+    ws = torch.empty(max(int(lib().vg_pyramid_workspace_bytes(n, levels, flags)), 256),
+                     dtype=torch.uint8, device=dev)
+    st = lib().vg_pyramid(_ptr(xyz), n, _ptr(org), ctypes.c_float(leaf), int(levels), _ptr(keys),
+                          _ptr(cents), _ptr(counts), cap, _ptr(loff), _ptr(p2v), _ptr(err),
+                          _ptr(ws), ws.numel(), flags, _stream_ptr(stream))
+    _check(st, "vg_pyramid")
+    (stream or torch.cuda.current_stream()).synchronize()
+    _check(int(err.item()), "vg_pyramid (device)")
+    o = loff.cpu().tolist()
+    out = []
+    for k in range(levels):
+        a, b = o[k], o[k + 1]
+        out.append(Decimation(keys[a:b], cents[a:b], counts[a:b], org,
+                              p2v[:n] if (point_to_voxel and k == 0) else None))
+    return out
+
+
+# ---- backward (step a7) ----------------------------------------------------------------
+def backward(grad_centroids: torch.Tensor, counts: torch.Tensor, point_to_voxel: torch.Tensor,
+             *, stream: Optional[torch.cuda.Stream] = None, check: bool = True) -> torch.Tensor:
+    """vg_downsample_backward: grad_xyz[i] = grad_c[v(i)] / count[v(i)], 0 if invalid."""
+    g = grad_centroids.contiguous().to(torch.float32)
+    v = g.shape[0]
+    n = point_to_voxel.shape[0]
+    out = torch.empty((n, 3), dtype=torch.float32, device=g.device)
+    err = torch.zeros(1, dtype=torch.int32, device=g.device)
+    st = lib().vg_downsample_backward(_ptr(g), _ptr(counts.contiguous()),
+                                      _ptr(point_to_voxel.contiguous()), n, v, _ptr(out), _ptr(err),
+                                      _stream_ptr(stream))
+    _check(st, "vg_downsample_backward")
+    if check:
+        (stream or torch.cuda.current_stream()).synchronize()
+        _check(int(err.item()), "vg_downsample_backward (device)")
+    return out
+
+
+class VoxelDownsample(torch.autograd.Function):
+    """centroids = VoxelDownsample.apply(xyz, leaf, origin): differentiable in xyz.
+
+    Forward is vg_downsample (with point_to_voxel); backward is vg_downsample_backward.
+    Keys and counts are returned as non-differentiable outputs.
+    """
+
+    @staticmethod
+    def forward(ctx, xyz, leaf, origin=None):
+        r = downsample(xyz.detach(), float(leaf), origin, point_to_voxel=True)
+        ctx.save_for_backward(r.counts, r.point_to_voxel)
+        ctx.mark_non_differentiable(r.keys, r.counts)
+        return r.centroids, r.keys, r.counts
+
+    @staticmethod
+    def backward(ctx, grad_c, grad_keys=None, grad_counts=None):
+        counts, p2v = ctx.saved_tensors
+        if grad_c is None:
+            return None, None, None
+        return backward(grad_c, counts, p2v), None, None
 
 
 def set_spin_limit(limit: int) -> None:
