@@ -45,7 +45,13 @@ def test_autograd_loss_gradient_vs_finite_differences():
     analytic = oracle.backward(oracle.loss_grad_centroids(ref.centroids, targets), ref.counts,
                                ref.point_to_voxel)
     valid = ref.point_to_voxel >= 0
-    assert np.allclose(g[valid], analytic[valid], rtol=1e-3, atol=1e-12)
+    # Each entry is 2 (c - t) / (3 V n): a GPU centroid within the 1e-5 m parity tolerance
+    # of the FP64 one, plus the binary32 rounding of the targets (< 1e-6 m here), bounds
+    # the difference by 2 * 1.1e-5 / (3 V n) -- an absolute bound per point.
+    n_of = np.zeros(len(xyz_np))
+    n_of[valid] = ref.counts[ref.point_to_voxel[valid]].astype(np.float64)
+    bound = 2 * 1.1e-5 / (3 * V * np.maximum(n_of, 1))
+    assert (np.abs(g - analytic)[valid] <= bound[valid, None]).all()
     assert (g[~valid] == 0).all()
     # central differences of the FP64 oracle loss on points >= 1e-3 leaf from faces
     x64 = xyz_np.astype(np.float64)
@@ -61,4 +67,4 @@ def test_autograd_loss_gradient_vs_finite_differences():
             xm[i, a] -= h
             fd = (oracle.centroid_loss(xp, ref.point_to_voxel, V, targets) -
                   oracle.centroid_loss(xm, ref.point_to_voxel, V, targets)) / (2 * h)
-            assert abs(fd - g[i, a]) <= 1e-3 * abs(fd) + 1e-12, (i, a, fd, g[i, a])
+            assert abs(fd - g[i, a]) <= bound[i] + 1e-6 * abs(fd), (i, a, fd, g[i, a])
