@@ -287,9 +287,15 @@ class Frames(NamedTuple):
                           None)
 
 
+def _is_cat_form(frames) -> bool:
+    """True for the (xyz [N,3], offsets [F+1]) form, False for a list of clouds."""
+    return (isinstance(frames, tuple) and len(frames) == 2 and isinstance(frames[0], torch.Tensor)
+            and not (isinstance(frames[1], torch.Tensor) and frames[1].dim() == 2))
+
+
 def _frame_inputs(frames, leaves, origins, device):
     """Concatenate a list of [N_f,3] clouds (or take (xyz, offsets) as given)."""
-    if isinstance(frames, (list, tuple)):
+    if not _is_cat_form(frames):
         sizes = [int(f.shape[0]) for f in frames]
         xyz = torch.cat([f.to(device=device, dtype=torch.float32) for f in frames]).contiguous() \
             if frames else torch.zeros((0, 3), dtype=torch.float32, device=device)
@@ -314,8 +320,7 @@ def downsample_frames(frames, leaves, origins=None, *, method="sort", point_to_v
     ``frames`` is a list of float32 [N_f, 3] CUDA tensors or a tuple (xyz [N,3], offsets).
     ``origins`` None means each frame's minimum.  Synchronises once to read the offsets.
     """
-    dev = (frames[0].device if isinstance(frames, (list, tuple)) and frames else
-           (frames[0].device if not isinstance(frames, (list, tuple)) else torch.device("cuda")))
+    dev = frames[0].device if len(frames) else torch.device("cuda")
     xyz, off_t, F, lv, og = _frame_inputs(frames, leaves, origins, dev)
     n = xyz.shape[0]
     flags = method_flag(method) | (ORIGIN_FROM_MIN if origins is None else 0) | \

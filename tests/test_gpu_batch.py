@@ -22,7 +22,8 @@ def small_batch(seed=0, frames=9):
         keep = np.sort(rng.choice(full.shape[0], n, replace=False))
         out.append(np.ascontiguousarray(full[keep]))
         leaves.append(float(rng.choice([0.02, 0.05, 0.1])))
-    out[5][:] = np.nan  # an all-invalid frame
+    if frames > 5:
+        out[5][:] = np.nan  # an all-invalid frame
     return out, np.asarray(leaves, np.float32)
 
 
