@@ -45,6 +45,10 @@ def parse():
     p.add_argument("--n", type=int, default=N_POINTS)
     p.add_argument("--leaf", type=float, default=LEAF)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-extra", action="store_true",
+                   help="skip the other configurations (single frame, batch, pyramid, "
+                        "backward, leaf 0.1 m, serving)")
+    p.add_argument("--serve-seconds", type=float, default=10.0)
     return p.parse_args()
 
 
@@ -140,6 +144,114 @@ def profiled_traffic(kernel: str, units: float):
 
 
 # --------------------------------------------------------------------------------------
+def _time_ms(fn, reps, warmup=3, stream=None):
+    """Mean device ms of fn() over `reps` calls (CUDA events on the launching stream)."""
+    import torch
+    s = stream or torch.cuda.current_stream()
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(s)
+    for _ in range(reps):
+        fn()
+    b.record(s)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def extra_measurements(args, dev):
+    """The other configurations of the workload set, each timed on the device."""
+    import torch
+    from paper_2102_11084_gb300 import serve, synth, vg
+    out = {}
+    stream = torch.cuda.current_stream(dev)
+
+    # 640x480 RGB-D frame, leaf 0.05 m: one plain call (sort and hash) and a 1-frame graph
+    frame = synth.rgbd_frame(640, 480, seed=0)
+    x = torch.from_numpy(frame).to(dev)
+    n = x.shape[0]
+    r = {}
+    for m in ("sort", "hash"):
+        buf = vg.alloc_buffers(n, dev, flags=vg.method_flag(m))
+        ms = _time_ms(lambda: vg.downsample_into(x, 0.05, buf, origin_from_min=True, method=m), 200)
+        r[m] = {"ms": ms, "points_per_s": n / (ms / 1e3)}
+    r["voxels"] = int(buf.num_voxels.item())
+    out["rgbd_640x480_leaf0.05"] = r
+
+    # 64 frames of uneven size: 64 plain calls vs one batched call (plan, tuned, graph)
+    spec = synth.batch_frames(64, seed=1)
+    frames = [torch.from_numpy(f).to(dev) for f in spec.frames]
+    sizes = [f.shape[0] for f in frames]
+    total = int(sum(sizes))
+    bufs = [vg.alloc_buffers(k, dev) for k in sizes]
+
+    def per_frame():
+        for f, b, lf in zip(frames, bufs, spec.leaves):
+            vg.downsample_into(f, float(lf), b, origin_from_min=True)
+    ms_per_frame = _time_ms(per_frame, 10)
+    xyz = torch.cat(frames).contiguous()
+    offs = torch.tensor([0] + list(np.cumsum(sizes)), dtype=torch.int64, device=dev)
+    F = len(frames)
+    bb = dict(xyz=xyz, frame_offsets=offs, n_frames=F,
+              origins=torch.zeros((F, 3), dtype=torch.float32, device=dev),
+              leaves=torch.from_numpy(spec.leaves).to(dev),
+              out_keys=torch.empty(total, dtype=torch.int64, device=dev),
+              out_centroids=torch.empty((total, 3), dtype=torch.float32, device=dev),
+              out_counts=torch.empty(total, dtype=torch.int32, device=dev),
+              out_frame_offsets=torch.zeros(F + 1, dtype=torch.int64, device=dev),
+              out_error=torch.zeros(1, dtype=torch.int32, device=dev))
+    side = torch.cuda.Stream(dev)
+    plan = vg.Plan(F, total)
+    with torch.cuda.stream(side):
+        tuned = plan.tune(**bb, reps=5, stream=side)
+        ms_batched = _time_ms(lambda: plan.run(**bb, stream=side), 20, stream=side)
+    chosen = plan.get()
+    plan.close()
+    out["batch_64_frames"] = {
+        "points": total, "per_frame_calls_ms": ms_per_frame, "batched_graph_ms": ms_batched,
+        "speedup": ms_per_frame / ms_batched, "batched_points_per_s": total / (ms_batched / 1e3),
+        "tuned": {"method": chosen["method"], "grid_per_sm": chosen["grid_per_sm"],
+                  "candidates_ms": tuned}}
+    del frames, bufs, xyz, bb
+
+    # 1280x720 frame: 4-level pyramid from 0.01 m, and the leaf sweep
+    hd = torch.from_numpy(synth.rgbd_frame(1280, 720, seed=0, cx=639.5, cy=359.5)).to(dev)
+    out["pyramid_1280x720_4_levels_ms"] = _time_ms(lambda: vg.pyramid(hd, 0.01, 4), 20)
+    sweep = {}
+    hb = vg.alloc_buffers(hd.shape[0], dev)
+    for lf in (0.01, 0.02, 0.05, 0.1):
+        ms = _time_ms(lambda: vg.downsample_into(hd, lf, hb, origin_from_min=True), 50)
+        sweep[str(lf)] = {"ms": ms, "points_per_s": hd.shape[0] / (ms / 1e3),
+                          "voxels": int(hb.num_voxels.item())}
+    out["rgbd_1280x720_sweep"] = sweep
+
+    # backward of the mean squared centroid loss, 307,200 points, leaf 0.05 m
+    res = vg.downsample(x, 0.05, point_to_voxel=True)
+    g = torch.randn_like(res.centroids)
+    out["backward_640x480_ms"] = _time_ms(
+        lambda: vg.backward(g, res.counts, res.point_to_voxel, check=False), 200)
+
+    # serving: 16 sensor streams x 30 Hz Poisson arrivals of 640x480 frames, leaf 0.05 m
+    pool = [synth.rgbd_frame(640, 480, seed=3000 + k) for k in range(64)]
+    trace = synth.serving_trace(16, 30.0, args.serve_seconds, len(pool), seed=5)
+    srv = serve.Server(max_points=16 * 307_200, max_frames=16, n_slots=2)
+    results, wall = serve.replay(srv, trace, pool, 0.05)
+    srv.close()
+    st = serve.latency_stats(results)
+    st["points_per_s"] = len(results) * 307_200 / wall
+    st["wall_s"] = wall
+    st["batches"] = srv.batches
+    sat_trace = [r._replace(arrival_s=0.0) for r in trace[:2000]]
+    srv = serve.Server(max_points=16 * 307_200, max_frames=16, n_slots=2)
+    sat, sat_wall = serve.replay(srv, sat_trace, pool, 0.05, realtime=False)
+    srv.close()
+    st["saturation_points_per_s"] = len(sat) * 307_200 / sat_wall
+    st["saturation_p99_ms"] = serve.latency_stats(sat)["p99_ms"]
+    out["serving_16x30Hz_640x480"] = st
+    return out
+
+
 def run_reference(args, rank, world):
     """Reference arm: the CPU oracle on bounded samples of the same workload."""
     if rank != 0:
@@ -309,6 +421,15 @@ def run_vg(args, rank, world, local):
             dist.destroy_process_group()
         return
     cpu = None if args.no_cpu_baseline else cpu_baseline(xyz_np, args.leaf)
+    extra = {}
+    if not args.no_extra:
+        # the same cloud at leaf 0.1 m
+        ms01 = _time_ms(lambda: vg.downsample_into(xyz, 0.1, buf, origin_from_min=True), 10)
+        extra["fused_map_50M_leaf0.1"] = {"ms": ms01, "points_per_s": n / (ms01 / 1e3),
+                                          "voxels": int(buf.num_voxels.item())}
+        del buf
+        torch.cuda.empty_cache()
+        extra.update(extra_measurements(args, dev))
     launches_per_step = 1 + 1 + 8 + 1
     out = {
         "metric": "points/s", "value": world * n / (ms / 1000), "unit": "points/s",
@@ -332,6 +453,7 @@ def run_vg(args, rank, world, local):
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk.summary(),
+        "extra": extra,
     }
     print(json.dumps(out), flush=True)
     if world > 1:

@@ -1,0 +1,264 @@
+"""Continuous-batching request loop for voxel-grid decimation of many sensor streams.
+
+Requests (one cloud each, from any number of sensor streams) are queued on the host.
+A scheduler thread owns `n_slots` device slots; each slot has its own CUDA stream,
+persistent device buffers (input cloud, frame table, outputs, workspace) and pinned host
+staging, all allocated once.  Whenever a slot is free the scheduler admits the oldest
+waiting requests into it -- as many as fit the slot's point budget and frame limit
+(memory admission) -- copies them host-to-device, launches one batched call
+(vg_downsample_frames) on the slot's stream and moves on; requests that arrive while
+other batches are on the GPU join the next free slot, so batches overlap on the device.
+A completion pass copies each finished batch's rows back and resolves every request's
+future with its own voxels and its latency (arrival -> result on the host).
+
+Every frame of a batch is decimated exactly as it would be alone (same keys, counts
+and centroid bits), so a result does not depend on what it was batched with.
+"""
+from __future__ import annotations
+
+import collections
+import ctypes
+import threading
+import time
+from concurrent.futures import Future
+from typing import NamedTuple, Optional
+
+import numpy as np
+import torch
+
+from . import vg
+
+
+class Result(NamedTuple):
+    keys: np.ndarray        # uint64 [V]
+    centroids: np.ndarray   # float32 [V, 3]
+    counts: np.ndarray      # uint32 [V]
+    origin: np.ndarray      # float32 [3]
+    latency_s: float
+    batch_frames: int       # how many requests shared the launch
+
+
+class _Request(NamedTuple):
+    stream_id: int
+    xyz: np.ndarray
+    leaf: float
+    arrival: float
+    future: Future
+
+
+class _Slot:
+    def __init__(self, device, max_points: int, max_frames: int, method: str):
+        self.stream = torch.cuda.Stream(device=device)
+        self.max_points = max_points
+        self.max_frames = max_frames
+        self.flags = vg.method_flag(method) | vg.ORIGIN_FROM_MIN
+        cap = max(max_points, 1)
+        d = device
+        self.xyz = torch.empty((cap, 3), dtype=torch.float32, device=d)
+        self.offsets = torch.zeros(max_frames + 1, dtype=torch.int64, device=d)
+        self.leaves = torch.ones(max_frames, dtype=torch.float32, device=d)
+        self.origins = torch.zeros((max_frames, 3), dtype=torch.float32, device=d)
+        self.keys = torch.empty(cap, dtype=torch.int64, device=d)
+        self.centroids = torch.empty((cap, 3), dtype=torch.float32, device=d)
+        self.counts = torch.empty(cap, dtype=torch.int32, device=d)
+        self.out_offsets = torch.zeros(max_frames + 1, dtype=torch.int64, device=d)
+        self.error = torch.zeros(1, dtype=torch.int32, device=d)
+        nbytes = int(vg.lib().vg_batch_workspace_bytes(cap, max_frames, self.flags))
+        self.workspace = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=d)
+        self.h_xyz = torch.empty((cap, 3), dtype=torch.float32).pin_memory()
+        self.h_off_in = torch.zeros(max_frames + 1, dtype=torch.int64).pin_memory()
+        self.h_leaf_in = torch.ones(max_frames, dtype=torch.float32).pin_memory()
+        self.h_offsets = torch.zeros(max_frames + 1, dtype=torch.int64).pin_memory()
+        self.h_origins = torch.zeros((max_frames, 3), dtype=torch.float32).pin_memory()
+        self.h_keys = torch.empty(cap, dtype=torch.int64).pin_memory()
+        self.h_centroids = torch.empty((cap, 3), dtype=torch.float32).pin_memory()
+        self.h_counts = torch.empty(cap, dtype=torch.int32).pin_memory()
+        self.h_error = torch.zeros(1, dtype=torch.int32).pin_memory()
+        self.done = torch.cuda.Event()
+        self.batch: list = []
+        self.busy = False
+
+    def device_bytes(self) -> int:
+        ts = [self.xyz, self.offsets, self.leaves, self.origins, self.keys, self.centroids,
+              self.counts, self.out_offsets, self.error, self.workspace]
+        return sum(t.numel() * t.element_size() for t in ts)
+
+    def launch(self, batch: list):
+        """H2D of the admitted clouds, one batched decimation, D2H of the small tables."""
+        self.batch = batch
+        self.busy = True
+        sizes = [r.xyz.shape[0] for r in batch]
+        offs = np.zeros(len(batch) + 1, np.int64)
+        np.cumsum(sizes, out=offs[1:])
+        n = int(offs[-1])
+        hx = self.h_xyz.numpy()
+        for r, a in zip(batch, offs[:-1]):
+            hx[a:a + r.xyz.shape[0]] = r.xyz
+        F = len(batch)
+        self.h_off_in.numpy()[:F + 1] = offs
+        self.h_leaf_in.numpy()[:F] = [r.leaf for r in batch]
+        with torch.cuda.stream(self.stream):
+            self.xyz[:n].copy_(self.h_xyz[:n], non_blocking=True)
+            self.offsets[:F + 1].copy_(self.h_off_in[:F + 1], non_blocking=True)
+            self.leaves[:F].copy_(self.h_leaf_in[:F], non_blocking=True)
+            st = vg.lib().vg_downsample_frames(
+                vg._ptr(self.xyz), n, vg._ptr(self.offsets), F, vg._ptr(self.origins),
+                vg._ptr(self.leaves), vg._ptr(self.keys), vg._ptr(self.centroids),
+                vg._ptr(self.counts), self.keys.shape[0], vg._ptr(self.out_offsets), None,
+                vg._ptr(self.error), vg._ptr(self.workspace), self.workspace.numel(), self.flags,
+                ctypes.c_void_p(self.stream.cuda_stream))
+            if st != 0:
+                raise vg.VGError(st, "vg_downsample_frames")
+            self.h_offsets[:F + 1].copy_(self.out_offsets[:F + 1], non_blocking=True)
+            self.h_origins[:F].copy_(self.origins[:F], non_blocking=True)
+            self.h_error.copy_(self.error, non_blocking=True)
+            self.done.record(self.stream)
+        self.n_frames = F
+
+    def finish(self):
+        """Copies the rows back and splits them per request (after `done` fired)."""
+        F = self.n_frames
+        err = int(self.h_error[0])
+        offs = self.h_offsets[:F + 1].numpy().copy()
+        v = int(offs[-1])
+        with torch.cuda.stream(self.stream):
+            self.h_keys[:v].copy_(self.keys[:v], non_blocking=True)
+            self.h_centroids[:v].copy_(self.centroids[:v], non_blocking=True)
+            self.h_counts[:v].copy_(self.counts[:v], non_blocking=True)
+        self.stream.synchronize()
+        keys = self.h_keys.numpy()[:v].view(np.uint64)
+        cents = self.h_centroids.numpy()[:v]
+        counts = self.h_counts.numpy()[:v].view(np.uint32)
+        origins = self.h_origins.numpy()[:F]
+        now = time.perf_counter()
+        for f, r in enumerate(self.batch):
+            if err:
+                r.future.set_exception(vg.VGError(err, "served batch"))
+                continue
+            a, b = int(offs[f]), int(offs[f + 1])
+            r.future.set_result(Result(keys[a:b].copy(), cents[a:b].copy(), counts[a:b].copy(),
+                                       origins[f].copy(), now - r.arrival, F))
+        self.batch = []
+        self.busy = False
+
+
+def admit(queue: collections.deque, max_points: int, max_frames: int) -> list:
+    """Memory admission: pops the oldest requests while the batch stays within the slot's
+    point budget and frame limit (FIFO: a request that does not fit waits for the next
+    slot rather than being overtaken)."""
+    batch, pts = [], 0
+    while queue and len(batch) < max_frames:
+        n = queue[0].xyz.shape[0]
+        if pts + n > max_points:
+            break
+        batch.append(queue.popleft())
+        pts += n
+    return batch
+
+
+class Server:
+    """Continuous-batching decimation server on one GPU.
+
+    max_points   point budget of one batch (per slot); a request larger than it is refused.
+    max_frames   most requests in one batch.
+    n_slots      device slots (>= 2 lets batches overlap on the GPU).
+    mem_budget   device bytes the slots may hold; fewer slots are made if needed.
+    """
+
+    def __init__(self, *, max_points: int = 8 * 307_200, max_frames: int = 16, n_slots: int = 2,
+                 method: str = "sort", device="cuda", mem_budget: Optional[int] = None):
+        dev = torch.device(device)
+        self.slots = []
+        used = 0
+        for _ in range(max(1, n_slots)):
+            s = _Slot(dev, max_points, max_frames, method)
+            if mem_budget is not None and self.slots and used + s.device_bytes() > mem_budget:
+                del s
+                break
+            used += s.device_bytes()
+            self.slots.append(s)
+        self.device_bytes = used
+        self.max_points = max_points
+        self.max_frames = max_frames
+        self._q = collections.deque()
+        self._cv = threading.Condition()
+        self._stop = False
+        self.batches = 0
+        self.points = 0
+        self._thread = threading.Thread(target=self._loop, name="vg-serve", daemon=True)
+        self._thread.start()
+
+    def submit(self, stream_id: int, xyz: np.ndarray, leaf: float,
+               arrival: Optional[float] = None) -> Future:
+        xyz = np.ascontiguousarray(xyz, np.float32).reshape(-1, 3)
+        fut: Future = Future()
+        if xyz.shape[0] > self.max_points:
+            fut.set_exception(ValueError("cloud larger than a batch's point budget"))
+            return fut
+        req = _Request(stream_id, xyz, float(leaf), time.perf_counter() if arrival is None else arrival,
+                       fut)
+        with self._cv:
+            self._q.append(req)
+            self._cv.notify()
+        return fut
+
+    def close(self):
+        with self._cv:
+            self._stop = True
+            self._cv.notify()
+        self._thread.join()
+
+    def _admit(self) -> list:
+        return admit(self._q, self.max_points, self.max_frames)
+
+    def _loop(self):
+        torch.cuda.set_device(self.slots[0].xyz.device)
+        while True:
+            progressed = False
+            for s in self.slots:
+                if s.busy and s.done.query():
+                    s.finish()
+                    progressed = True
+            with self._cv:
+                if self._stop and not self._q and not any(s.busy for s in self.slots):
+                    return
+                free = [s for s in self.slots if not s.busy]
+                batch = self._admit() if (free and self._q) else []
+                if not batch and not progressed and not any(s.busy for s in self.slots):
+                    self._cv.wait(timeout=0.05)
+                    continue
+            if batch:
+                try:
+                    free[0].launch(batch)
+                    self.batches += 1
+                    self.points += sum(r.xyz.shape[0] for r in batch)
+                except Exception as e:  # fail this batch's requests, keep serving
+                    for r in batch:
+                        if not r.future.done():
+                            r.future.set_exception(e)
+                    free[0].busy = False
+            elif not progressed:
+                time.sleep(0.0002)
+
+
+def replay(server: Server, trace, pool, leaf: float, *, realtime: bool = True):
+    """Feeds a request trace (synth.serving_trace) into the server; returns the results."""
+    t0 = time.perf_counter()
+    futs = []
+    for r in trace:
+        if realtime:
+            delay = t0 + r.arrival_s - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+        futs.append((r, server.submit(r.stream, pool[r.frame], leaf)))
+    out = [(r, f.result()) for r, f in futs]
+    return out, time.perf_counter() - t0
+
+
+def latency_stats(results) -> dict:
+    lat = np.array([res.latency_s for _, res in results]) * 1000.0
+    pts = sum(int(res.counts.sum()) for _, res in results)
+    return {"requests": len(results), "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "max_ms": float(lat.max()),
+            "valid_points": pts,
+            "mean_batch_frames": float(np.mean([res.batch_frames for _, res in results]))}

@@ -1,0 +1,58 @@
+"""The continuous-batching server: each request's result equals its solo decimation,
+whatever it was batched with; batches really mix requests and overlap on the device."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2102_11084_gb300 import serve, synth, vg
+
+pytestmark = pytest.mark.gpu
+
+
+def test_results_same_alone_and_in_the_mix():
+    pool = [synth.rgbd_frame(320, 240, seed=900 + k) for k in range(6)]
+    leaf = 0.05
+    solo = []
+    for x in pool:
+        r = vg.downsample(torch.from_numpy(x).cuda(), leaf)
+        solo.append((r.keys.cpu().numpy().view(np.uint64), r.centroids.cpu().numpy(),
+                     r.counts.cpu().numpy().view(np.uint32)))
+    srv = serve.Server(max_points=4 * 320 * 240, max_frames=8, n_slots=2)
+    rng = np.random.Generator(np.random.PCG64(3))
+    futs = []
+    for i in range(90):
+        k = int(rng.integers(len(pool)))
+        futs.append((k, srv.submit(i % 16, pool[k], leaf)))
+    results = [(k, f.result(timeout=120)) for k, f in futs]
+    srv.close()
+    assert max(res.batch_frames for _, res in results) > 1   # requests were batched together
+    for k, res in results:
+        keys, cents, counts = solo[k]
+        assert np.array_equal(res.keys, keys) and np.array_equal(res.counts, counts)
+        assert np.array_equal(res.centroids.view(np.int32), cents.view(np.int32))
+    ref = oracle.downsample(pool[0], leaf)
+    first = next(res for k, res in results if k == 0)
+    assert np.array_equal(first.keys, ref.keys)
+    assert np.abs(first.centroids.astype(np.float64) - ref.centroids).max() <= 1e-5
+
+
+def test_oversize_request_is_refused_and_server_keeps_serving():
+    srv = serve.Server(max_points=1000, max_frames=4, n_slots=2)
+    big = srv.submit(0, np.zeros((1001, 3), np.float32), 0.1)
+    with pytest.raises(ValueError):
+        big.result(timeout=10)
+    ok = srv.submit(0, synth.random_cloud(500, 1), 0.1).result(timeout=60)
+    srv.close()
+    assert ok.keys.shape[0] > 0
+
+
+def test_realtime_trace_latency():
+    pool = [synth.rgbd_frame(640, 480, seed=2000 + k) for k in range(4)]
+    trace = synth.serving_trace(16, 30.0, 1.0, len(pool), seed=5)
+    srv = serve.Server(max_points=16 * 307_200, max_frames=16, n_slots=2)
+    results, wall = serve.replay(srv, trace, pool, 0.05)
+    srv.close()
+    st = serve.latency_stats(results)
+    assert st["requests"] == len(trace)
+    assert st["p99_ms"] < 1000.0
