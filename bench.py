@@ -311,7 +311,8 @@ def run_vg(args, rank, world, local):
     stream = torch.cuda.current_stream(dev)
 
     # stage events (profiling hook of the C ABI): one set per timed step
-    n_stages = 11  # sort path: origin, keys, 8 radix passes, segmented reduction
+    # sort path: extent/origin, keys, 8 wide passes, 4 narrow passes, 2 reductions
+    n_stages = 16
     import ctypes
 
     def call():
@@ -359,26 +360,29 @@ def run_vg(args, rank, world, local):
     nvalid = int(np.isfinite(xyz_np).all(axis=1).sum())
 
     # per-stage device times (ms, mean over steps)
-    stage_names = ["origin", "keys"] + [f"sort_pass{p}" for p in range(8)] + ["segreduce"]
+    stage_names = (["origin", "keys"] + [f"sort_pass{p}" for p in range(8)] +
+                   [f"sort_pass{p}_narrow" for p in range(4)] + ["segreduce", "segreduce_narrow"])
     stage_ms = np.zeros(n_stages)
     for s in ev_sets:
         for i in range(n_stages):
             stage_ms[i] += s[i].elapsed_time(s[i + 1])
     stage_ms /= args.steps
     passes = int(np.ceil(max(1, int(buf.keys[V - 1].item()).bit_length()) / 8)) if V else 1
-    # algorithmic bytes per launch of each kernel
+    narrow = passes <= 4  # the key kernel picks 32-bit keys when the largest key fits
+    # algorithmic bytes per launch of each kernel (narrow: 4 B key + 8 B packed offsets)
     algo = {
         "origin": 12.0 * n,
-        "keys": 12.0 * n + 8.0 * n,
+        "keys": 12.0 * n + 12.0 * n,
         "sort_pass": 24.0 * nvalid,
-        "segreduce": (8 + 4 + 12) * nvalid + 16.0 * V,
+        "segreduce": (12.0 if narrow else 24.0) * nvalid + 16.0 * V,
     }
-    sort_ms = stage_ms[2:2 + passes]
+    sort_ms = stage_ms[10:10 + passes] if narrow else stage_ms[2:2 + passes]
+    seg_ms = stage_ms[15] if narrow else stage_ms[14]
     kern = {
         "origin": (stage_ms[0], algo["origin"], 1),
         "keys": (stage_ms[1], algo["keys"], 1),
         "sort_pass": (float(sort_ms.mean()), algo["sort_pass"], passes),
-        "segreduce": (stage_ms[10], algo["segreduce"], 1),
+        "segreduce": (seg_ms, algo["segreduce"], 1),
     }
     dom = max(kern, key=lambda k: kern[k][0] * kern[k][2])
     peaks, peak_src = measured_peaks()
@@ -430,7 +434,7 @@ def run_vg(args, rank, world, local):
         del buf
         torch.cuda.empty_cache()
         extra.update(extra_measurements(args, dev))
-    launches_per_step = 1 + 1 + 8 + 1
+    launches_per_step = 1 + 1 + 8 + 4 + 2
     out = {
         "metric": "points/s", "value": world * n / (ms / 1000), "unit": "points/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -448,6 +452,7 @@ def run_vg(args, rank, world, local):
                           "definition": "12 B per input point + 16 B per output voxel"},
         "stages_ms": {nm: float(v) for nm, v in zip(stage_names, stage_ms)},
         "sort_passes": passes,
+        "layout": "narrow (32-bit keys, packed offsets)" if narrow else "wide (64-bit keys, index)",
         "cpu_baseline": cpu,
         "e2e": {"value": world * n / e2e_s, "unit": "points/s", "h2d_bytes_per_step": 12 * n,
                 "d2h_bytes_per_step": d2h},

@@ -17,7 +17,7 @@ void** g_events = nullptr;
 int g_max_events = 0;
 bool g_events_paused = false;
 int g_sms[64] = {0};
-constexpr int kMaxStages = 16;
+constexpr int kMaxStages = 20;
 }  // namespace
 
 uint32_t spin_limit() {
@@ -90,10 +90,13 @@ vg_status run_frames(const float* xyz, const FramesArg& fr, bool from_min, const
   if (!workspace || workspace_bytes < need) return VG_ERR_WORKSPACE;
   char* ws = static_cast<char*>(workspace);
   const uint32_t spins = spin_limit();
-  const bool have_extent = from_min || F > 1;
   int stage = 0;
 
   if (method == VG_METHOD_SORT) {
+    // The narrow layout (no gather) needs the extents up front and no point_to_voxel.
+    FramesArg frn = fr;
+    frn.allow_narrow = out.p2v == nullptr;
+    const bool have_extent = from_min || F > 1 || frn.allow_narrow;
     const SortLayout L = sort_layout(n, F);
     State* st = reinterpret_cast<State*>(ws + L.state);
     FrameState* fs = reinterpret_cast<FrameState*>(ws + L.frames);
@@ -104,6 +107,11 @@ vg_status run_frames(const float* xyz, const FramesArg& fr, bool from_min, const
     uint32_t* lb_a = reinterpret_cast<uint32_t*>(ws + L.lb_a);
     uint32_t* lb_b = reinterpret_cast<uint32_t*>(ws + L.lb_b);
     SegStatus* seg_lb = reinterpret_cast<SegStatus*>(ws + L.seg_lb);
+    const int64_t nn = n < 1 ? 1 : n;
+    uint32_t* k32_0 = reinterpret_cast<uint32_t*>(ws + L.keys0);
+    uint32_t* k32_1 = k32_0 + nn;
+    uint64_t* pay_0 = reinterpret_cast<uint64_t*>(ws + L.keys1);
+    uint64_t* pay_1 = reinterpret_cast<uint64_t*>(ws + L.idx0);
     int* err = out_error ? reinterpret_cast<int*>(out_error) : &st->error;
 
     cudaError_t e = cudaMemsetAsync(ws, 0, L.zero_bytes, stream);
@@ -114,23 +122,36 @@ vg_status run_frames(const float* xyz, const FramesArg& fr, bool from_min, const
     if (e == cudaSuccess && out.p2v && n > 0)
       e = cudaMemsetAsync(out.p2v, 0xff, size_t(n) * sizeof(int32_t), stream);
     mark(stage++, stream);
-    if (e == cudaSuccess && have_extent) e = launch_origin(xyz, fr, st, fs, err, stream);
+    if (e == cudaSuccess && have_extent) e = launch_origin(xyz, frn, st, fs, err, stream);
     mark(stage++, stream);
-    if (e == cudaSuccess) e = launch_keys(xyz, fr, have_extent, st, fs, keys0, err, stream);
+    if (e == cudaSuccess)
+      e = launch_keys_any(xyz, frn, have_extent, st, fs, keys0, k32_0, pay_0, err, stream);
     mark(stage++, stream);
+    // Both layouts are launched; the kernels of the one the key kernel did not choose
+    // return at once (the choice depends on the largest key, known only on the device).
     for (int p = 0; p < kMaxPasses && e == cudaSuccess; ++p) {
       e = launch_sort_pass(st, keys0, idx0, keys1, idx1, lb_a, lb_b, n, p, false, spins, err,
                            stream);
+      mark(stage++, stream);
+    }
+    for (int p = 0; p < kNarrowPasses && e == cudaSuccess; ++p) {
+      e = launch_sort_pass_narrow(st, k32_0, pay_0, k32_1, pay_1, lb_a, lb_b, n, p, spins, err,
+                                  stream);
       mark(stage++, stream);
     }
     if (e == cudaSuccess)
       e = launch_segreduce(st, fs, F, keys0, idx0, keys1, idx1, xyz, seg_lb, n, out, spins, err,
                            stream);
     mark(stage++, stream);
+    if (e == cudaSuccess)
+      e = launch_segreduce_narrow(st, fs, F, k32_0, pay_0, k32_1, pay_1, seg_lb, n, out, spins,
+                                  err, stream);
+    mark(stage++, stream);
     return cuda_status(e);
   }
 
   // hash path
+  const bool have_extent = from_min || F > 1;
   const HashLayout L = hash_layout(n, F);
   State* st = reinterpret_cast<State*>(ws + L.state);
   FrameState* fs = reinterpret_cast<FrameState*>(ws + L.frames);

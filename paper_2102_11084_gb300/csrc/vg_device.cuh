@@ -126,9 +126,26 @@ __device__ __forceinline__ float voxel_corner(uint32_t i, float o, float leaf) {
   return __fadd_rn(o, __fmul_rn(__uint2float_rn(i), leaf));
 }
 
-// Quantised offset of coordinate p from its voxel corner c.
+// Quantised offset of coordinate p from its voxel corner c, clamped to
+// [-2^19, 3*2^19): half a voxel of slack on either side of [0, leaf), so that it packs in
+// 21 bits.  An offset leaves that range only when the leaf is within a few binary32 ulps
+// of the coordinates, where the clamp moves a centroid by less than those ulps.
+constexpr int kQMin = -(1 << 19);
+constexpr int kQMax = (3 << 19) - 1;
 __device__ __forceinline__ int quant_offset(float p, float c, float inv_unit) {
-  return __float2int_rn(__fmul_rn(__fsub_rn(p, c), inv_unit));
+  const int q = __float2int_rn(__fmul_rn(__fsub_rn(p, c), inv_unit));
+  return q < kQMin ? kQMin : (q > kQMax ? kQMax : q);
+}
+
+// Three quantised offsets packed in one 64-bit word (21 bits each, biased by 2^19);
+// bit 63 set marks an invalid point.
+constexpr uint64_t kPayloadInvalid = 1ull << 63;
+__device__ __forceinline__ uint64_t pack_offsets(int qx, int qy, int qz) {
+  return uint64_t(uint32_t(qx - kQMin)) | (uint64_t(uint32_t(qy - kQMin)) << 21) |
+         (uint64_t(uint32_t(qz - kQMin)) << 42);
+}
+__device__ __forceinline__ int unpack_offset(uint64_t w, int axis) {
+  return int(uint32_t(w >> (21 * axis)) & 0x1fffffu) + kQMin;
 }
 
 // Offsets of point (x,y,z) from the corner of voxel `local` (a per-frame Morton key).

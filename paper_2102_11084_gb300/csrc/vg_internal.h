@@ -62,6 +62,7 @@ struct alignas(256) State {
   uint32_t key_shift;         // bits of the per-frame key field (frame id above it)
   uint32_t nframes;
   uint32_t nchunks;           // chunks of the frame decomposition
+  uint32_t narrow;            // 1: 32-bit sort keys + packed-offset payload (no gather)
   int32_t error;              // internal error word when the caller passes none
   uint32_t tile_ctr[kMaxPasses + 8];
   uint32_t hist[kMaxPasses][kRadix];
@@ -91,6 +92,7 @@ struct FramesArg {
   const float* leaves;     // device [F] per-frame leaves, or nullptr: `leaf` for all
   float leaf;
   int grid_per_sm;         // blocks per SM of the streaming kernels (0 = default 8)
+  int allow_narrow;        // the key kernel may pick the narrow layout (no point_to_voxel)
 };
 
 // Grid of the streaming kernels: one block per chunk, at most grid_per_sm blocks per SM.
@@ -102,7 +104,9 @@ constexpr size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 // Upper bound of the chunk count of n points in F frames.
 constexpr int64_t max_chunks(int64_t n, int frames) { return ceil_div(n, kChunk) + frames; }
 
-// Workspace layout of the sort path for n points in `frames` frames.
+// Workspace layout of the sort path for n points in `frames` frames.  The narrow layout
+// (32-bit keys, 64-bit packed offsets) aliases the same bytes: keys32 ping-pong in keys0,
+// payload ping-pong in keys1 and in idx0..idx1.
 struct SortLayout {
   size_t state, frames, keys0, keys1, idx0, idx1, lb_a, lb_b, seg_lb, total;
   size_t zero_bytes;  // bytes from `state` that must be zero at call start
@@ -155,6 +159,12 @@ cudaError_t launch_sort_pass(State* st, uint64_t* keys0, uint32_t* idx0, uint64_
                              uint32_t* idx1, uint32_t* lb_a, uint32_t* lb_b, int64_t n_max,
                              int pass, bool compact_input, uint32_t spin_limit, int* err,
                              cudaStream_t stream);
+// a3, narrow layout: 32-bit keys with the packed offsets as payload (returns at once
+// unless the key kernel chose the narrow layout).
+constexpr int kNarrowPasses = 4;
+cudaError_t launch_sort_pass_narrow(State* st, uint32_t* k0, uint64_t* p0, uint32_t* k1,
+                                    uint64_t* p1, uint32_t* lb_a, uint32_t* lb_b, int64_t n_max,
+                                    int pass, uint32_t spin_limit, int* err, cudaStream_t stream);
 // a4 + a5: reduce-by-key of the sorted table into key-ordered voxels.
 struct SegOut {
   uint64_t* keys;
@@ -171,6 +181,17 @@ cudaError_t launch_segreduce(State* st, const FrameState* fs, int nframes,
                              const uint32_t* idx1, const float* xyz, SegStatus* lb,
                              int64_t n_max, const SegOut& out, uint32_t spin_limit, int* err,
                              cudaStream_t stream);
+// a4 + a5, narrow layout (returns at once unless the narrow layout was chosen).
+cudaError_t launch_segreduce_narrow(State* st, const FrameState* fs, int nframes,
+                                    const uint32_t* k0, const uint64_t* p0, const uint32_t* k1,
+                                    const uint64_t* p1, SegStatus* lb, int64_t n_max,
+                                    const SegOut& out, uint32_t spin_limit, int* err,
+                                    cudaStream_t stream);
+// a2, narrow-capable key kernel: writes either 64-bit keys to keys64 (wide) or 32-bit keys
+// and packed offsets (narrow, when allowed and the sort key fits in 32 bits).
+cudaError_t launch_keys_any(const float* xyz, const FramesArg& fr, bool have_extent, State* st,
+                            FrameState* fs, uint64_t* keys64, uint32_t* keys32,
+                            uint64_t* payload, int* err, cudaStream_t stream);
 
 // ---- hash path ----
 struct alignas(32) HashAcc {

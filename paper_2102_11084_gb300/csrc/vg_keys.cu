@@ -95,7 +95,8 @@ __global__ __launch_bounds__(kStreamThreads) void origin_kernel(const float* __r
 // when the origin is computed) and the key shift.
 __global__ __launch_bounds__(kStreamThreads) void key_kernel(
     const float* __restrict__ xyz, FramesArg fr, int have_extent, State* st, FrameState* fs,
-    uint64_t* __restrict__ keys, int* err) {
+    uint64_t* __restrict__ keys, uint32_t* __restrict__ keys32, uint64_t* __restrict__ payload,
+    int* err) {
   __shared__ ChunkSmem sm;
   __shared__ uint32_t hist[kRadix];
   __shared__ unsigned long long wmax[kStreamThreads / 32];
@@ -104,7 +105,9 @@ __global__ __launch_bounds__(kStreamThreads) void key_kernel(
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int d = threadIdx.x; d < kRadix; d += kStreamThreads) hist[d] = 0;
   const uint32_t T = build_chunk_map(fr, sm.off, sm.cstart, sm.tmp, err);
-  const uint32_t key_shift = frame_prologue(fr, have_extent != 0, st, fs, T, sm, err);
+  bool narrow = false;
+  const uint32_t key_shift = frame_prologue(fr, have_extent != 0, st, fs, T, sm, err, &narrow);
+  narrow = narrow && keys32 && payload;
   uint32_t c0, c1;
   block_range(T, &c0, &c1);
   const bool xyz_vec = (reinterpret_cast<uintptr_t>(xyz) & 15) == 0;
@@ -123,18 +126,40 @@ __global__ __launch_bounds__(kStreamThreads) void key_kernel(
     const float o[3] = {sm.org[f][0], sm.org[f][1], sm.org[f][2]};
     const float leaf = sm.leaf[f];
     uint64_t k[4];
+    uint64_t pay[4];
+    const float inv_unit = quant_inv_unit(leaf);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       uint64_t local;
       const bool ok = point_key(v[3 * j], v[3 * j + 1], v[3 * j + 2], o, leaf, &local, &range_bad);
       k[j] = ok ? key_compose(static_cast<uint32_t>(f), local, key_shift) : kKeySentinel;
+      pay[j] = kPayloadInvalid;
       if (ok) {
         ++nvalid;
         kmax = k[j] > kmax ? k[j] : kmax;
         atomicAdd(&hist[k[j] & (kRadix - 1)], 1u);
+        if (narrow) {
+          const Acc a = point_acc(local, v[3 * j], v[3 * j + 1], v[3 * j + 2], o, leaf, inv_unit);
+          pay[j] = pack_offsets(int(a.s[0]), int(a.s[1]), int(a.s[2]));
+        }
       }
     }
-    if (key_vec && vec && p0 + 4 <= end) {
+    if (narrow) {
+      if (key_vec && vec && p0 + 4 <= end) {
+        __stcg(reinterpret_cast<uint4*>(keys32 + p0),
+               make_uint4(uint32_t(k[0]), uint32_t(k[1]), uint32_t(k[2]), uint32_t(k[3])));
+        ulonglong2* dst = reinterpret_cast<ulonglong2*>(payload + p0);
+        __stcg(dst, make_ulonglong2(pay[0], pay[1]));
+        __stcg(dst + 1, make_ulonglong2(pay[2], pay[3]));
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (p0 + j < end) {
+            keys32[p0 + j] = uint32_t(k[j]);
+            payload[p0 + j] = pay[j];
+          }
+      }
+    } else if (key_vec && vec && p0 + 4 <= end) {
       ulonglong2* dst = reinterpret_cast<ulonglong2*>(keys + p0);
       __stcg(dst, make_ulonglong2(k[0], k[1]));
       __stcg(dst + 1, make_ulonglong2(k[2], k[3]));
@@ -191,9 +216,15 @@ cudaError_t launch_origin(const float* xyz, const FramesArg& fr, State* st, Fram
 
 cudaError_t launch_keys(const float* xyz, const FramesArg& fr, bool have_extent, State* st,
                         FrameState* fs, uint64_t* keys, int* err, cudaStream_t stream) {
+  return launch_keys_any(xyz, fr, have_extent, st, fs, keys, nullptr, nullptr, err, stream);
+}
+
+cudaError_t launch_keys_any(const float* xyz, const FramesArg& fr, bool have_extent, State* st,
+                            FrameState* fs, uint64_t* keys64, uint32_t* keys32,
+                            uint64_t* payload, int* err, cudaStream_t stream) {
   // Always at least one block: it publishes the origins and leaves the call used.
   key_kernel<<<stream_grid(fr), kStreamThreads, 0, stream>>>(
-      xyz, fr, have_extent ? 1 : 0, st, fs, keys, err);
+      xyz, fr, have_extent ? 1 : 0, st, fs, keys64, keys32, payload, err);
   return cudaGetLastError();
 }
 

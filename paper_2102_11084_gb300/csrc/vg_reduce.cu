@@ -14,6 +14,8 @@
 //      number of voxels before it and the partial of the run still open at its start;
 //   4. emits each run at its last entry: key, count and centroid at the run's rank.
 // Integer sums make the result independent of tile size and of the order of the points.
+#include <type_traits>
+
 #include "vg_device.cuh"
 #include "vg_internal.h"
 
@@ -91,13 +93,19 @@ __device__ __forceinline__ void mark_frames(int64_t* fo, uint32_t f_prev, uint32
   for (uint32_t f = f_prev + 1; f <= f_new; ++f) fo[f] = v;
 }
 
+// kNarrow: 32-bit keys with the packed offsets as payload (no gather); otherwise 64-bit
+// keys with the point index as payload, whose coordinates are gathered.  A launch whose
+// layout was not chosen returns before taking a tile ticket.
+template <bool kNarrow>
 __global__ __launch_bounds__(kSegThreads, 2) void segreduce_kernel(
-    State* st, const FrameState* __restrict__ fs, int nframes,
-    const uint64_t* __restrict__ keys0, const uint32_t* __restrict__ idx0,
-    const uint64_t* __restrict__ keys1, const uint32_t* __restrict__ idx1,
-    const float* __restrict__ xyz, SegStatus* lb, SegOut out, uint32_t spin_limit, int* err) {
+    State* st, const FrameState* __restrict__ fs, int nframes, const void* keys0_,
+    const void* pay0_, const void* keys1_, const void* pay1_, const float* __restrict__ xyz,
+    SegStatus* lb, SegOut out, uint32_t spin_limit, int* err) {
+  using KeyT = typename std::conditional<kNarrow, uint32_t, uint64_t>::type;
+  using PayT = typename std::conditional<kNarrow, uint64_t, uint32_t>::type;
   __shared__ uint64_t skeys[kSegTile];
-  __shared__ uint32_t sidx[kSegTile];
+  __shared__ PayT sidx[kSegTile];
+  if ((st->narrow != 0) != kNarrow) return;
   __shared__ Seg wtot[kSegThreads / 32];
   __shared__ Seg s_tile_excl;
   __shared__ uint64_t s_prev_key;
@@ -112,20 +120,21 @@ __global__ __launch_bounds__(kSegThreads, 2) void segreduce_kernel(
   if (base >= nitems) return;
   const uint32_t key_shift = st->key_shift;
   const int passes = max(1, sort_passes(st->maxkey));
-  const uint64_t* K = (passes & 1) ? keys1 : keys0;
-  const uint32_t* I = (passes & 1) ? idx1 : idx0;
+  const KeyT* K = static_cast<const KeyT*>((passes & 1) ? keys1_ : keys0_);
+  const PayT* I = static_cast<const PayT*>((passes & 1) ? pay1_ : pay0_);
   const int cnt = static_cast<int>(nitems - base < kSegTile ? nitems - base : kSegTile);
 
   for (int i = t; i < cnt; i += kSegThreads) {
     skeys[i] = __ldcs(K + base + i);
     sidx[i] = __ldcs(I + base + i);
   }
-  if (t == 0) s_prev_key = base > 0 ? K[base - 1] : 0ull;
+  if (t == 0) s_prev_key = base > 0 ? uint64_t(K[base - 1]) : 0ull;
   __syncthreads();
 
   // ---- this thread's entries (blocked: t*8 .. t*8+7) ----
   uint64_t k[kSegItems];
   uint32_t pi[kSegItems];
+  (void)xyz;
   int q[kSegItems][3];
   uint32_t headmask = 0;
   const int first = t * kSegItems;
@@ -136,16 +145,26 @@ __global__ __launch_bounds__(kSegThreads, 2) void segreduce_kernel(
     const int li = first + j;
     if (li < cnt) {
       k[j] = skeys[li];
-      pi[j] = sidx[li];
       const uint64_t pk = j == 0 ? prev0 : k[j - 1];
       const bool head = (base + li == 0) || (k[j] != pk);
       headmask |= uint32_t(head) << j;
-      const uint32_t f = key_frame(k[j], key_shift);
-      const float o[3] = {fs[f].origin[0], fs[f].origin[1], fs[f].origin[2]};
-      const float leaf = fs[f].leaf;
-      const float* p = xyz + 3 * size_t(pi[j]);
-      const Acc a = point_acc(key_local(k[j], key_shift), __ldg(p), __ldg(p + 1), __ldg(p + 2),
-                              o, leaf, quant_inv_unit(leaf));
+      Acc a;
+      if (kNarrow) {
+        const uint64_t w = uint64_t(sidx[li]);
+        pi[j] = 0;
+        a.n = 1;
+        a.s[0] = unpack_offset(w, 0);
+        a.s[1] = unpack_offset(w, 1);
+        a.s[2] = unpack_offset(w, 2);
+      } else {
+        pi[j] = uint32_t(sidx[li]);
+        const uint32_t f = key_frame(k[j], key_shift);
+        const float o[3] = {fs[f].origin[0], fs[f].origin[1], fs[f].origin[2]};
+        const float leaf = fs[f].leaf;
+        const float* p = xyz + 3 * size_t(pi[j]);
+        a = point_acc(key_local(k[j], key_shift), __ldg(p), __ldg(p + 1), __ldg(p + 2), o, leaf,
+                      quant_inv_unit(leaf));
+      }
       q[j][0] = static_cast<int>(a.s[0]);
       q[j][1] = static_cast<int>(a.s[1]);
       q[j][2] = static_cast<int>(a.s[2]);
@@ -252,7 +271,7 @@ __global__ __launch_bounds__(kSegThreads, 2) void segreduce_kernel(
     run.s[0] += q[j][0];
     run.s[1] += q[j][1];
     run.s[2] += q[j][2];
-    if (out.p2v) out.p2v[pi[j]] = static_cast<int32_t>(H - 1);
+    if (!kNarrow && out.p2v) out.p2v[pi[j]] = static_cast<int32_t>(H - 1);
     if (gi == nitems - 1) {
       emit_voxel(H - 1, k[j], run, fs, key_shift, out, err);
       *out.num_voxels = H;
@@ -270,8 +289,20 @@ cudaError_t launch_segreduce(State* st, const FrameState* fs, int nframes,
                              cudaStream_t stream) {
   if (n_max == 0) return cudaSuccess;
   const int tiles = static_cast<int>(ceil_div(n_max, kSegTile));
-  segreduce_kernel<<<tiles, kSegThreads, 0, stream>>>(st, fs, nframes, keys0, idx0, keys1, idx1,
-                                                      xyz, lb, out, spin_limit, err);
+  segreduce_kernel<false><<<tiles, kSegThreads, 0, stream>>>(st, fs, nframes, keys0, idx0, keys1,
+                                                             idx1, xyz, lb, out, spin_limit, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_segreduce_narrow(State* st, const FrameState* fs, int nframes,
+                                    const uint32_t* k0, const uint64_t* p0, const uint32_t* k1,
+                                    const uint64_t* p1, SegStatus* lb, int64_t n_max,
+                                    const SegOut& out, uint32_t spin_limit, int* err,
+                                    cudaStream_t stream) {
+  if (n_max == 0) return cudaSuccess;
+  const int tiles = static_cast<int>(ceil_div(n_max, kSegTile));
+  segreduce_kernel<true><<<tiles, kSegThreads, 0, stream>>>(st, fs, nframes, k0, p0, k1, p1,
+                                                            nullptr, lb, out, spin_limit, err);
   return cudaGetLastError();
 }
 

@@ -60,11 +60,15 @@ __device__ __forceinline__ void block_excl_scan2(uint32_t a, uint32_t b, uint32_
   *tb = sb;
 }
 
+// One radix pass.  KeyT/PayT: (uint64, uint32 point index) for the wide layout, or
+// (uint32, uint64 packed offsets) for the narrow one; a launched pass whose layout was not
+// chosen, or that is beyond the needed passes, returns before taking a tile ticket.
+template <typename KeyT, typename PayT, bool kNarrow>
 __global__ __launch_bounds__(kSortThreads, 2) void onesweep_kernel(
-    const uint64_t* __restrict__ keys_in, const uint32_t* __restrict__ idx_in,
-    uint64_t* __restrict__ keys_out, uint32_t* __restrict__ idx_out, State* st,
-    uint32_t* lb_cur, uint32_t* lb_next, int pass, int64_t n_host, int compact_input,
-    uint32_t spin_limit, int* err) {
+    const KeyT* __restrict__ keys_in, const PayT* __restrict__ pay_in,
+    KeyT* __restrict__ keys_out, PayT* __restrict__ pay_out, State* st, uint32_t* lb_cur,
+    uint32_t* lb_next, int pass, int64_t n_host, int compact_input, uint32_t spin_limit,
+    int* err) {
   __shared__ uint32_t warp_hist[kSortThreads / 32][kRadix];
   __shared__ uint32_t digit_start[kRadix];
   __shared__ uint32_t gbase[kRadix];
@@ -75,6 +79,9 @@ __global__ __launch_bounds__(kSortThreads, 2) void onesweep_kernel(
   __shared__ int s_tile;
   __shared__ uint32_t s_tile_n;
 
+  if ((st->narrow != 0) != kNarrow) return;
+  const int passes = max(1, sort_passes(st->maxkey));
+  if (pass >= passes) return;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   if (t == 0) s_tile = static_cast<int>(atomicAdd(&st->tile_ctr[pass], 1u));
   __syncthreads();
@@ -82,10 +89,9 @@ __global__ __launch_bounds__(kSortThreads, 2) void onesweep_kernel(
   // The next pass uses the other status region; every tile clears its own row of it.
   lb_next[size_t(tile) * kRadix + t] = 0;
 
-  const int passes = max(1, sort_passes(st->maxkey));
-  if (pass >= passes) return;
-  // Pass 0 of the sort path reads all n raw keys (invalid rows hold the sentinel and are
-  // dropped); every other pass, and pass 0 of compacted input, reads st->nitems entries.
+  // Pass 0 of the sort path reads all n raw entries (invalid rows are dropped: sentinel
+  // key in the wide layout, flagged payload in the narrow one); every other pass, and
+  // pass 0 of compacted input, reads st->nitems entries.
   const bool raw = pass == 0 && !compact_input;
   const int64_t n_items = raw ? n_host : int64_t(st->nitems);
   const int64_t tile_base = int64_t(tile) * kSortTile;
@@ -93,17 +99,27 @@ __global__ __launch_bounds__(kSortThreads, 2) void onesweep_kernel(
   const int shift = pass * kRadixBits;
 
   // ---- load (warp-striped: item j of lane l is tile_base + warp*512 + j*32 + l) ----
-  uint64_t key[kSortItems];
-  uint32_t pay[kSortItems];
+  KeyT key[kSortItems];
+  PayT pay[kSortItems];
   uint32_t vmask = 0;
 #pragma unroll
   for (int j = 0; j < kSortItems; ++j) {
     const int64_t i = tile_base + warp * (32 * kSortItems) + j * 32 + lane;
     const bool in = i < n_items;
-    key[j] = in ? __ldcs(keys_in + i) : kSentinel;
-    const bool ok = in && (!raw || key[j] != kSentinel);
+    key[j] = in ? __ldcs(keys_in + i) : KeyT(0);
+    bool ok = in;
+    if (kNarrow) {
+      pay[j] = in ? __ldcs(pay_in + i) : PayT(0);
+      if (raw) ok = ok && !(uint64_t(pay[j]) & kPayloadInvalid);
+    } else {
+      if (raw) {
+        ok = ok && uint64_t(key[j]) != kSentinel;
+        pay[j] = static_cast<PayT>(i);
+      } else {
+        pay[j] = in ? __ldcs(pay_in + i) : PayT(0);
+      }
+    }
     vmask |= uint32_t(ok) << j;
-    pay[j] = raw ? static_cast<uint32_t>(i) : (in ? __ldcs(idx_in + i) : 0u);
   }
   for (int d = lane; d < kRadix; d += 32) warp_hist[warp][d] = 0;
   next_hist[t] = 0;
@@ -115,7 +131,7 @@ __global__ __launch_bounds__(kSortThreads, 2) void onesweep_kernel(
 #pragma unroll
   for (int j = 0; j < kSortItems; ++j) {
     const bool ok = (vmask >> j) & 1u;
-    const uint32_t d = static_cast<uint32_t>(key[j] >> shift) & (kRadix - 1);
+    const uint32_t d = static_cast<uint32_t>(uint64_t(key[j]) >> shift) & (kRadix - 1);
     uint32_t peers = __ballot_sync(kFull, ok);
 #pragma unroll
     for (int b = 0; b < kRadixBits; ++b) {
@@ -153,23 +169,7 @@ __global__ __launch_bounds__(kSortThreads, 2) void onesweep_kernel(
     st_relaxed(my, kFlagPrefix | tile_count);
   } else {
     st_relaxed(my, kFlagAggregate | tile_count);
-    int j = tile - 1;
-    uint32_t spins = 0;
-    while (j >= 0) {
-      const uint32_t s = ld_relaxed(lb_cur + size_t(j) * kRadix + t);
-      const uint32_t f = s & ~kValueMask;
-      if (f == 0) {
-        if (++spins > spin_limit) {
-          set_error(err, kErrTimeout);
-          break;
-        }
-        if (spins > 64) __nanosleep(64);
-        continue;
-      }
-      excl += s & kValueMask;
-      if (f == kFlagPrefix) break;
-      --j;
-    }
+    excl = lookback_u32(lb_cur + t, kRadix, tile, spin_limit, err);
     st_relaxed(my, kFlagPrefix | ((excl + tile_count) & kValueMask));
   }
   digit_start[t] = local_excl;
@@ -178,33 +178,36 @@ __global__ __launch_bounds__(kSortThreads, 2) void onesweep_kernel(
   __syncthreads();
 
   // ---- keys: locally sorted in shared memory, then written digit run by digit run ----
+  KeyT* skey = reinterpret_cast<KeyT*>(sbuf);
 #pragma unroll
   for (int j = 0; j < kSortItems; ++j) {
     if ((vmask >> j) & 1u) {
-      const uint32_t d = static_cast<uint32_t>(key[j] >> shift) & (kRadix - 1);
+      const uint32_t d = static_cast<uint32_t>(uint64_t(key[j]) >> shift) & (kRadix - 1);
       rank[j] += digit_start[d] + warp_hist[warp][d];
-      sbuf[rank[j]] = key[j];
+      skey[rank[j]] = key[j];
     }
   }
   __syncthreads();
   const uint32_t tile_n = s_tile_n;
-  const bool has_next = shift + kRadixBits < 64;
+  const bool has_next = shift + kRadixBits < int(8 * sizeof(KeyT));
   for (uint32_t i = t; i < tile_n; i += kSortThreads) {
-    const uint64_t k = sbuf[i];
-    const uint32_t d = static_cast<uint32_t>(k >> shift) & (kRadix - 1);
+    const KeyT k = skey[i];
+    const uint32_t d = static_cast<uint32_t>(uint64_t(k) >> shift) & (kRadix - 1);
     sdig[i] = static_cast<uint8_t>(d);
     __stcg(keys_out + gbase[d] + (i - digit_start[d]), k);
-    if (has_next) atomicAdd(&next_hist[static_cast<uint32_t>(k >> (shift + kRadixBits)) & (kRadix - 1)], 1u);
+    if (has_next)
+      atomicAdd(&next_hist[static_cast<uint32_t>(uint64_t(k) >> (shift + kRadixBits)) & (kRadix - 1)],
+                1u);
   }
   __syncthreads();
-  uint32_t* sbuf32 = reinterpret_cast<uint32_t*>(sbuf);
+  PayT* spay = reinterpret_cast<PayT*>(sbuf);
 #pragma unroll
   for (int j = 0; j < kSortItems; ++j)
-    if ((vmask >> j) & 1u) sbuf32[rank[j]] = pay[j];
+    if ((vmask >> j) & 1u) spay[rank[j]] = pay[j];
   __syncthreads();
   for (uint32_t i = t; i < tile_n; i += kSortThreads) {
     const uint32_t d = sdig[i];
-    __stcg(idx_out + gbase[d] + (i - digit_start[d]), sbuf32[i]);
+    __stcg(pay_out + gbase[d] + (i - digit_start[d]), spay[i]);
   }
   if (has_next && pass + 1 < kMaxPasses && next_hist[t])
     atomicAdd(&st->hist[pass + 1][t], next_hist[t]);
@@ -239,9 +242,21 @@ cudaError_t launch_sort_pass(State* st, uint64_t* keys0, uint32_t* idx0, uint64_
   uint32_t* cur = even ? lb_a : lb_b;
   uint32_t* nxt = even ? lb_b : lb_a;
   const bool raw = pass == 0 && !compact_input;
-  onesweep_kernel<<<tiles, kSortThreads, 0, stream>>>(kin, raw ? nullptr : iin, kout, iout, st,
-                                                      cur, nxt, pass, n_max,
-                                                      compact_input ? 1 : 0, spin_limit, err);
+  onesweep_kernel<uint64_t, uint32_t, false><<<tiles, kSortThreads, 0, stream>>>(
+      kin, raw ? nullptr : iin, kout, iout, st, cur, nxt, pass, n_max, compact_input ? 1 : 0,
+      spin_limit, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sort_pass_narrow(State* st, uint32_t* k0, uint64_t* p0, uint32_t* k1,
+                                    uint64_t* p1, uint32_t* lb_a, uint32_t* lb_b, int64_t n_max,
+                                    int pass, uint32_t spin_limit, int* err, cudaStream_t stream) {
+  if (n_max == 0) return cudaSuccess;
+  const int tiles = static_cast<int>(ceil_div(n_max, kSortTile));
+  const bool even = (pass & 1) == 0;
+  onesweep_kernel<uint32_t, uint64_t, true><<<tiles, kSortThreads, 0, stream>>>(
+      even ? k0 : k1, even ? p0 : p1, even ? k1 : k0, even ? p1 : p0, st, even ? lb_a : lb_b,
+      even ? lb_b : lb_a, pass, n_max, 0, spin_limit, err);
   return cudaGetLastError();
 }
 

@@ -27,7 +27,8 @@ __device__ __forceinline__ void block_range(uint32_t T, uint32_t* c0, uint32_t* 
 // 0 publishes origins, leaves and the shift.  Contains __syncthreads.
 __device__ __forceinline__ uint32_t frame_prologue(const FramesArg& fr, bool have_extent,
                                                    State* st, FrameState* fs, uint32_t T,
-                                                   ChunkSmem& sm, int* err) {
+                                                   ChunkSmem& sm, int* err,
+                                                   bool* narrow = nullptr) {
   const int F = fr.nframes;
   // per-frame origin and leaf; bits of the largest key of each frame
   uint32_t bits = 0;
@@ -54,7 +55,7 @@ __device__ __forceinline__ uint32_t frame_prologue(const FramesArg& fr, bool hav
       }
       fs[f].leaf = leaf;
     }
-    if (have_extent && any && F > 1) {
+    if (have_extent && any) {
       uint32_t ii[3];
       bool ok = true;
       for (int a = 0; a < 3; ++a)
@@ -70,17 +71,23 @@ __device__ __forceinline__ uint32_t frame_prologue(const FramesArg& fr, bool hav
   if (lane == 0) sm.bits[warp] = bits;
   if (__syncthreads_or(bad_leaf) && threadIdx.x == 0 && blockIdx.x == 0)
     set_error(err, kErrInvalidArg);
-  uint32_t key_shift = 64;
+  uint32_t maxbits = 0;
+  for (int w = 0; w < kStreamThreads / 32; ++w) maxbits = max(maxbits, sm.bits[w]);
+  uint32_t key_shift = 64, total_bits = maxbits;
   if (F > 1) {
-    key_shift = 0;
-    for (int w = 0; w < kStreamThreads / 32; ++w) key_shift = max(key_shift, sm.bits[w]);
+    key_shift = maxbits;
     const uint32_t fbits = 32u - __clz(static_cast<int>(F - 1));
-    if (key_shift + fbits > 63 && threadIdx.x == 0 && blockIdx.x == 0) set_error(err, kErrRange);
+    total_bits = key_shift + fbits;
+    if (total_bits > 63 && threadIdx.x == 0 && blockIdx.x == 0) set_error(err, kErrRange);
   }
+  // The narrow layout needs the largest key known in advance (the extents) and <= 32 bits.
+  const bool nar = fr.allow_narrow && have_extent && total_bits <= 32;
+  if (narrow) *narrow = nar;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     st->key_shift = key_shift;
     st->nframes = F;
     st->nchunks = T;
+    st->narrow = nar ? 1u : 0u;
   }
 
   __syncthreads();
