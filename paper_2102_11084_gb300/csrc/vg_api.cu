@@ -2,6 +2,7 @@
 // layouts and the launch sequence of each call.  No allocation happens here (the plan
 // object in vg_plan.cu is the only owner of device memory in the library).
 #include <atomic>
+#include <mutex>
 #include <cmath>
 #include <cstring>
 
@@ -38,6 +39,47 @@ int num_sms() {
 }
 
 void pause_stage_events(bool paused) { g_events_paused = paused; }
+
+namespace {
+struct OccEntry {
+  const void* fn;
+  int dev;
+  int blocks;
+};
+std::mutex g_occ_mu;
+OccEntry g_occ[64];
+int g_occ_n = 0;
+}  // namespace
+
+void warm_launch_config() {
+  num_sms();
+  warm_sort_config();
+  warm_reduce_config();
+}
+
+int persistent_grid(const void* kernel, int threads, size_t dyn_smem, int64_t work_tiles) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int blocks = 0;
+  {
+    std::lock_guard<std::mutex> lock(g_occ_mu);
+    for (int i = 0; i < g_occ_n; ++i)
+      if (g_occ[i].fn == kernel && g_occ[i].dev == dev) blocks = g_occ[i].blocks;
+    if (blocks == 0) {
+      if (dyn_smem > 48 * 1024 - 4096)
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(dyn_smem));
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kernel, threads, dyn_smem) !=
+              cudaSuccess ||
+          blocks < 1)
+        blocks = 1;
+      if (g_occ_n < 64) g_occ[g_occ_n++] = OccEntry{kernel, dev, blocks};
+    }
+  }
+  const int64_t cap = int64_t(blocks) * num_sms();
+  const int64_t g = work_tiles < cap ? work_tiles : cap;
+  return static_cast<int>(g < 1 ? 1 : g);
+}
 
 namespace {
 

@@ -86,6 +86,21 @@ __device__ __forceinline__ bool point_key(float x, float y, float z, const float
   return true;
 }
 
+// point_key that also returns the voxel indices.
+__device__ __forceinline__ bool point_key_ijk(float x, float y, float z, const float o[3],
+                                              float leaf, uint64_t* key, uint32_t ijk[3],
+                                              bool* range_bad) {
+  if (!point_valid(x, y, z)) return false;
+  const bool ok = axis_index(x, o[0], leaf, &ijk[0]) & axis_index(y, o[1], leaf, &ijk[1]) &
+                  axis_index(z, o[2], leaf, &ijk[2]);
+  if (!ok) {
+    *range_bad = true;
+    return false;
+  }
+  *key = morton3(ijk[0], ijk[1], ijk[2]);
+  return true;
+}
+
 // Split a sort key into (frame, per-frame voxel key).  key_shift == 64: one frame.
 __device__ __forceinline__ uint32_t key_frame(uint64_t key, uint32_t key_shift) {
   return key_shift >= 64 ? 0u : static_cast<uint32_t>(key >> key_shift);

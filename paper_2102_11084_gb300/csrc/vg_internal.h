@@ -145,6 +145,14 @@ constexpr SortLayout sort_layout(int64_t n, int frames = 1) {
 
 int num_sms();
 uint32_t spin_limit();
+// Grid of a persistent kernel: all its blocks resident at once (occupancy x SMs), at most
+// one block per unit of work.  Sets the dynamic shared-memory limit when needed.
+int persistent_grid(const void* kernel, int threads, size_t dyn_smem, int64_t work_tiles);
+// Runs the occupancy queries of every persistent kernel on the current device (so that a
+// later CUDA-graph capture makes none).
+void warm_launch_config();
+void warm_sort_config();
+void warm_reduce_config();
 
 // Launchers (all asynchronous on `stream`).
 // a1: per-frame min (and max) of the valid points into FrameState.

@@ -131,7 +131,9 @@ __global__ __launch_bounds__(kStreamThreads) void key_kernel(
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       uint64_t local;
-      const bool ok = point_key(v[3 * j], v[3 * j + 1], v[3 * j + 2], o, leaf, &local, &range_bad);
+      uint32_t ijk[3];
+      const bool ok =
+          point_key_ijk(v[3 * j], v[3 * j + 1], v[3 * j + 2], o, leaf, &local, ijk, &range_bad);
       k[j] = ok ? key_compose(static_cast<uint32_t>(f), local, key_shift) : kKeySentinel;
       pay[j] = kPayloadInvalid;
       if (ok) {
@@ -139,8 +141,11 @@ __global__ __launch_bounds__(kStreamThreads) void key_kernel(
         kmax = k[j] > kmax ? k[j] : kmax;
         atomicAdd(&hist[k[j] & (kRadix - 1)], 1u);
         if (narrow) {
-          const Acc a = point_acc(local, v[3 * j], v[3 * j + 1], v[3 * j + 2], o, leaf, inv_unit);
-          pay[j] = pack_offsets(int(a.s[0]), int(a.s[1]), int(a.s[2]));
+          int qq[3];
+#pragma unroll
+          for (int a = 0; a < 3; ++a)
+            qq[a] = quant_offset(v[3 * j + a], voxel_corner(ijk[a], o[a], leaf), inv_unit);
+          pay[j] = pack_offsets(qq[0], qq[1], qq[2]);
         }
       }
     }

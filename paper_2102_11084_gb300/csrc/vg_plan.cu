@@ -75,6 +75,7 @@ vg_status vg_plan_create(vg_plan** out, int max_frames, int64_t max_points, int 
     delete p;
     return VG_ERR_CUDA;
   }
+  vg::warm_launch_config();  // occupancy queries happen here, never inside a capture
   *out = p;
   return VG_OK;
 }

@@ -60,10 +60,17 @@ __device__ __forceinline__ Seg seg_shfl_up(const Seg& s, int off) {
   return r;
 }
 
-// Writes voxel v (sort key `key`, sums `a`) and its centroid.
-__device__ __forceinline__ void emit_voxel(uint32_t v, uint64_t key, const Acc& a,
+// Output rows of one tile, staged in shared memory and written out coalesced.
+struct Stage {
+  uint64_t* key;    // [kSegTile + 1]
+  uint32_t* count;  // [kSegTile + 1]; 0 = not emitted by this tile
+  float* cent;      // [3 * (kSegTile + 1)]
+};
+
+// Stages voxel v (sort key `key`, sums `a`) at e = v - e0 of this tile.
+__device__ __forceinline__ void emit_voxel(uint32_t v, int64_t e0, uint64_t key, const Acc& a,
                                            const FrameState* fs, uint32_t key_shift,
-                                           const SegOut& out, int* err) {
+                                           const SegOut& out, const Stage& sg, int* err) {
   if (int64_t(v) >= out.cap) {
     set_error(err, kErrCapacity);
     return;
@@ -74,11 +81,12 @@ __device__ __forceinline__ void emit_voxel(uint32_t v, uint64_t key, const Acc& 
   const float leaf = fs[f].leaf;
   float c[3];
   acc_centroid(local, a, o, leaf, quant_inv_unit(leaf), c);
-  out.keys[v] = local;
-  out.counts[v] = a.n;
-  out.centroids[3 * size_t(v)] = c[0];
-  out.centroids[3 * size_t(v) + 1] = c[1];
-  out.centroids[3 * size_t(v) + 2] = c[2];
+  const int e = static_cast<int>(int64_t(v) - e0);
+  sg.key[e] = local;
+  sg.count[e] = a.n;
+  sg.cent[3 * e] = c[0];
+  sg.cent[3 * e + 1] = c[1];
+  sg.cent[3 * e + 2] = c[2];
   if (out.sums) {
     out.sums[3 * size_t(v)] = a.s[0];
     out.sums[3 * size_t(v) + 1] = a.s[1];
@@ -93,9 +101,20 @@ __device__ __forceinline__ void mark_frames(int64_t* fo, uint32_t f_prev, uint32
   for (uint32_t f = f_prev + 1; f <= f_new; ++f) fo[f] = v;
 }
 
+}  // namespace
+
+// Shared-memory bytes of the reduction: the staged rows; the sorted input entries of a tile
+// (keys and payloads) overlay the same bytes before they are consumed.
+constexpr size_t kSegStageBytes =
+    size_t(kSegTile + 1) * (sizeof(uint64_t) + sizeof(uint32_t) + 3 * sizeof(float));
+static_assert(kSegStageBytes >= size_t(kSegTile) * 2 * sizeof(uint64_t), "stage overlay");
+
+namespace {
+
 // kNarrow: 32-bit keys with the packed offsets as payload (no gather); otherwise 64-bit
-// keys with the point index as payload, whose coordinates are gathered.  A launch whose
-// layout was not chosen returns before taking a tile ticket.
+// keys with the point index as payload, whose coordinates are gathered.  Persistent: each
+// block takes tiles from a ticket until none is left.  A launch whose layout was not
+// chosen returns before taking a ticket.
 template <bool kNarrow>
 __global__ __launch_bounds__(kSegThreads, 2) void segreduce_kernel(
     State* st, const FrameState* __restrict__ fs, int nframes, const void* keys0_,
@@ -103,180 +122,211 @@ __global__ __launch_bounds__(kSegThreads, 2) void segreduce_kernel(
     SegStatus* lb, SegOut out, uint32_t spin_limit, int* err) {
   using KeyT = typename std::conditional<kNarrow, uint32_t, uint64_t>::type;
   using PayT = typename std::conditional<kNarrow, uint64_t, uint32_t>::type;
-  __shared__ uint64_t skeys[kSegTile];
-  __shared__ PayT sidx[kSegTile];
-  if ((st->narrow != 0) != kNarrow) return;
+  extern __shared__ __align__(16) unsigned char seg_smem[];
   __shared__ Seg wtot[kSegThreads / 32];
   __shared__ Seg s_tile_excl;
+  __shared__ uint32_t s_tile_heads;
   __shared__ uint64_t s_prev_key;
   __shared__ int s_tile;
+  if ((st->narrow != 0) != kNarrow) return;
+
+  uint64_t* skeys = reinterpret_cast<uint64_t*>(seg_smem);
+  PayT* sidx = reinterpret_cast<PayT*>(seg_smem + size_t(kSegTile) * sizeof(uint64_t));
+  Stage sg;
+  sg.key = reinterpret_cast<uint64_t*>(seg_smem);
+  sg.count = reinterpret_cast<uint32_t*>(seg_smem + size_t(kSegTile + 1) * sizeof(uint64_t));
+  sg.cent = reinterpret_cast<float*>(seg_smem + size_t(kSegTile + 1) * (sizeof(uint64_t) +
+                                                                         sizeof(uint32_t)));
 
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  if (t == 0) s_tile = static_cast<int>(atomicAdd(&st->tile_ctr[kMaxPasses], 1u));
-  __syncthreads();
-  const int tile = s_tile;
   const int64_t nitems = st->nitems;
-  const int64_t base = int64_t(tile) * kSegTile;
-  if (base >= nitems) return;
+  const int64_t ntiles = ceil_div(nitems, kSegTile);
   const uint32_t key_shift = st->key_shift;
   const int passes = max(1, sort_passes(st->maxkey));
   const KeyT* K = static_cast<const KeyT*>((passes & 1) ? keys1_ : keys0_);
   const PayT* I = static_cast<const PayT*>((passes & 1) ? pay1_ : pay0_);
-  const int cnt = static_cast<int>(nitems - base < kSegTile ? nitems - base : kSegTile);
-
-  for (int i = t; i < cnt; i += kSegThreads) {
-    skeys[i] = __ldcs(K + base + i);
-    sidx[i] = __ldcs(I + base + i);
-  }
-  if (t == 0) s_prev_key = base > 0 ? uint64_t(K[base - 1]) : 0ull;
-  __syncthreads();
-
-  // ---- this thread's entries (blocked: t*8 .. t*8+7) ----
-  uint64_t k[kSegItems];
-  uint32_t pi[kSegItems];
   (void)xyz;
-  int q[kSegItems][3];
-  uint32_t headmask = 0;
-  const int first = t * kSegItems;
-  const uint64_t prev0 = first == 0 ? s_prev_key : skeys[first > 0 ? first - 1 : 0];
-  Seg mine = seg_identity();
-#pragma unroll
-  for (int j = 0; j < kSegItems; ++j) {
-    const int li = first + j;
-    if (li < cnt) {
-      k[j] = skeys[li];
-      const uint64_t pk = j == 0 ? prev0 : k[j - 1];
-      const bool head = (base + li == 0) || (k[j] != pk);
-      headmask |= uint32_t(head) << j;
-      Acc a;
-      if (kNarrow) {
-        const uint64_t w = uint64_t(sidx[li]);
-        pi[j] = 0;
-        a.n = 1;
-        a.s[0] = unpack_offset(w, 0);
-        a.s[1] = unpack_offset(w, 1);
-        a.s[2] = unpack_offset(w, 2);
-      } else {
-        pi[j] = uint32_t(sidx[li]);
-        const uint32_t f = key_frame(k[j], key_shift);
-        const float o[3] = {fs[f].origin[0], fs[f].origin[1], fs[f].origin[2]};
-        const float leaf = fs[f].leaf;
-        const float* p = xyz + 3 * size_t(pi[j]);
-        a = point_acc(key_local(k[j], key_shift), __ldg(p), __ldg(p + 1), __ldg(p + 2), o, leaf,
-                      quant_inv_unit(leaf));
-      }
-      q[j][0] = static_cast<int>(a.s[0]);
-      q[j][1] = static_cast<int>(a.s[1]);
-      q[j][2] = static_cast<int>(a.s[2]);
-      if (head) {
-        mine.h += 1;
-        mine.a = acc_zero();
-      }
-      acc_add(mine.a, a);
-    } else {
-      k[j] = 0;
-      pi[j] = 0;
-      q[j][0] = q[j][1] = q[j][2] = 0;
+
+  for (;;) {
+    if (t == 0) s_tile = static_cast<int>(atomicAdd(&st->tile_ctr[kMaxPasses], 1u));
+    __syncthreads();
+    const int tile = s_tile;
+    if (tile >= ntiles) break;
+    const int64_t base = int64_t(tile) * kSegTile;
+    const int cnt = static_cast<int>(nitems - base < kSegTile ? nitems - base : kSegTile);
+
+    for (int i = t; i < cnt; i += kSegThreads) {
+      skeys[i] = uint64_t(__ldcs(K + base + i));
+      sidx[i] = __ldcs(I + base + i);
     }
-  }
+    if (t == 0) s_prev_key = base > 0 ? uint64_t(K[base - 1]) : 0ull;
+    __syncthreads();
 
-  // ---- block segmented scan over threads ----
-  Seg incl = mine;
+    // ---- this thread's entries (blocked: t*8 .. t*8+7) ----
+    uint64_t k[kSegItems];
+    uint32_t pi[kSegItems];
+    int q[kSegItems][3];
+    uint32_t headmask = 0;
+    const int first = t * kSegItems;
+    const uint64_t prev0 = first == 0 ? s_prev_key : skeys[first > 0 ? first - 1 : 0];
+    Seg mine = seg_identity();
 #pragma unroll
-  for (int off = 1; off < 32; off <<= 1) {
-    const Seg y = seg_shfl_up(incl, off);
-    if (lane >= off) incl = seg_combine(y, incl);
-  }
-  Seg lane_excl = seg_shfl_up(incl, 1);
-  if (lane == 0) lane_excl = seg_identity();
-  if (lane == 31) wtot[warp] = incl;
-  __syncthreads();
-
-  if (t == 0) {
-    Seg agg = seg_identity();
-    for (int w = 0; w < kSegThreads / 32; ++w) agg = seg_combine(agg, wtot[w]);
-    SegStatus* me = lb + tile;
-    Seg excl = seg_identity();
-    if (tile == 0) {
-      me->heads_incl = agg.h;
-      me->n_incl = agg.a.n;
-      for (int a = 0; a < 3; ++a) me->s_incl[a] = agg.a.s[a];
-      st_release(&me->flag, 2u);
-    } else {
-      me->heads_agg = agg.h;
-      me->n_agg = agg.a.n;
-      for (int a = 0; a < 3; ++a) me->s_agg[a] = agg.a.s[a];
-      st_release(&me->flag, 1u);
-      Seg suffix = seg_identity();
-      int j = tile - 1;
-      uint32_t spins = 0;
-      while (j >= 0) {
-        const SegStatus* other = lb + j;
-        const uint32_t f = ld_acquire(&other->flag);
-        if (f == 0) {
-          if (++spins > spin_limit) {
-            set_error(err, kErrTimeout);
-            break;
-          }
-          if (spins > 64) __nanosleep(64);
-          continue;
-        }
-        Seg v;
-        if (f == 1u) {
-          v.h = __ldcg(&other->heads_agg);
-          v.a.n = __ldcg(&other->n_agg);
-          for (int a = 0; a < 3; ++a) v.a.s[a] = __ldcg(&other->s_agg[a]);
-        } else {
-          v.h = __ldcg(&other->heads_incl);
-          v.a.n = __ldcg(&other->n_incl);
-          for (int a = 0; a < 3; ++a) v.a.s[a] = __ldcg(&other->s_incl[a]);
-        }
-        suffix = seg_combine(v, suffix);
-        if (f != 1u) break;
-        --j;
-      }
-      excl = suffix;
-      const Seg inc = seg_combine(excl, agg);
-      me->heads_incl = inc.h;
-      me->n_incl = inc.a.n;
-      for (int a = 0; a < 3; ++a) me->s_incl[a] = inc.a.s[a];
-      st_release(&me->flag, 2u);
-    }
-    s_tile_excl = excl;
-  }
-  __syncthreads();
-
-  Seg wexcl = seg_identity();
-  for (int w = 0; w < warp; ++w) wexcl = seg_combine(wexcl, wtot[w]);
-  const Seg pre = seg_combine(seg_combine(s_tile_excl, wexcl), lane_excl);
-
-  // ---- emit every run at its last entry ----
-  uint32_t H = pre.h;
-  Acc run = pre.a;
-#pragma unroll
-  for (int j = 0; j < kSegItems; ++j) {
-    const int li = first + j;
-    if (li >= cnt) break;
-    const int64_t gi = base + li;
-    if ((headmask >> j) & 1u) {
-      if (gi > 0) {
+    for (int j = 0; j < kSegItems; ++j) {
+      const int li = first + j;
+      if (li < cnt) {
+        k[j] = skeys[li];
         const uint64_t pk = j == 0 ? prev0 : k[j - 1];
-        emit_voxel(H - 1, pk, run, fs, key_shift, out, err);
-        mark_frames(out.frame_offsets, key_frame(pk, key_shift), key_frame(k[j], key_shift), H);
+        const bool head = (base + li == 0) || (k[j] != pk);
+        headmask |= uint32_t(head) << j;
+        Acc a;
+        if (kNarrow) {
+          const uint64_t w = uint64_t(sidx[li]);
+          pi[j] = 0;
+          a.n = 1;
+          a.s[0] = unpack_offset(w, 0);
+          a.s[1] = unpack_offset(w, 1);
+          a.s[2] = unpack_offset(w, 2);
+        } else {
+          pi[j] = uint32_t(sidx[li]);
+          const uint32_t f = key_frame(k[j], key_shift);
+          const float o[3] = {fs[f].origin[0], fs[f].origin[1], fs[f].origin[2]};
+          const float leaf = fs[f].leaf;
+          const float* p = xyz + 3 * size_t(pi[j]);
+          a = point_acc(key_local(k[j], key_shift), __ldg(p), __ldg(p + 1), __ldg(p + 2), o,
+                        leaf, quant_inv_unit(leaf));
+        }
+        q[j][0] = static_cast<int>(a.s[0]);
+        q[j][1] = static_cast<int>(a.s[1]);
+        q[j][2] = static_cast<int>(a.s[2]);
+        if (head) {
+          mine.h += 1;
+          mine.a = acc_zero();
+        }
+        acc_add(mine.a, a);
+      } else {
+        k[j] = 0;
+        pi[j] = 0;
+        q[j][0] = q[j][1] = q[j][2] = 0;
       }
-      H += 1;
-      run = acc_zero();
     }
-    run.n += 1;
-    run.s[0] += q[j][0];
-    run.s[1] += q[j][1];
-    run.s[2] += q[j][2];
-    if (!kNarrow && out.p2v) out.p2v[pi[j]] = static_cast<int32_t>(H - 1);
-    if (gi == nitems - 1) {
-      emit_voxel(H - 1, k[j], run, fs, key_shift, out, err);
-      *out.num_voxels = H;
-      mark_frames(out.frame_offsets, key_frame(k[j], key_shift), uint32_t(nframes), H);
+
+    // ---- block segmented scan over threads ----
+    Seg incl = mine;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const Seg y = seg_shfl_up(incl, off);
+      if (lane >= off) incl = seg_combine(y, incl);
     }
+    Seg lane_excl = seg_shfl_up(incl, 1);
+    if (lane == 0) lane_excl = seg_identity();
+    if (lane == 31) wtot[warp] = incl;
+    __syncthreads();
+
+    if (t == 0) {
+      Seg agg = seg_identity();
+      for (int w = 0; w < kSegThreads / 32; ++w) agg = seg_combine(agg, wtot[w]);
+      SegStatus* me = lb + tile;
+      Seg excl = seg_identity();
+      if (tile == 0) {
+        me->heads_incl = agg.h;
+        me->n_incl = agg.a.n;
+        for (int a = 0; a < 3; ++a) me->s_incl[a] = agg.a.s[a];
+        st_release(&me->flag, 2u);
+      } else {
+        me->heads_agg = agg.h;
+        me->n_agg = agg.a.n;
+        for (int a = 0; a < 3; ++a) me->s_agg[a] = agg.a.s[a];
+        st_release(&me->flag, 1u);
+        Seg suffix = seg_identity();
+        int j = tile - 1;
+        uint32_t spins = 0;
+        while (j >= 0) {
+          const SegStatus* other = lb + j;
+          const uint32_t f = ld_acquire(&other->flag);
+          if (f == 0) {
+            if (++spins > spin_limit) {
+              set_error(err, kErrTimeout);
+              break;
+            }
+            if (spins > 64) __nanosleep(64);
+            continue;
+          }
+          Seg v;
+          if (f == 1u) {
+            v.h = __ldcg(&other->heads_agg);
+            v.a.n = __ldcg(&other->n_agg);
+            for (int a = 0; a < 3; ++a) v.a.s[a] = __ldcg(&other->s_agg[a]);
+          } else {
+            v.h = __ldcg(&other->heads_incl);
+            v.a.n = __ldcg(&other->n_incl);
+            for (int a = 0; a < 3; ++a) v.a.s[a] = __ldcg(&other->s_incl[a]);
+          }
+          suffix = seg_combine(v, suffix);
+          if (f != 1u) break;
+          --j;
+        }
+        excl = suffix;
+        const Seg inc = seg_combine(excl, agg);
+        me->heads_incl = inc.h;
+        me->n_incl = inc.a.n;
+        for (int a = 0; a < 3; ++a) me->s_incl[a] = inc.a.s[a];
+        st_release(&me->flag, 2u);
+      }
+      s_tile_excl = excl;
+      s_tile_heads = agg.h;
+    }
+    __syncthreads();
+
+    // rows this tile can emit: [e0, e0 + span), staged from here on (inputs are consumed)
+    const uint32_t H0 = s_tile_excl.h;
+    const int64_t e0 = H0 > 0 ? int64_t(H0) - 1 : 0;
+    const int span = static_cast<int>(int64_t(H0) + s_tile_heads - e0);
+    for (int e = t; e < span; e += kSegThreads) sg.count[e] = 0;
+    Seg wexcl = seg_identity();
+    for (int w = 0; w < warp; ++w) wexcl = seg_combine(wexcl, wtot[w]);
+    const Seg pre = seg_combine(seg_combine(s_tile_excl, wexcl), lane_excl);
+    __syncthreads();
+
+    // ---- emit every run at its last entry ----
+    uint32_t H = pre.h;
+    Acc run = pre.a;
+#pragma unroll
+    for (int j = 0; j < kSegItems; ++j) {
+      const int li = first + j;
+      if (li >= cnt) break;
+      const int64_t gi = base + li;
+      if ((headmask >> j) & 1u) {
+        if (gi > 0) {
+          const uint64_t pk = j == 0 ? prev0 : k[j - 1];
+          emit_voxel(H - 1, e0, pk, run, fs, key_shift, out, sg, err);
+          mark_frames(out.frame_offsets, key_frame(pk, key_shift), key_frame(k[j], key_shift), H);
+        }
+        H += 1;
+        run = acc_zero();
+      }
+      run.n += 1;
+      run.s[0] += q[j][0];
+      run.s[1] += q[j][1];
+      run.s[2] += q[j][2];
+      if (!kNarrow && out.p2v) out.p2v[pi[j]] = static_cast<int32_t>(H - 1);
+      if (gi == nitems - 1) {
+        emit_voxel(H - 1, e0, k[j], run, fs, key_shift, out, sg, err);
+        *out.num_voxels = H;
+        mark_frames(out.frame_offsets, key_frame(k[j], key_shift), uint32_t(nframes), H);
+      }
+    }
+    __syncthreads();
+
+    // ---- coalesced write-out of the staged rows ----
+    for (int e = t; e < span; e += kSegThreads) {
+      if (sg.count[e]) {
+        out.keys[e0 + e] = sg.key[e];
+        out.counts[e0 + e] = sg.count[e];
+      }
+    }
+    for (int x = t; x < 3 * span; x += kSegThreads)
+      if (sg.count[x / 3]) out.centroids[3 * e0 + x] = sg.cent[x];
+    __syncthreads();
   }
 }
 
@@ -288,10 +338,18 @@ cudaError_t launch_segreduce(State* st, const FrameState* fs, int nframes,
                              int64_t n_max, const SegOut& out, uint32_t spin_limit, int* err,
                              cudaStream_t stream) {
   if (n_max == 0) return cudaSuccess;
-  const int tiles = static_cast<int>(ceil_div(n_max, kSegTile));
-  segreduce_kernel<false><<<tiles, kSegThreads, 0, stream>>>(st, fs, nframes, keys0, idx0, keys1,
-                                                             idx1, xyz, lb, out, spin_limit, err);
+  const int grid = persistent_grid(reinterpret_cast<const void*>(segreduce_kernel<false>),
+                                   kSegThreads, kSegStageBytes, ceil_div(n_max, kSegTile));
+  segreduce_kernel<false><<<grid, kSegThreads, kSegStageBytes, stream>>>(
+      st, fs, nframes, keys0, idx0, keys1, idx1, xyz, lb, out, spin_limit, err);
   return cudaGetLastError();
+}
+
+void warm_reduce_config() {
+  persistent_grid(reinterpret_cast<const void*>(segreduce_kernel<false>), kSegThreads,
+                  kSegStageBytes, 1);
+  persistent_grid(reinterpret_cast<const void*>(segreduce_kernel<true>), kSegThreads,
+                  kSegStageBytes, 1);
 }
 
 cudaError_t launch_segreduce_narrow(State* st, const FrameState* fs, int nframes,
@@ -300,9 +358,10 @@ cudaError_t launch_segreduce_narrow(State* st, const FrameState* fs, int nframes
                                     const SegOut& out, uint32_t spin_limit, int* err,
                                     cudaStream_t stream) {
   if (n_max == 0) return cudaSuccess;
-  const int tiles = static_cast<int>(ceil_div(n_max, kSegTile));
-  segreduce_kernel<true><<<tiles, kSegThreads, 0, stream>>>(st, fs, nframes, k0, p0, k1, p1,
-                                                            nullptr, lb, out, spin_limit, err);
+  const int grid = persistent_grid(reinterpret_cast<const void*>(segreduce_kernel<true>),
+                                   kSegThreads, kSegStageBytes, ceil_div(n_max, kSegTile));
+  segreduce_kernel<true><<<grid, kSegThreads, kSegStageBytes, stream>>>(
+      st, fs, nframes, k0, p0, k1, p1, nullptr, lb, out, spin_limit, err);
   return cudaGetLastError();
 }
 

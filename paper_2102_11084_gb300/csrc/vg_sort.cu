@@ -83,20 +83,22 @@ __global__ __launch_bounds__(kSortThreads, 2) void onesweep_kernel(
   const int passes = max(1, sort_passes(st->maxkey));
   if (pass >= passes) return;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  if (t == 0) s_tile = static_cast<int>(atomicAdd(&st->tile_ctr[pass], 1u));
-  __syncthreads();
-  const int tile = s_tile;
-  // The next pass uses the other status region; every tile clears its own row of it.
-  lb_next[size_t(tile) * kRadix + t] = 0;
-
   // Pass 0 of the sort path reads all n raw entries (invalid rows are dropped: sentinel
   // key in the wide layout, flagged payload in the narrow one); every other pass, and
   // pass 0 of compacted input, reads st->nitems entries.
   const bool raw = pass == 0 && !compact_input;
   const int64_t n_items = raw ? n_host : int64_t(st->nitems);
-  const int64_t tile_base = int64_t(tile) * kSortTile;
-  if (tile_base >= n_items) return;
+  const int64_t ntiles = ceil_div(n_items, kSortTile);
   const int shift = pass * kRadixBits;
+
+  for (;;) {  // persistent: tiles from a ticket until none is left
+  if (t == 0) s_tile = static_cast<int>(atomicAdd(&st->tile_ctr[pass], 1u));
+  __syncthreads();
+  const int tile = s_tile;
+  if (tile >= ntiles) break;
+  // The next pass uses the other status region; every tile clears its own row of it.
+  lb_next[size_t(tile) * kRadix + t] = 0;
+  const int64_t tile_base = int64_t(tile) * kSortTile;
 
   // ---- load (warp-striped: item j of lane l is tile_base + warp*512 + j*32 + l) ----
   KeyT key[kSortItems];
@@ -211,6 +213,8 @@ __global__ __launch_bounds__(kSortThreads, 2) void onesweep_kernel(
   }
   if (has_next && pass + 1 < kMaxPasses && next_hist[t])
     atomicAdd(&st->hist[pass + 1][t], next_hist[t]);
+  __syncthreads();
+  }
 }
 
 // Test kernel: one chained-scan wait of tile `tile` on status words nobody publishes; it
@@ -232,7 +236,9 @@ cudaError_t launch_sort_pass(State* st, uint64_t* keys0, uint32_t* idx0, uint64_
                              int pass, bool compact_input, uint32_t spin_limit, int* err,
                              cudaStream_t stream) {
   if (n_max == 0) return cudaSuccess;
-  const int tiles = static_cast<int>(ceil_div(n_max, kSortTile));
+  const int tiles = persistent_grid(
+      reinterpret_cast<const void*>(onesweep_kernel<uint64_t, uint32_t, false>), kSortThreads, 0,
+      ceil_div(n_max, kSortTile));
   const bool even = (pass & 1) == 0;
   // pass p reads buffer (p odd ? 1 : 0) and writes the other; pass 0 reads raw keys.
   const uint64_t* kin = even ? keys0 : keys1;
@@ -248,11 +254,20 @@ cudaError_t launch_sort_pass(State* st, uint64_t* keys0, uint32_t* idx0, uint64_
   return cudaGetLastError();
 }
 
+void warm_sort_config() {
+  persistent_grid(reinterpret_cast<const void*>(onesweep_kernel<uint64_t, uint32_t, false>),
+                  kSortThreads, 0, 1);
+  persistent_grid(reinterpret_cast<const void*>(onesweep_kernel<uint32_t, uint64_t, true>),
+                  kSortThreads, 0, 1);
+}
+
 cudaError_t launch_sort_pass_narrow(State* st, uint32_t* k0, uint64_t* p0, uint32_t* k1,
                                     uint64_t* p1, uint32_t* lb_a, uint32_t* lb_b, int64_t n_max,
                                     int pass, uint32_t spin_limit, int* err, cudaStream_t stream) {
   if (n_max == 0) return cudaSuccess;
-  const int tiles = static_cast<int>(ceil_div(n_max, kSortTile));
+  const int tiles = persistent_grid(
+      reinterpret_cast<const void*>(onesweep_kernel<uint32_t, uint64_t, true>), kSortThreads, 0,
+      ceil_div(n_max, kSortTile));
   const bool even = (pass & 1) == 0;
   onesweep_kernel<uint32_t, uint64_t, true><<<tiles, kSortThreads, 0, stream>>>(
       even ? k0 : k1, even ? p0 : p1, even ? k1 : k0, even ? p1 : p0, st, even ? lb_a : lb_b,
