@@ -40,6 +40,31 @@ __device__ __forceinline__ bool axis_index(float p, float o, float leaf, uint32_
   return true;
 }
 
+// The same index as axis_index, cheaper: q1 = fl(fl(p-o) * r) with r = fl(1/leaf) is
+// within 1.5*2^-23*|q| of fl((p-o)/leaf), so whenever q1 lies farther than |q1|*2^-20 from
+// every integer both have the same floor (and the same side of 0 and 2^21, which are
+// integers); otherwise the exact division decides.  Valid for 2^-100 < leaf < 2^100
+// (r is then a normal number); callers check that range.
+__device__ __forceinline__ bool axis_index_fast(float p, float o, float leaf, float r,
+                                                uint32_t* i) {
+  const float t = __fsub_rn(p, o);
+  const float q1 = __fmul_rn(t, r);
+  const float fl = floorf(q1);
+  const float d = q1 - fl;
+  const float margin = fabsf(q1) * 9.5367431640625e-07f;  // 2^-20
+  if (d > margin && 1.0f - d > margin) {
+    if (!(fl >= 0.0f) || !(fl < kAxisLimitF)) return false;
+    *i = static_cast<uint32_t>(fl);
+    return true;
+  }
+  return axis_index(p, o, leaf, i);
+}
+
+// leaf range in which axis_index_fast may be used
+__device__ __forceinline__ bool fast_leaf(float leaf) {
+  return leaf > 7.8886090522101181e-31f && leaf < 1.2676506002282294e30f;  // 2^-100, 2^100
+}
+
 __device__ __forceinline__ bool point_valid(float x, float y, float z) {
   return isfinite(x) && isfinite(y) && isfinite(z);
 }
@@ -70,35 +95,35 @@ __device__ __forceinline__ uint64_t morton3(uint32_t ix, uint32_t iy, uint32_t i
   return spread3(ix) | (spread3(iy) << 1) | (spread3(iz) << 2);
 }
 
-// Morton key of a point, or false if the point is invalid / out of range (*range_bad
-// set for the latter).
-__device__ __forceinline__ bool point_key(float x, float y, float z, const float o[3],
-                                          float leaf, uint64_t* key, bool* range_bad) {
-  if (!point_valid(x, y, z)) return false;
-  uint32_t ix, iy, iz;
-  const bool ok = axis_index(x, o[0], leaf, &ix) & axis_index(y, o[1], leaf, &iy) &
-                  axis_index(z, o[2], leaf, &iz);
-  if (!ok) {
-    *range_bad = true;
-    return false;
-  }
-  *key = morton3(ix, iy, iz);
-  return true;
-}
-
 // point_key that also returns the voxel indices.
+// rleaf = fl(1/leaf) when fast_leaf(leaf), else 0 (exact division for every point).
 __device__ __forceinline__ bool point_key_ijk(float x, float y, float z, const float o[3],
-                                              float leaf, uint64_t* key, uint32_t ijk[3],
-                                              bool* range_bad) {
+                                              float leaf, float rleaf, uint64_t* key,
+                                              uint32_t ijk[3], bool* range_bad) {
   if (!point_valid(x, y, z)) return false;
-  const bool ok = axis_index(x, o[0], leaf, &ijk[0]) & axis_index(y, o[1], leaf, &ijk[1]) &
-                  axis_index(z, o[2], leaf, &ijk[2]);
+  bool ok;
+  if (rleaf != 0.0f)
+    ok = axis_index_fast(x, o[0], leaf, rleaf, &ijk[0]) &
+         axis_index_fast(y, o[1], leaf, rleaf, &ijk[1]) &
+         axis_index_fast(z, o[2], leaf, rleaf, &ijk[2]);
+  else
+    ok = axis_index(x, o[0], leaf, &ijk[0]) & axis_index(y, o[1], leaf, &ijk[1]) &
+         axis_index(z, o[2], leaf, &ijk[2]);
   if (!ok) {
     *range_bad = true;
     return false;
   }
   *key = morton3(ijk[0], ijk[1], ijk[2]);
   return true;
+}
+
+// Morton key of a point, or false if the point is invalid / out of range (*range_bad
+// set for the latter).
+__device__ __forceinline__ bool point_key(float x, float y, float z, const float o[3],
+                                          float leaf, float rleaf, uint64_t* key,
+                                          bool* range_bad) {
+  uint32_t ijk[3];
+  return point_key_ijk(x, y, z, o, leaf, rleaf, key, ijk, range_bad);
 }
 
 // Split a sort key into (frame, per-frame voxel key).  key_shift == 64: one frame.

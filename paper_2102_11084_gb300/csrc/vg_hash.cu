@@ -99,11 +99,12 @@ __global__ __launch_bounds__(kStreamThreads) void hash_insert_kernel(
     load4(xyz, p0, end, xyz_vec && (start & 3) == 0, v);
     const float o[3] = {sm.org[f][0], sm.org[f][1], sm.org[f][2]};
     const float leaf = sm.leaf[f];
+    const float rleaf = fast_leaf(leaf) ? __fdiv_rn(1.0f, leaf) : 0.0f;
     const float inv_unit = quant_inv_unit(leaf);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       uint64_t local = 0;
-      const bool ok = point_key(v[3 * j], v[3 * j + 1], v[3 * j + 2], o, leaf, &local, &range_bad);
+      const bool ok = point_key(v[3 * j], v[3 * j + 1], v[3 * j + 2], o, leaf, rleaf, &local, &range_bad);
       const uint64_t key = ok ? key_compose(static_cast<uint32_t>(f), local, key_shift) : 0;
       uint32_t slot = kNoSlot;
       const uint32_t vm = __ballot_sync(kFullMask, ok);

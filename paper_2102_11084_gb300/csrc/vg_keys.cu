@@ -125,6 +125,7 @@ __global__ __launch_bounds__(kStreamThreads) void key_kernel(
     load4(xyz, p0, end, xyz_vec && vec, v);
     const float o[3] = {sm.org[f][0], sm.org[f][1], sm.org[f][2]};
     const float leaf = sm.leaf[f];
+    const float rleaf = fast_leaf(leaf) ? __fdiv_rn(1.0f, leaf) : 0.0f;
     uint64_t k[4];
     uint64_t pay[4];
     const float inv_unit = quant_inv_unit(leaf);
@@ -133,7 +134,7 @@ __global__ __launch_bounds__(kStreamThreads) void key_kernel(
       uint64_t local;
       uint32_t ijk[3];
       const bool ok =
-          point_key_ijk(v[3 * j], v[3 * j + 1], v[3 * j + 2], o, leaf, &local, ijk, &range_bad);
+          point_key_ijk(v[3 * j], v[3 * j + 1], v[3 * j + 2], o, leaf, rleaf, &local, ijk, &range_bad);
       k[j] = ok ? key_compose(static_cast<uint32_t>(f), local, key_shift) : kKeySentinel;
       pay[j] = kPayloadInvalid;
       if (ok) {

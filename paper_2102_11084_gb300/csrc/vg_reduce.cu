@@ -60,6 +60,68 @@ __device__ __forceinline__ Seg seg_shfl_up(const Seg& s, int off) {
   return r;
 }
 
+__device__ __forceinline__ Seg seg_shfl_down(const Seg& s, int off) {
+  Seg r;
+  r.h = __shfl_down_sync(kFull, s.h, off);
+  r.a.n = __shfl_down_sync(kFull, s.a.n, off);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) r.a.s[a] = __shfl_down_sync(kFull, s.a.s[a], off);
+  return r;
+}
+
+// Exclusive prefix of tile `tile` over tiles 0..tile-1, by one warp: each round reads the
+// status of 32 predecessors at once (lane l: tile j - l), waits (bounded) until every
+// tile up to the nearest one with an inclusive prefix is ready, and folds them in tile
+// order with a shuffle tree.  Returns the same value to every lane.
+__device__ __forceinline__ Seg warp_lookback(const SegStatus* lb, int tile, int lane,
+                                             uint32_t spin_limit, int* err) {
+  Seg suffix = seg_identity();
+  int j = tile - 1;
+  uint32_t spins = 0;
+  while (true) {
+    const int jt = j - lane;
+    const uint32_t f = jt >= 0 ? ld_acquire(&lb[jt].flag) : 2u;
+    const uint32_t prefix_lanes = __ballot_sync(kFull, f == 2u);
+    const int plane = prefix_lanes ? __ffs(prefix_lanes) - 1 : 31;
+    const uint32_t need = plane == 31 ? kFull : ((2u << plane) - 1u);
+    const uint32_t not_ready = __ballot_sync(kFull, f == 0u) & need;
+    if (not_ready) {
+      if (++spins > spin_limit) {
+        set_error(err, kErrTimeout);
+        return suffix;
+      }
+      if (spins > 64) __nanosleep(64);
+      continue;
+    }
+    Seg v = seg_identity();
+    if (((need >> lane) & 1u) && jt >= 0) {
+      const SegStatus* o = lb + jt;
+      if (f == 1u) {
+        v.h = __ldcg(&o->heads_agg);
+        v.a.n = __ldcg(&o->n_agg);
+        for (int a = 0; a < 3; ++a) v.a.s[a] = __ldcg(&o->s_agg[a]);
+      } else {
+        v.h = __ldcg(&o->heads_incl);
+        v.a.n = __ldcg(&o->n_incl);
+        for (int a = 0; a < 3; ++a) v.a.s[a] = __ldcg(&o->s_incl[a]);
+      }
+    }
+    // lane l holds tile j - l: higher lanes are earlier tiles
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const Seg o = seg_shfl_down(v, off);
+      if (lane + off < 32) v = seg_combine(o, v);
+    }
+    Seg w;
+    w.h = __shfl_sync(kFull, v.h, 0);
+    w.a.n = __shfl_sync(kFull, v.a.n, 0);
+    for (int a = 0; a < 3; ++a) w.a.s[a] = __shfl_sync(kFull, v.a.s[a], 0);
+    suffix = seg_combine(w, suffix);
+    if (prefix_lanes) return suffix;
+    j -= 32;
+  }
+}
+
 // Output rows of one tile, staged in shared memory and written out coalesced.
 struct Stage {
   uint64_t* key;    // [kSegTile + 1]
@@ -222,58 +284,38 @@ __global__ __launch_bounds__(kSegThreads, 2) void segreduce_kernel(
     if (lane == 31) wtot[warp] = incl;
     __syncthreads();
 
-    if (t == 0) {
+    if (warp == 0) {
       Seg agg = seg_identity();
       for (int w = 0; w < kSegThreads / 32; ++w) agg = seg_combine(agg, wtot[w]);
       SegStatus* me = lb + tile;
       Seg excl = seg_identity();
       if (tile == 0) {
-        me->heads_incl = agg.h;
-        me->n_incl = agg.a.n;
-        for (int a = 0; a < 3; ++a) me->s_incl[a] = agg.a.s[a];
-        st_release(&me->flag, 2u);
-      } else {
-        me->heads_agg = agg.h;
-        me->n_agg = agg.a.n;
-        for (int a = 0; a < 3; ++a) me->s_agg[a] = agg.a.s[a];
-        st_release(&me->flag, 1u);
-        Seg suffix = seg_identity();
-        int j = tile - 1;
-        uint32_t spins = 0;
-        while (j >= 0) {
-          const SegStatus* other = lb + j;
-          const uint32_t f = ld_acquire(&other->flag);
-          if (f == 0) {
-            if (++spins > spin_limit) {
-              set_error(err, kErrTimeout);
-              break;
-            }
-            if (spins > 64) __nanosleep(64);
-            continue;
-          }
-          Seg v;
-          if (f == 1u) {
-            v.h = __ldcg(&other->heads_agg);
-            v.a.n = __ldcg(&other->n_agg);
-            for (int a = 0; a < 3; ++a) v.a.s[a] = __ldcg(&other->s_agg[a]);
-          } else {
-            v.h = __ldcg(&other->heads_incl);
-            v.a.n = __ldcg(&other->n_incl);
-            for (int a = 0; a < 3; ++a) v.a.s[a] = __ldcg(&other->s_incl[a]);
-          }
-          suffix = seg_combine(v, suffix);
-          if (f != 1u) break;
-          --j;
+        if (lane == 0) {
+          me->heads_incl = agg.h;
+          me->n_incl = agg.a.n;
+          for (int a = 0; a < 3; ++a) me->s_incl[a] = agg.a.s[a];
+          st_release(&me->flag, 2u);
         }
-        excl = suffix;
-        const Seg inc = seg_combine(excl, agg);
-        me->heads_incl = inc.h;
-        me->n_incl = inc.a.n;
-        for (int a = 0; a < 3; ++a) me->s_incl[a] = inc.a.s[a];
-        st_release(&me->flag, 2u);
+      } else {
+        if (lane == 0) {
+          me->heads_agg = agg.h;
+          me->n_agg = agg.a.n;
+          for (int a = 0; a < 3; ++a) me->s_agg[a] = agg.a.s[a];
+          st_release(&me->flag, 1u);
+        }
+        excl = warp_lookback(lb, tile, lane, spin_limit, err);
+        if (lane == 0) {
+          const Seg inc = seg_combine(excl, agg);
+          me->heads_incl = inc.h;
+          me->n_incl = inc.a.n;
+          for (int a = 0; a < 3; ++a) me->s_incl[a] = inc.a.s[a];
+          st_release(&me->flag, 2u);
+        }
       }
-      s_tile_excl = excl;
-      s_tile_heads = agg.h;
+      if (lane == 0) {
+        s_tile_excl = excl;
+        s_tile_heads = agg.h;
+      }
     }
     __syncthreads();
 
