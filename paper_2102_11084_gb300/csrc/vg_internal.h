@@ -6,18 +6,34 @@
 
 namespace vg {
 
-// Radix sort geometry (8-bit digits, 256 threads x 16 keys per tile).
+// Tile geometry (build-time choices; the defaults are the measured best on GB300).
+#ifndef VG_SORT_ITEMS
+#define VG_SORT_ITEMS 16
+#endif
+#ifndef VG_SORT_MINB
+#define VG_SORT_MINB 2
+#endif
+#ifndef VG_SEG_ITEMS
+#define VG_SEG_ITEMS 8
+#endif
+#ifndef VG_SEG_MINB
+#define VG_SEG_MINB 2
+#endif
+
+// Radix sort geometry (8-bit digits, 256 threads x VG_SORT_ITEMS keys per tile).
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
 constexpr int kMaxPasses = 8;  // 64-bit keys
 constexpr int kSortThreads = 256;
-constexpr int kSortItems = 16;
+constexpr int kSortItems = VG_SORT_ITEMS;
 constexpr int kSortTile = kSortThreads * kSortItems;
+constexpr int kSortMinBlocks = VG_SORT_MINB;
 
-// Segmented reduction geometry (256 threads x 8 keys per tile).
+// Segmented reduction geometry (256 threads x VG_SEG_ITEMS keys per tile).
 constexpr int kSegThreads = 256;
-constexpr int kSegItems = 8;
+constexpr int kSegItems = VG_SEG_ITEMS;
 constexpr int kSegTile = kSegThreads * kSegItems;
+constexpr int kSegMinBlocks = VG_SEG_MINB;
 
 // Streaming kernels (origin, keys, hash insert): 256 threads, 4 points per thread; the
 // cloud is cut into chunks of 1024 points that never cross a frame boundary.

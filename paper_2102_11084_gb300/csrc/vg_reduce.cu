@@ -178,7 +178,7 @@ namespace {
 // block takes tiles from a ticket until none is left.  A launch whose layout was not
 // chosen returns before taking a ticket.
 template <bool kNarrow>
-__global__ __launch_bounds__(kSegThreads, 2) void segreduce_kernel(
+__global__ __launch_bounds__(kSegThreads, kSegMinBlocks) void segreduce_kernel(
     State* st, const FrameState* __restrict__ fs, int nframes, const void* keys0_,
     const void* pay0_, const void* keys1_, const void* pay1_, const float* __restrict__ xyz,
     SegStatus* lb, SegOut out, uint32_t spin_limit, int* err) {

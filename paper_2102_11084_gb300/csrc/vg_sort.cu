@@ -64,7 +64,7 @@ __device__ __forceinline__ void block_excl_scan2(uint32_t a, uint32_t b, uint32_
 // (uint32, uint64 packed offsets) for the narrow one; a launched pass whose layout was not
 // chosen, or that is beyond the needed passes, returns before taking a tile ticket.
 template <typename KeyT, typename PayT, bool kNarrow>
-__global__ __launch_bounds__(kSortThreads, 2) void onesweep_kernel(
+__global__ __launch_bounds__(kSortThreads, kSortMinBlocks) void onesweep_kernel(
     const KeyT* __restrict__ keys_in, const PayT* __restrict__ pay_in,
     KeyT* __restrict__ keys_out, PayT* __restrict__ pay_out, State* st, uint32_t* lb_cur,
     uint32_t* lb_next, int pass, int64_t n_host, int compact_input, uint32_t spin_limit,
