@@ -91,6 +91,21 @@ __device__ __forceinline__ uint32_t compact3(uint64_t x) {
   return static_cast<uint32_t>(x);
 }
 
+// compact3 for keys below 2^32 (11 bits of x and y, 10 of z), with 32-bit operations.
+__device__ __forceinline__ uint32_t compact3_32(uint32_t x) {
+  x &= 0x49249249u;
+  x = (x | (x >> 2)) & 0xc30c30c3u;
+  x = (x | (x >> 4)) & 0x0f00f00fu;
+  x = (x | (x >> 8)) & 0xff0000ffu;
+  x = (x | (x >> 16)) & 0x000007ffu;
+  return x;
+}
+
+// Voxel index on `axis` (0, 1, 2) of a per-frame Morton key.
+__device__ __forceinline__ uint32_t key_axis(uint64_t key, int axis) {
+  return (key >> 32) == 0 ? compact3_32(static_cast<uint32_t>(key) >> axis) : compact3(key >> axis);
+}
+
 __device__ __forceinline__ uint64_t morton3(uint32_t ix, uint32_t iy, uint32_t iz) {
   return spread3(ix) | (spread3(iy) << 1) | (spread3(iz) << 2);
 }
@@ -193,22 +208,22 @@ __device__ __forceinline__ Acc point_acc(uint64_t local, float x, float y, float
                                          const float o[3], float leaf, float inv_unit) {
   Acc a;
   a.n = 1;
-  a.s[0] = quant_offset(x, voxel_corner(compact3(local), o[0], leaf), inv_unit);
-  a.s[1] = quant_offset(y, voxel_corner(compact3(local >> 1), o[1], leaf), inv_unit);
-  a.s[2] = quant_offset(z, voxel_corner(compact3(local >> 2), o[2], leaf), inv_unit);
+  a.s[0] = quant_offset(x, voxel_corner(key_axis(local, 0), o[0], leaf), inv_unit);
+  a.s[1] = quant_offset(y, voxel_corner(key_axis(local, 1), o[1], leaf), inv_unit);
+  a.s[2] = quant_offset(z, voxel_corner(key_axis(local, 2), o[2], leaf), inv_unit);
   return a;
 }
 
-// Centroid of voxel `local` from a sum S in units of leaf/2^20 relative to its corner.
+// Centroid of voxel `local` (edge `leaf`) from n points whose offsets from its corner sum
+// to S, in units of unit_leaf/2^20: c + S * (unit_leaf / (n * 2^20)), one division per
+// voxel.  (unit_leaf = leaf except in the pyramid, whose sums keep the level-0 unit.)
 __device__ __forceinline__ void acc_centroid(uint64_t local, const Acc& a, const float o[3],
-                                             float leaf, float inv_unit, float out[3]) {
-  const float fn = __uint2float_rn(a.n);
-  const uint32_t ii[3] = {compact3(local), compact3(local >> 1), compact3(local >> 2)};
+                                             float leaf, float unit_leaf, float out[3]) {
+  const float scale = __fdiv_rn(unit_leaf, __fmul_rn(__uint2float_rn(a.n), kQuantScale));
 #pragma unroll
   for (int ax = 0; ax < 3; ++ax) {
-    const float c = voxel_corner(ii[ax], o[ax], leaf);
-    const float m = __fdiv_rn(__fdiv_rn(__ll2float_rn(a.s[ax]), fn), inv_unit);
-    out[ax] = __fadd_rn(c, m);
+    const float c = voxel_corner(key_axis(local, ax), o[ax], leaf);
+    out[ax] = __fadd_rn(c, __fmul_rn(__ll2float_rn(a.s[ax]), scale));
   }
 }
 

@@ -217,7 +217,7 @@ __global__ __launch_bounds__(256) void hash_finalize_kernel(
     const float o[3] = {fs[f].origin[0], fs[f].origin[1], fs[f].origin[2]};
     const float leaf = fs[f].leaf;
     float c[3];
-    acc_centroid(local, a, o, leaf, quant_inv_unit(leaf), c);
+    acc_centroid(local, a, o, leaf, leaf, c);
     out.keys[i] = local;
     out.counts[i] = a.n;
     out.centroids[3 * i] = c[0];

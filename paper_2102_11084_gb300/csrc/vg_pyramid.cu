@@ -78,7 +78,7 @@ __global__ __launch_bounds__(kMergeThreads) void pyramid_merge_kernel(
     if (!((headmask >> j) & 1u)) continue;
     const int64_t r = r0 + j;
     const uint64_t pkey = ck[r] >> 3;
-    const uint32_t pi[3] = {compact3(pkey), compact3(pkey >> 1), compact3(pkey >> 2)};
+    const uint32_t pi[3] = {key_axis(pkey, 0), key_axis(pkey, 1), key_axis(pkey, 2)};
     float C[3];
     for (int a = 0; a < 3; ++a) C[a] = voxel_corner(pi[a], o[a], leaf_par);
     Acc acc = acc_zero();
@@ -87,7 +87,7 @@ __global__ __launch_bounds__(kMergeThreads) void pyramid_merge_kernel(
       if ((k >> 3) != pkey) break;
       const uint32_t n = cn[c];
       acc.n += n;
-      const uint32_t ci[3] = {compact3(k), compact3(k >> 1), compact3(k >> 2)};
+      const uint32_t ci[3] = {key_axis(k, 0), key_axis(k, 1), key_axis(k, 2)};
       for (int a = 0; a < 3; ++a) {
         const float cc = voxel_corner(ci[a], o[a], leaf_child);
         const double shift = (double(cc) - double(C[a])) * double(inv_unit0);
@@ -101,7 +101,7 @@ __global__ __launch_bounds__(kMergeThreads) void pyramid_merge_kernel(
       continue;
     }
     float cent[3];
-    acc_centroid(pkey, acc, o, leaf_par, inv_unit0, cent);
+    acc_centroid(pkey, acc, o, leaf_par, leaf0, cent);
     keys[out] = pkey;
     counts[out] = acc.n;
     centroids[3 * out] = cent[0];

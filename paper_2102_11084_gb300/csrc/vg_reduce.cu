@@ -129,20 +129,28 @@ struct Stage {
   float* cent;      // [3 * (kSegTile + 1)]
 };
 
-// Stages voxel v (sort key `key`, sums `a`) at e = v - e0 of this tile.
+// Stages voxel v (sort key `key`, sums `a`) at e = v - e0 of this tile.  o1/leaf1: the
+// frame's origin and leaf when the call has one frame (key_shift == 64).
 __device__ __forceinline__ void emit_voxel(uint32_t v, int64_t e0, uint64_t key, const Acc& a,
                                            const FrameState* fs, uint32_t key_shift,
-                                           const SegOut& out, const Stage& sg, int* err) {
+                                           const float o1[3], float leaf1, const SegOut& out,
+                                           const Stage& sg, int* err) {
   if (int64_t(v) >= out.cap) {
     set_error(err, kErrCapacity);
     return;
   }
-  const uint32_t f = key_frame(key, key_shift);
   const uint64_t local = key_local(key, key_shift);
-  const float o[3] = {fs[f].origin[0], fs[f].origin[1], fs[f].origin[2]};
-  const float leaf = fs[f].leaf;
+  float o[3] = {o1[0], o1[1], o1[2]};
+  float leaf = leaf1;
+  if (key_shift < 64) {
+    const uint32_t f = key_frame(key, key_shift);
+    o[0] = fs[f].origin[0];
+    o[1] = fs[f].origin[1];
+    o[2] = fs[f].origin[2];
+    leaf = fs[f].leaf;
+  }
   float c[3];
-  acc_centroid(local, a, o, leaf, quant_inv_unit(leaf), c);
+  acc_centroid(local, a, o, leaf, leaf, c);
   const int e = static_cast<int>(int64_t(v) - e0);
   sg.key[e] = local;
   sg.count[e] = a.n;
@@ -208,6 +216,8 @@ __global__ __launch_bounds__(kSegThreads, kSegMinBlocks) void segreduce_kernel(
   const KeyT* K = static_cast<const KeyT*>((passes & 1) ? keys1_ : keys0_);
   const PayT* I = static_cast<const PayT*>((passes & 1) ? pay1_ : pay0_);
   (void)xyz;
+  const float o1[3] = {fs[0].origin[0], fs[0].origin[1], fs[0].origin[2]};
+  const float leaf1 = fs[0].leaf;
 
   for (;;) {
     if (t == 0) s_tile = static_cast<int>(atomicAdd(&st->tile_ctr[kMaxPasses], 1u));
@@ -340,7 +350,7 @@ __global__ __launch_bounds__(kSegThreads, kSegMinBlocks) void segreduce_kernel(
       if ((headmask >> j) & 1u) {
         if (gi > 0) {
           const uint64_t pk = j == 0 ? prev0 : k[j - 1];
-          emit_voxel(H - 1, e0, pk, run, fs, key_shift, out, sg, err);
+          emit_voxel(H - 1, e0, pk, run, fs, key_shift, o1, leaf1, out, sg, err);
           mark_frames(out.frame_offsets, key_frame(pk, key_shift), key_frame(k[j], key_shift), H);
         }
         H += 1;
@@ -352,7 +362,7 @@ __global__ __launch_bounds__(kSegThreads, kSegMinBlocks) void segreduce_kernel(
       run.s[2] += q[j][2];
       if (!kNarrow && out.p2v) out.p2v[pi[j]] = static_cast<int32_t>(H - 1);
       if (gi == nitems - 1) {
-        emit_voxel(H - 1, e0, k[j], run, fs, key_shift, out, sg, err);
+        emit_voxel(H - 1, e0, k[j], run, fs, key_shift, o1, leaf1, out, sg, err);
         *out.num_voxels = H;
         mark_frames(out.frame_offsets, key_frame(k[j], key_shift), uint32_t(nframes), H);
       }
