@@ -148,7 +148,7 @@ vg_status run_frames(const float* xyz, const FramesArg& fr, bool from_min, const
     uint32_t* idx1 = reinterpret_cast<uint32_t*>(ws + L.idx1);
     uint32_t* lb_a = reinterpret_cast<uint32_t*>(ws + L.lb_a);
     uint32_t* lb_b = reinterpret_cast<uint32_t*>(ws + L.lb_b);
-    SegStatus* seg_lb = reinterpret_cast<SegStatus*>(ws + L.seg_lb);
+    TileRec* recs = reinterpret_cast<TileRec*>(ws + L.seg_lb);
     const int64_t nn = n < 1 ? 1 : n;
     uint32_t* k32_0 = reinterpret_cast<uint32_t*>(ws + L.keys0);
     uint32_t* k32_1 = k32_0 + nn;
@@ -182,12 +182,11 @@ vg_status run_frames(const float* xyz, const FramesArg& fr, bool from_min, const
       mark(stage++, stream);
     }
     if (e == cudaSuccess)
-      e = launch_segreduce(st, fs, F, keys0, idx0, keys1, idx1, xyz, seg_lb, n, out, spins, err,
-                           stream);
+      e = launch_segreduce(st, fs, F, keys0, idx0, keys1, idx1, xyz, recs, n, out, err, stream);
     mark(stage++, stream);
     if (e == cudaSuccess)
-      e = launch_segreduce_narrow(st, fs, F, k32_0, pay_0, k32_1, pay_1, seg_lb, n, out, spins,
-                                  err, stream);
+      e = launch_segreduce_narrow(st, fs, F, k32_0, pay_0, k32_1, pay_1, recs, n, out, err,
+                                  stream);
     mark(stage++, stream);
     return cuda_status(e);
   }

@@ -8,16 +8,10 @@ namespace vg {
 
 // Tile geometry (build-time choices; the defaults are the measured best on GB300).
 #ifndef VG_SORT_ITEMS
-#define VG_SORT_ITEMS 16
+#define VG_SORT_ITEMS 8
 #endif
 #ifndef VG_SORT_MINB
-#define VG_SORT_MINB 2
-#endif
-#ifndef VG_SEG_ITEMS
-#define VG_SEG_ITEMS 8
-#endif
-#ifndef VG_SEG_MINB
-#define VG_SEG_MINB 2
+#define VG_SORT_MINB 4
 #endif
 
 // Radix sort geometry (8-bit digits, 256 threads x VG_SORT_ITEMS keys per tile).
@@ -29,11 +23,10 @@ constexpr int kSortItems = VG_SORT_ITEMS;
 constexpr int kSortTile = kSortThreads * kSortItems;
 constexpr int kSortMinBlocks = VG_SORT_MINB;
 
-// Segmented reduction geometry (256 threads x VG_SEG_ITEMS keys per tile).
-constexpr int kSegThreads = 256;
-constexpr int kSegItems = VG_SEG_ITEMS;
-constexpr int kSegTile = kSegThreads * kSegItems;
-constexpr int kSegMinBlocks = VG_SEG_MINB;
+// Segmented reduction geometry (256 threads x 4 sorted entries per tile).
+constexpr int kRedThreads = 256;
+constexpr int kRedItems = 4;
+constexpr int kRedTile = kRedThreads * kRedItems;
 
 // Streaming kernels (origin, keys, hash insert): 256 threads, 4 points per thread; the
 // cloud is cut into chunks of 1024 points that never cross a frame boundary.
@@ -84,18 +77,14 @@ struct alignas(256) State {
   uint32_t hist[kMaxPasses][kRadix];
 };
 
-// Segmented-reduction chained-scan record of one tile.
-struct alignas(16) SegStatus {
-  uint32_t flag;
-  uint32_t heads_agg;
-  uint32_t heads_incl;
-  uint32_t n_agg;
-  uint32_t n_incl;
-  uint32_t pad[3];
-  long long s_agg[3];
-  long long pad2;
-  long long s_incl[3];
-  long long pad3;
+// Per-tile record of the segmented reduction: run heads in the tile, the tile's first
+// output row, and the sums of its leading entries (those continuing an earlier run).
+struct alignas(8) TileRec {
+  uint32_t heads;
+  uint32_t vbase;
+  uint32_t lead_n;
+  uint32_t pad;
+  long long lead_s[3];
 };
 
 // Frames of one call.  A single cloud is one frame [0, n) with offsets == nullptr.
@@ -134,7 +123,7 @@ constexpr SortLayout sort_layout(int64_t n, int frames = 1) {
   const int64_t nn = n < 1 ? 1 : n;
   const int64_t ff = frames < 1 ? 1 : frames;
   L.sort_tiles = ceil_div(nn, kSortTile);
-  L.seg_tiles = ceil_div(nn, kSegTile);
+  L.seg_tiles = ceil_div(nn, kRedTile);
   size_t off = 0;
   L.state = off;
   off = align_up(off + sizeof(State), 256);
@@ -143,7 +132,7 @@ constexpr SortLayout sort_layout(int64_t n, int frames = 1) {
   L.lb_a = off;
   off = align_up(off + size_t(L.sort_tiles) * kRadix * sizeof(uint32_t), 256);
   L.seg_lb = off;
-  off = align_up(off + size_t(L.seg_tiles) * sizeof(SegStatus), 256);
+  off = align_up(off + size_t(L.seg_tiles) * sizeof(TileRec), 256);
   L.zero_bytes = off;  // state, frames, pass-0 status rows and segment status
   L.lb_b = off;
   off = align_up(off + size_t(L.sort_tiles) * kRadix * sizeof(uint32_t), 256);
@@ -202,15 +191,13 @@ struct SegOut {
 };
 cudaError_t launch_segreduce(State* st, const FrameState* fs, int nframes,
                              const uint64_t* keys0, const uint32_t* idx0, const uint64_t* keys1,
-                             const uint32_t* idx1, const float* xyz, SegStatus* lb,
-                             int64_t n_max, const SegOut& out, uint32_t spin_limit, int* err,
-                             cudaStream_t stream);
+                             const uint32_t* idx1, const float* xyz, TileRec* recs,
+                             int64_t n_max, const SegOut& out, int* err, cudaStream_t stream);
 // a4 + a5, narrow layout (returns at once unless the narrow layout was chosen).
 cudaError_t launch_segreduce_narrow(State* st, const FrameState* fs, int nframes,
                                     const uint32_t* k0, const uint64_t* p0, const uint32_t* k1,
-                                    const uint64_t* p1, SegStatus* lb, int64_t n_max,
-                                    const SegOut& out, uint32_t spin_limit, int* err,
-                                    cudaStream_t stream);
+                                    const uint64_t* p1, TileRec* recs, int64_t n_max,
+                                    const SegOut& out, int* err, cudaStream_t stream);
 // a2, narrow-capable key kernel: writes either 64-bit keys to keys64 (wide) or 32-bit keys
 // and packed offsets (narrow, when allowed and the sort key fits in 32 bits).
 cudaError_t launch_keys_any(const float* xyz, const FramesArg& fr, bool have_extent, State* st,
