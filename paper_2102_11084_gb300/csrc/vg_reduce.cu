@@ -156,27 +156,27 @@ __global__ __launch_bounds__(kRedThreads) void seg_count_kernel(
 }
 
 // One block of 1024 threads: exclusive scan of the tiles' head counts into vbase, and V.
+// Thread t owns a contiguous run of ceil(ntiles/1024) tiles, so its loads are all in
+// flight at once; one block-wide scan of the 1024 run totals joins them.
 template <bool kNarrow>
 __global__ __launch_bounds__(1024) void seg_scan_kernel(const State* st, TileRec* recs,
                                                         int64_t* num_voxels) {
   __shared__ uint32_t s_tmp[32];
-  __shared__ uint32_t s_carry;
   if ((st->narrow != 0) != kNarrow) return;
   const int64_t ntiles = ceil_div(int64_t(st->nitems), kRedTile);
-  if (threadIdx.x == 0) s_carry = 0;
-  __syncthreads();
-  for (int64_t c = 0; c < ntiles; c += 1024) {
-    const int64_t i = c + threadIdx.x;
-    const uint32_t v = i < ntiles ? recs[i].heads : 0u;
-    uint32_t total;
-    const uint32_t ex = block_excl_scan(v, &total, s_tmp);
-    const uint32_t carry = s_carry;
-    if (i < ntiles) recs[i].vbase = carry + ex;
-    __syncthreads();
-    if (threadIdx.x == 0) s_carry = carry + total;
-    __syncthreads();
+  const int64_t per = ceil_div(ntiles, 1024);
+  const int64_t t0 = int64_t(threadIdx.x) * per;
+  const int64_t t1 = t0 + per < ntiles ? t0 + per : ntiles;
+  uint32_t sum = 0;
+  for (int64_t i = t0; i < t1; ++i) sum += recs[i].heads;
+  uint32_t total;
+  uint32_t run = block_excl_scan(sum, &total, s_tmp);
+  for (int64_t i = t0; i < t1; ++i) {
+    const uint32_t h = recs[i].heads;
+    recs[i].vbase = run;
+    run += h;
   }
-  if (threadIdx.x == 0) *num_voxels = s_carry;
+  if (threadIdx.x == 0) *num_voxels = total;
 }
 
 // Output offsets of frames (f_prev, f_new] start at voxel v.
