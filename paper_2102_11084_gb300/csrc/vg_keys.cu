@@ -115,6 +115,14 @@ __global__ __launch_bounds__(kStreamThreads) void key_kernel(
   uint32_t nvalid = 0;
   unsigned long long kmax = 0;
   bool range_bad = false;
+  // software pipeline: the next chunk's points are loaded while this one is computed
+  float vn[12];
+  if (c0 < c1) {
+    const int f = chunk_frame(sm.cstart, F, c0);
+    const int64_t start = sm.off[f] + int64_t(c0 - sm.cstart[f]) * kChunk;
+    load4(xyz, start + int64_t(threadIdx.x) * kStreamPoints, min(start + kChunk, sm.off[f + 1]),
+          xyz_vec && (start & 3) == 0, vn);
+  }
   for (uint32_t c = c0; c < c1; ++c) {
     const int f = chunk_frame(sm.cstart, F, c);
     const int64_t start = sm.off[f] + int64_t(c - sm.cstart[f]) * kChunk;
@@ -122,7 +130,14 @@ __global__ __launch_bounds__(kStreamThreads) void key_kernel(
     const int64_t p0 = start + int64_t(threadIdx.x) * kStreamPoints;
     const bool vec = (start & 3) == 0;
     float v[12];
-    load4(xyz, p0, end, xyz_vec && vec, v);
+#pragma unroll
+    for (int x = 0; x < 12; ++x) v[x] = vn[x];
+    if (c + 1 < c1) {
+      const int fn = chunk_frame(sm.cstart, F, c + 1);
+      const int64_t sn = sm.off[fn] + int64_t(c + 1 - sm.cstart[fn]) * kChunk;
+      load4(xyz, sn + int64_t(threadIdx.x) * kStreamPoints, min(sn + kChunk, sm.off[fn + 1]),
+            xyz_vec && (sn & 3) == 0, vn);
+    }
     const float o[3] = {sm.org[f][0], sm.org[f][1], sm.org[f][2]};
     const float leaf = sm.leaf[f];
     const float rleaf = fast_leaf(leaf) ? __fdiv_rn(1.0f, leaf) : 0.0f;

@@ -104,10 +104,18 @@ __global__ __launch_bounds__(kRedThreads) void seg_count_kernel(
     const int cnt = static_cast<int>(nitems - base < kRedTile ? nitems - base : kRedTile);
     uint32_t heads = 0;
     int first = kRedTile;
-    for (int li = t; li < cnt; li += kRedThreads) {
+    uint64_t rk[kRedItems], rq[kRedItems];
+#pragma unroll
+    for (int j = 0; j < kRedItems; ++j) {
+      const int li = j * kRedThreads + t;
       const int64_t gi = base + li;
-      const uint64_t k = uint64_t(K[gi]);
-      const bool head = gi == 0 || uint64_t(K[gi - 1]) != k;
+      rk[j] = li < cnt ? uint64_t(K[gi]) : 0ull;
+      rq[j] = (li < cnt && gi > 0) ? uint64_t(K[gi - 1]) : ~rk[j];
+    }
+#pragma unroll
+    for (int j = 0; j < kRedItems; ++j) {
+      const int li = j * kRedThreads + t;
+      const bool head = li < cnt && rk[j] != rq[j];
       heads += head;
       if (head && li < first) first = li;
     }
@@ -219,17 +227,26 @@ __global__ __launch_bounds__(kRedThreads, 2) void seg_reduce_kernel(
     const int cnt = static_cast<int>(nitems - base < kRedTile ? nitems - base : kRedTile);
     const uint32_t vbase = recs[tile].vbase;
     const uint32_t theads = recs[tile].heads;
-    for (int li = t; li < cnt; li += kRedThreads) {
-      const int64_t gi = base + li;
-      const uint64_t k = uint64_t(__ldcs(K + gi));
-      const uint64_t pay = uint64_t(__ldcs(P + gi));
-      skey[li] = k;
-      int q[3];
-      entry_offsets<kNarrow>(k, pay, xyz, fs, key_shift, o1, leaf1, q);
-      sq[li] = q[0];
-      sq[kRedTile + li] = q[1];
-      sq[2 * kRedTile + li] = q[2];
-      if (!kNarrow) sidx[li] = uint32_t(pay);
+    // all of this thread's loads first (kRedItems in flight), then unpack into shared memory
+    uint64_t rk[kRedItems], rp[kRedItems];
+#pragma unroll
+    for (int j = 0; j < kRedItems; ++j) {
+      const int li = j * kRedThreads + t;
+      rk[j] = li < cnt ? uint64_t(__ldcs(K + base + li)) : 0ull;
+      rp[j] = li < cnt ? uint64_t(__ldcs(P + base + li)) : 0ull;
+    }
+#pragma unroll
+    for (int j = 0; j < kRedItems; ++j) {
+      const int li = j * kRedThreads + t;
+      if (li < cnt) {
+        skey[li] = rk[j];
+        int q[3];
+        entry_offsets<kNarrow>(rk[j], rp[j], xyz, fs, key_shift, o1, leaf1, q);
+        sq[li] = q[0];
+        sq[kRedTile + li] = q[1];
+        sq[2 * kRedTile + li] = q[2];
+        if (!kNarrow) sidx[li] = uint32_t(rp[j]);
+      }
     }
     if (t == 0) s_prev = base > 0 ? uint64_t(K[base - 1]) : ~uint64_t(0);
     __syncthreads();
