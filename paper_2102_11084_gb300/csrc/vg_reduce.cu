@@ -195,7 +195,7 @@ __device__ __forceinline__ void mark_frames(int64_t* fo, uint32_t f_prev, uint32
 }
 
 template <bool kNarrow>
-__global__ __launch_bounds__(kRedThreads, 2) void seg_reduce_kernel(
+__global__ __launch_bounds__(kRedThreads, 4) void seg_reduce_kernel(
     const State* st, const FrameState* __restrict__ fs, int nframes, const void* k0_,
     const void* p0_, const void* k1_, const void* p1_, const float* __restrict__ xyz,
     const TileRec* __restrict__ recs, SegOut out, int* err) {

@@ -134,13 +134,9 @@ __global__ __launch_bounds__(kSortThreads, kSortMinBlocks) void onesweep_kernel(
   for (int j = 0; j < kSortItems; ++j) {
     const bool ok = (vmask >> j) & 1u;
     const uint32_t d = static_cast<uint32_t>(uint64_t(key[j]) >> shift) & (kRadix - 1);
-    uint32_t peers = __ballot_sync(kFull, ok);
-#pragma unroll
-    for (int b = 0; b < kRadixBits; ++b) {
-      const bool bit = (d >> b) & 1u;
-      const uint32_t bal = __ballot_sync(kFull, bit);
-      peers &= bit ? bal : ~bal;
-    }
+    const uint32_t vm = __ballot_sync(kFull, ok);
+    uint32_t peers = 0;
+    if (ok) peers = __match_any_sync(vm, d);  // valid lanes of this warp with digit d
     const uint32_t lower = peers & lt;
     uint32_t old = 0;
     if (ok) old = warp_hist[warp][d];
