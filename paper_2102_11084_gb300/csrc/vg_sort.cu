@@ -77,6 +77,7 @@ __global__ __launch_bounds__(kSortThreads, kSortMinBlocks) void onesweep_kernel(
   __shared__ uint64_t sbuf[kSortTile];
   __shared__ uint8_t sdig[kSortTile];
   __shared__ int s_tile;
+  __shared__ int s_next_tile;
   __shared__ uint32_t s_tile_n;
 
   if ((st->narrow != 0) != kNarrow) return;
@@ -91,11 +92,16 @@ __global__ __launch_bounds__(kSortThreads, kSortMinBlocks) void onesweep_kernel(
   const int64_t ntiles = ceil_div(n_items, kSortTile);
   const int shift = pass * kRadixBits;
 
-  for (;;) {  // persistent: tiles from a ticket until none is left
+  // The next digit's histogram is accumulated over all tiles of this block and folded
+  // into the global one once, at exit; the next tile ticket is taken one tile ahead.
+  next_hist[t] = 0;
   if (t == 0) s_tile = static_cast<int>(atomicAdd(&st->tile_ctr[pass], 1u));
   __syncthreads();
-  const int tile = s_tile;
+  int tile = s_tile;
+  for (;;) {  // persistent: tiles from a ticket until none is left
   if (tile >= ntiles) break;
+  __syncthreads();
+  if (t == 0) s_next_tile = static_cast<int>(atomicAdd(&st->tile_ctr[pass], 1u));
   // The next pass uses the other status region; every tile clears its own row of it.
   lb_next[size_t(tile) * kRadix + t] = 0;
   const int64_t tile_base = int64_t(tile) * kSortTile;
@@ -124,7 +130,6 @@ __global__ __launch_bounds__(kSortThreads, kSortMinBlocks) void onesweep_kernel(
     vmask |= uint32_t(ok) << j;
   }
   for (int d = lane; d < kRadix; d += 32) warp_hist[warp][d] = 0;
-  next_hist[t] = 0;
   __syncwarp();
 
   // ---- stable rank of every item among the same digit within its warp ----
@@ -134,9 +139,13 @@ __global__ __launch_bounds__(kSortThreads, kSortMinBlocks) void onesweep_kernel(
   for (int j = 0; j < kSortItems; ++j) {
     const bool ok = (vmask >> j) & 1u;
     const uint32_t d = static_cast<uint32_t>(uint64_t(key[j]) >> shift) & (kRadix - 1);
-    const uint32_t vm = __ballot_sync(kFull, ok);
-    uint32_t peers = 0;
-    if (ok) peers = __match_any_sync(vm, d);  // valid lanes of this warp with digit d
+    uint32_t peers = __ballot_sync(kFull, ok);
+#pragma unroll
+    for (int b = 0; b < kRadixBits; ++b) {
+      const bool bit = (d >> b) & 1u;
+      const uint32_t bal = __ballot_sync(kFull, bit);
+      peers &= bit ? bal : ~bal;
+    }
     const uint32_t lower = peers & lt;
     uint32_t old = 0;
     if (ok) old = warp_hist[warp][d];
@@ -207,10 +216,12 @@ __global__ __launch_bounds__(kSortThreads, kSortMinBlocks) void onesweep_kernel(
     const uint32_t d = sdig[i];
     __stcg(pay_out + gbase[d] + (i - digit_start[d]), spay[i]);
   }
-  if (has_next && pass + 1 < kMaxPasses && next_hist[t])
-    atomicAdd(&st->hist[pass + 1][t], next_hist[t]);
   __syncthreads();
+  tile = s_next_tile;
   }
+  __syncthreads();
+  if (shift + kRadixBits < int(8 * sizeof(KeyT)) && pass + 1 < kMaxPasses && next_hist[t])
+    atomicAdd(&st->hist[pass + 1][t], next_hist[t]);
 }
 
 // Test kernel: one chained-scan wait of tile `tile` on status words nobody publishes; it
