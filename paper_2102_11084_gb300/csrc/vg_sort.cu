@@ -77,7 +77,6 @@ __global__ __launch_bounds__(kSortThreads, kSortMinBlocks) void onesweep_kernel(
   __shared__ uint64_t sbuf[kSortTile];
   __shared__ uint8_t sdig[kSortTile];
   __shared__ int s_tile;
-  __shared__ int s_next_tile;
   __shared__ uint32_t s_tile_n;
 
   if ((st->narrow != 0) != kNarrow) return;
@@ -93,15 +92,15 @@ __global__ __launch_bounds__(kSortThreads, kSortMinBlocks) void onesweep_kernel(
   const int shift = pass * kRadixBits;
 
   // The next digit's histogram is accumulated over all tiles of this block and folded
-  // into the global one once, at exit; the next tile ticket is taken one tile ahead.
+  // into the global one once, at exit.
   next_hist[t] = 0;
+  for (;;) {  // persistent: tiles from a ticket until none is left
+  // (a ticket is taken only when the block can start the tile at once: a tile held
+  // but not started would stall every later tile's look-back)
   if (t == 0) s_tile = static_cast<int>(atomicAdd(&st->tile_ctr[pass], 1u));
   __syncthreads();
-  int tile = s_tile;
-  for (;;) {  // persistent: tiles from a ticket until none is left
+  const int tile = s_tile;
   if (tile >= ntiles) break;
-  __syncthreads();
-  if (t == 0) s_next_tile = static_cast<int>(atomicAdd(&st->tile_ctr[pass], 1u));
   // The next pass uses the other status region; every tile clears its own row of it.
   lb_next[size_t(tile) * kRadix + t] = 0;
   const int64_t tile_base = int64_t(tile) * kSortTile;
@@ -217,7 +216,6 @@ __global__ __launch_bounds__(kSortThreads, kSortMinBlocks) void onesweep_kernel(
     __stcg(pay_out + gbase[d] + (i - digit_start[d]), spay[i]);
   }
   __syncthreads();
-  tile = s_next_tile;
   }
   __syncthreads();
   if (shift + kRadixBits < int(8 * sizeof(KeyT)) && pass + 1 < kMaxPasses && next_hist[t])
