@@ -91,6 +91,16 @@ __device__ __forceinline__ uint32_t compact3(uint64_t x) {
   return static_cast<uint32_t>(x);
 }
 
+// spread3 for indices below 2^11, with 32-bit operations (bit b -> bit 3b, up to bit 30).
+__device__ __forceinline__ uint32_t spread3_32(uint32_t x) {
+  x &= 0x7ffu;
+  x = (x | (x << 16)) & 0x070000ffu;
+  x = (x | (x << 8)) & 0x0700f00fu;
+  x = (x | (x << 4)) & 0x430c30c3u;
+  x = (x | (x << 2)) & 0x49249249u;
+  return x;
+}
+
 // compact3 for keys below 2^32 (11 bits of x and y, 10 of z), with 32-bit operations.
 __device__ __forceinline__ uint32_t compact3_32(uint32_t x) {
   x &= 0x49249249u;
@@ -108,6 +118,23 @@ __device__ __forceinline__ uint32_t key_axis(uint64_t key, int axis) {
 
 __device__ __forceinline__ uint64_t morton3(uint32_t ix, uint32_t iy, uint32_t iz) {
   return spread3(ix) | (spread3(iy) << 1) | (spread3(iz) << 2);
+}
+
+// Validity and voxel indices of a point (no key); *range_bad set when out of range.
+__device__ __forceinline__ bool point_index(float x, float y, float z, const float o[3],
+                                            float leaf, float rleaf, uint32_t ijk[3],
+                                            bool* range_bad) {
+  if (!point_valid(x, y, z)) return false;
+  bool ok;
+  if (rleaf != 0.0f)
+    ok = axis_index_fast(x, o[0], leaf, rleaf, &ijk[0]) &
+         axis_index_fast(y, o[1], leaf, rleaf, &ijk[1]) &
+         axis_index_fast(z, o[2], leaf, rleaf, &ijk[2]);
+  else
+    ok = axis_index(x, o[0], leaf, &ijk[0]) & axis_index(y, o[1], leaf, &ijk[1]) &
+         axis_index(z, o[2], leaf, &ijk[2]);
+  if (!ok) *range_bad = true;
+  return ok;
 }
 
 // point_key that also returns the voxel indices.

@@ -146,10 +146,15 @@ __global__ __launch_bounds__(kStreamThreads) void key_kernel(
     const float inv_unit = quant_inv_unit(leaf);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      uint64_t local;
       uint32_t ijk[3];
-      const bool ok =
-          point_key_ijk(v[3 * j], v[3 * j + 1], v[3 * j + 2], o, leaf, rleaf, &local, ijk, &range_bad);
+      const bool ok = point_index(v[3 * j], v[3 * j + 1], v[3 * j + 2], o, leaf, rleaf, ijk,
+                                  &range_bad);
+      // narrow layout: every key is below 2^32 (checked from the extents), so the indices
+      // have at most 11 bits and the interleave runs on 32-bit words
+      const uint64_t local =
+          narrow ? uint64_t(spread3_32(ijk[0]) | (spread3_32(ijk[1]) << 1) |
+                            (spread3_32(ijk[2]) << 2))
+                 : morton3(ijk[0], ijk[1], ijk[2]);
       k[j] = ok ? key_compose(static_cast<uint32_t>(f), local, key_shift) : kKeySentinel;
       pay[j] = kPayloadInvalid;
       if (ok) {
