@@ -311,8 +311,8 @@ def run_vg(args, rank, world, local):
     stream = torch.cuda.current_stream(dev)
 
     # stage events (profiling hook of the C ABI): one set per timed step
-    # sort path: extent/origin, keys, 8 wide passes, 4 narrow passes, 2 reductions
-    n_stages = 16
+    # sort path: extent/origin, keys, 8 radix passes (the needed ones do work), reduction
+    n_stages = 11
     import ctypes
 
     def call():
@@ -360,8 +360,7 @@ def run_vg(args, rank, world, local):
     nvalid = int(np.isfinite(xyz_np).all(axis=1).sum())
 
     # per-stage device times (ms, mean over steps)
-    stage_names = (["origin", "keys"] + [f"sort_pass{p}" for p in range(8)] +
-                   [f"sort_pass{p}_narrow" for p in range(4)] + ["segreduce", "segreduce_narrow"])
+    stage_names = ["origin", "keys"] + [f"sort_pass{p}" for p in range(8)] + ["segreduce"]
     stage_ms = np.zeros(n_stages)
     for s in ev_sets:
         for i in range(n_stages):
@@ -376,8 +375,8 @@ def run_vg(args, rank, world, local):
         "sort_pass": 24.0 * nvalid,
         "segreduce": (12.0 if narrow else 24.0) * nvalid + 16.0 * V,
     }
-    sort_ms = stage_ms[10:10 + passes] if narrow else stage_ms[2:2 + passes]
-    seg_ms = stage_ms[15] if narrow else stage_ms[14]
+    sort_ms = stage_ms[2:2 + passes]
+    seg_ms = stage_ms[10]
     kern = {
         "origin": (stage_ms[0], algo["origin"], 1),
         "keys": (stage_ms[1], algo["keys"], 1),
@@ -434,7 +433,7 @@ def run_vg(args, rank, world, local):
         del buf
         torch.cuda.empty_cache()
         extra.update(extra_measurements(args, dev))
-    launches_per_step = 1 + 1 + 8 + 4 + 2
+    launches_per_step = 1 + 1 + 8 + 3
     out = {
         "metric": "points/s", "value": world * n / (ms / 1000), "unit": "points/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,

@@ -255,10 +255,10 @@ VG_API size_t vg_downsample_noalloc_scratch_bytes(void);
  * events[0] on its stream before its first kernel and events[k] after stage k, for
  * k = 1 .. min(max_events - 1, number of stages); NULL turns it off.  The events are
  * cudaEvent_t handles owned by the caller.  Stages of the sort path, in order: extent /
- * origin (recorded even when skipped), keys, 8 wide radix passes, 4 narrow radix passes,
- * wide segmented reduction, narrow segmented reduction (the layout the key kernel did not
- * choose returns at once); of the hash path: origin, insert, compaction, 8 radix passes,
- * finalize, point-to-voxel.  Returns the largest number of events a call records (20). */
+ * origin (recorded even when skipped), keys, 8 radix passes (those beyond the key's
+ * significant digits return at once), segmented reduction (count, scan, reduce); of the
+ * hash path: origin, insert, compaction, 8 radix passes, finalize, point-to-voxel.
+ * Returns the largest number of events a call records (20). */
 VG_API int vg_set_stage_events(void** events, int max_events);
 
 /* Test of the bounded waits: runs one chained-scan wait on four device words

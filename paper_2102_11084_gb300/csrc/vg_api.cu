@@ -169,24 +169,17 @@ vg_status run_frames(const float* xyz, const FramesArg& fr, bool from_min, const
     if (e == cudaSuccess)
       e = launch_keys_any(xyz, frn, have_extent, st, fs, keys0, k32_0, pay_0, err, stream);
     mark(stage++, stream);
-    // Both layouts are launched; the kernels of the one the key kernel did not choose
-    // return at once (the choice depends on the largest key, known only on the device).
+    // The layout is chosen on the device (it depends on the largest key); every kernel
+    // below reads it and runs that layout's code.
+    const NarrowBuffers nb{k32_0, pay_0, k32_1, pay_1};
     for (int p = 0; p < kMaxPasses && e == cudaSuccess; ++p) {
       e = launch_sort_pass(st, keys0, idx0, keys1, idx1, lb_a, lb_b, n, p, false, spins, err,
-                           stream);
-      mark(stage++, stream);
-    }
-    for (int p = 0; p < kNarrowPasses && e == cudaSuccess; ++p) {
-      e = launch_sort_pass_narrow(st, k32_0, pay_0, k32_1, pay_1, lb_a, lb_b, n, p, spins, err,
-                                  stream);
+                           stream, &nb);
       mark(stage++, stream);
     }
     if (e == cudaSuccess)
-      e = launch_segreduce(st, fs, F, keys0, idx0, keys1, idx1, xyz, recs, n, out, err, stream);
-    mark(stage++, stream);
-    if (e == cudaSuccess)
-      e = launch_segreduce_narrow(st, fs, F, k32_0, pay_0, k32_1, pay_1, recs, n, out, err,
-                                  stream);
+      e = launch_segreduce(st, fs, F, keys0, idx0, keys1, idx1, xyz, recs, n, out, err, stream,
+                           &nb);
     mark(stage++, stream);
     return cuda_status(e);
   }

@@ -166,18 +166,21 @@ cudaError_t launch_origin(const float* xyz, const FramesArg& fr, State* st, Fram
 // a2: per-point sort keys (frame id above a key_shift-bit Morton field; ~0 = invalid).
 cudaError_t launch_keys(const float* xyz, const FramesArg& fr, bool have_extent, State* st,
                         FrameState* fs, uint64_t* keys, int* err, cudaStream_t stream);
-// a3: one radix pass.  compact_input: pass 0 reads st->nitems compacted keys with their
-// payload from idx0 (hash path) instead of n raw keys with an implicit index.
+// Buffers of the narrow layout (32-bit keys, packed-offset payloads), ping-pong.
+struct NarrowBuffers {
+  uint32_t* k0;
+  uint64_t* p0;
+  uint32_t* k1;
+  uint64_t* p1;
+};
+constexpr int kNarrowPasses = 4;
+// a3: one radix pass of the layout the key kernel chose.  compact_input: pass 0 reads
+// st->nitems compacted keys with their payload from idx0 (hash path, wide layout only)
+// instead of n raw keys with an implicit index.  nb = nullptr: wide layout only.
 cudaError_t launch_sort_pass(State* st, uint64_t* keys0, uint32_t* idx0, uint64_t* keys1,
                              uint32_t* idx1, uint32_t* lb_a, uint32_t* lb_b, int64_t n_max,
                              int pass, bool compact_input, uint32_t spin_limit, int* err,
-                             cudaStream_t stream);
-// a3, narrow layout: 32-bit keys with the packed offsets as payload (returns at once
-// unless the key kernel chose the narrow layout).
-constexpr int kNarrowPasses = 4;
-cudaError_t launch_sort_pass_narrow(State* st, uint32_t* k0, uint64_t* p0, uint32_t* k1,
-                                    uint64_t* p1, uint32_t* lb_a, uint32_t* lb_b, int64_t n_max,
-                                    int pass, uint32_t spin_limit, int* err, cudaStream_t stream);
+                             cudaStream_t stream, const NarrowBuffers* nb = nullptr);
 // a4 + a5: reduce-by-key of the sorted table into key-ordered voxels.
 struct SegOut {
   uint64_t* keys;
@@ -192,12 +195,8 @@ struct SegOut {
 cudaError_t launch_segreduce(State* st, const FrameState* fs, int nframes,
                              const uint64_t* keys0, const uint32_t* idx0, const uint64_t* keys1,
                              const uint32_t* idx1, const float* xyz, TileRec* recs,
-                             int64_t n_max, const SegOut& out, int* err, cudaStream_t stream);
-// a4 + a5, narrow layout (returns at once unless the narrow layout was chosen).
-cudaError_t launch_segreduce_narrow(State* st, const FrameState* fs, int nframes,
-                                    const uint32_t* k0, const uint64_t* p0, const uint32_t* k1,
-                                    const uint64_t* p1, TileRec* recs, int64_t n_max,
-                                    const SegOut& out, int* err, cudaStream_t stream);
+                             int64_t n_max, const SegOut& out, int* err, cudaStream_t stream,
+                             const NarrowBuffers* nb = nullptr);
 // a2, narrow-capable key kernel: writes either 64-bit keys to keys64 (wide) or 32-bit keys
 // and packed offsets (narrow, when allowed and the sort key fits in 32 bits).
 cudaError_t launch_keys_any(const float* xyz, const FramesArg& fr, bool have_extent, State* st,

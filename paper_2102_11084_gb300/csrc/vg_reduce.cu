@@ -80,7 +80,7 @@ __device__ __forceinline__ Acc block_sum_acc(Acc a, Acc* tmp) {
 }
 
 template <bool kNarrow>
-__global__ __launch_bounds__(kRedThreads) void seg_count_kernel(
+__device__ __forceinline__ void seg_count_body(
     const State* st, const FrameState* __restrict__ fs, const void* k0_, const void* p0_,
     const void* k1_, const void* p1_, const float* __restrict__ xyz, TileRec* recs) {
   using KeyT = typename Layout<kNarrow>::KeyT;
@@ -88,7 +88,6 @@ __global__ __launch_bounds__(kRedThreads) void seg_count_kernel(
   __shared__ uint32_t s_heads[kRedThreads / 32];
   __shared__ int s_first[kRedThreads / 32];
   __shared__ Acc s_acc[kRedThreads / 32];
-  if ((st->narrow != 0) != kNarrow) return;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int64_t nitems = st->nitems;
   const int64_t ntiles = ceil_div(nitems, kRedTile);
@@ -166,11 +165,9 @@ __global__ __launch_bounds__(kRedThreads) void seg_count_kernel(
 // One block of 1024 threads: exclusive scan of the tiles' head counts into vbase, and V.
 // Thread t owns a contiguous run of ceil(ntiles/1024) tiles, so its loads are all in
 // flight at once; one block-wide scan of the 1024 run totals joins them.
-template <bool kNarrow>
 __global__ __launch_bounds__(1024) void seg_scan_kernel(const State* st, TileRec* recs,
                                                         int64_t* num_voxels) {
   __shared__ uint32_t s_tmp[32];
-  if ((st->narrow != 0) != kNarrow) return;
   const int64_t ntiles = ceil_div(int64_t(st->nitems), kRedTile);
   const int64_t per = ceil_div(ntiles, 1024);
   const int64_t t0 = int64_t(threadIdx.x) * per;
@@ -195,16 +192,15 @@ __device__ __forceinline__ void mark_frames(int64_t* fo, uint32_t f_prev, uint32
 }
 
 template <bool kNarrow>
-__global__ __launch_bounds__(kRedThreads, 4) void seg_reduce_kernel(
+__device__ __forceinline__ void seg_reduce_body(
     const State* st, const FrameState* __restrict__ fs, int nframes, const void* k0_,
     const void* p0_, const void* k1_, const void* p1_, const float* __restrict__ xyz,
-    const TileRec* __restrict__ recs, SegOut out, int* err) {
+    const TileRec* __restrict__ recs, const SegOut& out, int* err) {
   using KeyT = typename Layout<kNarrow>::KeyT;
   using PayT = typename Layout<kNarrow>::PayT;
   extern __shared__ __align__(16) unsigned char red_smem[];
   __shared__ uint32_t s_tmp[kRedThreads / 32];
   __shared__ uint64_t s_prev;
-  if ((st->narrow != 0) != kNarrow) return;
   uint64_t* skey = reinterpret_cast<uint64_t*>(red_smem);           // [kRedTile]
   uint64_t* gkey = skey + kRedTile;                                 // [kRedTile]
   int* sq = reinterpret_cast<int*>(gkey + kRedTile);                // [3][kRedTile]
@@ -352,54 +348,65 @@ __global__ __launch_bounds__(kRedThreads, 4) void seg_reduce_kernel(
   }
 }
 
+// Pointers of both layouts; the kernels dispatch on the layout the key kernel chose.
+struct RedPtrs {
+  const void* wk0;
+  const void* wp0;
+  const void* wk1;
+  const void* wp1;
+  const void* nk0;
+  const void* np0;
+  const void* nk1;
+  const void* np1;
+};
+
+__global__ __launch_bounds__(kRedThreads) void seg_count_kernel(
+    const State* st, const FrameState* __restrict__ fs, RedPtrs rp, const float* __restrict__ xyz,
+    TileRec* recs) {
+  if (st->narrow)
+    seg_count_body<true>(st, fs, rp.nk0, rp.np0, rp.nk1, rp.np1, xyz, recs);
+  else
+    seg_count_body<false>(st, fs, rp.wk0, rp.wp0, rp.wk1, rp.wp1, xyz, recs);
+}
+
+__global__ __launch_bounds__(kRedThreads, 4) void seg_reduce_kernel(
+    const State* st, const FrameState* __restrict__ fs, int nframes, RedPtrs rp,
+    const float* __restrict__ xyz, const TileRec* __restrict__ recs, SegOut out, int* err) {
+  if (st->narrow)
+    seg_reduce_body<true>(st, fs, nframes, rp.nk0, rp.np0, rp.nk1, rp.np1, xyz, recs, out, err);
+  else
+    seg_reduce_body<false>(st, fs, nframes, rp.wk0, rp.wp0, rp.wk1, rp.wp1, xyz, recs, out, err);
+}
+
 // Bytes of dynamic shared memory of seg_reduce_kernel.
 constexpr size_t kRedSmem = size_t(kRedTile) * (2 * sizeof(uint64_t) + 3 * sizeof(int) +
                                                 2 * sizeof(uint32_t) + 3 * sizeof(float));
 
-template <bool kNarrow>
-cudaError_t launch_reduce_layout(State* st, const FrameState* fs, int nframes, const void* k0,
-                                 const void* p0, const void* k1, const void* p1,
-                                 const float* xyz, TileRec* recs, int64_t n_max,
-                                 const SegOut& out, int* err, cudaStream_t stream) {
-  const int64_t tiles = ceil_div(n_max, kRedTile);
-  const int gc = persistent_grid(reinterpret_cast<const void*>(seg_count_kernel<kNarrow>),
-                                 kRedThreads, 0, tiles);
-  seg_count_kernel<kNarrow><<<gc, kRedThreads, 0, stream>>>(st, fs, k0, p0, k1, p1, xyz, recs);
-  seg_scan_kernel<kNarrow><<<1, 1024, 0, stream>>>(st, recs, out.num_voxels);
-  const int gr = persistent_grid(reinterpret_cast<const void*>(seg_reduce_kernel<kNarrow>),
-                                 kRedThreads, kRedSmem, tiles);
-  seg_reduce_kernel<kNarrow><<<gr, kRedThreads, kRedSmem, stream>>>(
-      st, fs, nframes, k0, p0, k1, p1, xyz, recs, out, err);
-  return cudaGetLastError();
-}
-
 }  // namespace
 
 void warm_reduce_config() {
-  persistent_grid(reinterpret_cast<const void*>(seg_count_kernel<false>), kRedThreads, 0, 1);
-  persistent_grid(reinterpret_cast<const void*>(seg_count_kernel<true>), kRedThreads, 0, 1);
-  persistent_grid(reinterpret_cast<const void*>(seg_reduce_kernel<false>), kRedThreads, kRedSmem,
-                  1);
-  persistent_grid(reinterpret_cast<const void*>(seg_reduce_kernel<true>), kRedThreads, kRedSmem,
-                  1);
+  persistent_grid(reinterpret_cast<const void*>(seg_count_kernel), kRedThreads, 0, 1);
+  persistent_grid(reinterpret_cast<const void*>(seg_reduce_kernel), kRedThreads, kRedSmem, 1);
 }
 
 cudaError_t launch_segreduce(State* st, const FrameState* fs, int nframes,
                              const uint64_t* keys0, const uint32_t* idx0, const uint64_t* keys1,
                              const uint32_t* idx1, const float* xyz, TileRec* recs,
-                             int64_t n_max, const SegOut& out, int* err, cudaStream_t stream) {
+                             int64_t n_max, const SegOut& out, int* err, cudaStream_t stream,
+                             const NarrowBuffers* nb) {
   if (n_max == 0) return cudaSuccess;
-  return launch_reduce_layout<false>(st, fs, nframes, keys0, idx0, keys1, idx1, xyz, recs, n_max,
-                                     out, err, stream);
-}
-
-cudaError_t launch_segreduce_narrow(State* st, const FrameState* fs, int nframes,
-                                    const uint32_t* k0, const uint64_t* p0, const uint32_t* k1,
-                                    const uint64_t* p1, TileRec* recs, int64_t n_max,
-                                    const SegOut& out, int* err, cudaStream_t stream) {
-  if (n_max == 0) return cudaSuccess;
-  return launch_reduce_layout<true>(st, fs, nframes, k0, p0, k1, p1, nullptr, recs, n_max, out,
-                                    err, stream);
+  RedPtrs rp{keys0, idx0, keys1, idx1, nb ? nb->k0 : nullptr, nb ? nb->p0 : nullptr,
+             nb ? nb->k1 : nullptr, nb ? nb->p1 : nullptr};
+  const int64_t tiles = ceil_div(n_max, kRedTile);
+  const int gc = persistent_grid(reinterpret_cast<const void*>(seg_count_kernel), kRedThreads, 0,
+                                 tiles);
+  seg_count_kernel<<<gc, kRedThreads, 0, stream>>>(st, fs, rp, xyz, recs);
+  seg_scan_kernel<<<1, 1024, 0, stream>>>(st, recs, out.num_voxels);
+  const int gr = persistent_grid(reinterpret_cast<const void*>(seg_reduce_kernel), kRedThreads,
+                                 kRedSmem, tiles);
+  seg_reduce_kernel<<<gr, kRedThreads, kRedSmem, stream>>>(st, fs, nframes, rp, xyz, recs, out,
+                                                          err);
+  return cudaGetLastError();
 }
 
 }  // namespace vg

@@ -60,26 +60,38 @@ __device__ __forceinline__ void block_excl_scan2(uint32_t a, uint32_t b, uint32_
   *tb = sb;
 }
 
+// Shared memory of one radix-pass block.
+struct SortSmem {
+  uint32_t warp_hist[kSortThreads / 32][kRadix];
+  uint32_t digit_start[kRadix];
+  uint32_t gbase[kRadix];
+  uint32_t next_hist[kRadix];
+  uint32_t scan_tmp[kSortThreads / 32][2];
+  uint64_t sbuf[kSortTile];
+  uint8_t sdig[kSortTile];
+  int s_tile;
+  uint32_t s_tile_n;
+};
+
 // One radix pass.  KeyT/PayT: (uint64, uint32 point index) for the wide layout, or
-// (uint32, uint64 packed offsets) for the narrow one; a launched pass whose layout was not
-// chosen, or that is beyond the needed passes, returns before taking a tile ticket.
+// (uint32, uint64 packed offsets) for the narrow one.  A pass beyond the needed ones
+// returns before taking a tile ticket.
 template <typename KeyT, typename PayT, bool kNarrow>
-__global__ __launch_bounds__(kSortThreads, kSortMinBlocks) void onesweep_kernel(
+__device__ __forceinline__ void onesweep_body(
     const KeyT* __restrict__ keys_in, const PayT* __restrict__ pay_in,
     KeyT* __restrict__ keys_out, PayT* __restrict__ pay_out, State* st, uint32_t* lb_cur,
     uint32_t* lb_next, int pass, int64_t n_host, int compact_input, uint32_t spin_limit,
-    int* err) {
-  __shared__ uint32_t warp_hist[kSortThreads / 32][kRadix];
-  __shared__ uint32_t digit_start[kRadix];
-  __shared__ uint32_t gbase[kRadix];
-  __shared__ uint32_t next_hist[kRadix];
-  __shared__ uint32_t scan_tmp[kSortThreads / 32][2];
-  __shared__ uint64_t sbuf[kSortTile];
-  __shared__ uint8_t sdig[kSortTile];
-  __shared__ int s_tile;
-  __shared__ uint32_t s_tile_n;
+    int* err, SortSmem& sm) {
+  uint32_t (&warp_hist)[kSortThreads / 32][kRadix] = sm.warp_hist;
+  uint32_t* digit_start = sm.digit_start;
+  uint32_t* gbase = sm.gbase;
+  uint32_t* next_hist = sm.next_hist;
+  uint32_t (&scan_tmp)[kSortThreads / 32][2] = sm.scan_tmp;
+  uint64_t* sbuf = sm.sbuf;
+  uint8_t* sdig = sm.sdig;
+  int& s_tile = sm.s_tile;
+  uint32_t& s_tile_n = sm.s_tile_n;
 
-  if ((st->narrow != 0) != kNarrow) return;
   const int passes = max(1, sort_passes(st->maxkey));
   if (pass >= passes) return;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -222,6 +234,21 @@ __global__ __launch_bounds__(kSortThreads, kSortMinBlocks) void onesweep_kernel(
     atomicAdd(&st->hist[pass + 1][t], next_hist[t]);
 }
 
+// One radix pass of whichever layout the key kernel chose (read on the device).
+__global__ __launch_bounds__(kSortThreads, kSortMinBlocks) void onesweep_kernel(
+    const uint64_t* kw_in, const uint32_t* iw_in, uint64_t* kw_out, uint32_t* iw_out,
+    const uint32_t* kn_in, const uint64_t* pn_in, uint32_t* kn_out, uint64_t* pn_out, State* st,
+    uint32_t* lb_cur, uint32_t* lb_next, int pass, int64_t n_host, int compact_input,
+    uint32_t spin_limit, int* err) {
+  __shared__ SortSmem sm;
+  if (st->narrow)
+    onesweep_body<uint32_t, uint64_t, true>(kn_in, pn_in, kn_out, pn_out, st, lb_cur, lb_next, pass,
+                                            n_host, compact_input, spin_limit, err, sm);
+  else
+    onesweep_body<uint64_t, uint32_t, false>(kw_in, iw_in, kw_out, iw_out, st, lb_cur, lb_next,
+                                             pass, n_host, compact_input, spin_limit, err, sm);
+}
+
 // Test kernel: one chained-scan wait of tile `tile` on status words nobody publishes; it
 // must give up after `limit` polls and record kErrTimeout.
 __global__ void debug_wait_kernel(const uint32_t* status, int tile, uint32_t limit, int* err) {
@@ -239,45 +266,26 @@ cudaError_t launch_debug_wait(const uint32_t* status, int tile, uint32_t limit, 
 cudaError_t launch_sort_pass(State* st, uint64_t* keys0, uint32_t* idx0, uint64_t* keys1,
                              uint32_t* idx1, uint32_t* lb_a, uint32_t* lb_b, int64_t n_max,
                              int pass, bool compact_input, uint32_t spin_limit, int* err,
-                             cudaStream_t stream) {
+                             cudaStream_t stream, const NarrowBuffers* nb) {
   if (n_max == 0) return cudaSuccess;
-  const int tiles = persistent_grid(
-      reinterpret_cast<const void*>(onesweep_kernel<uint64_t, uint32_t, false>), kSortThreads, 0,
-      ceil_div(n_max, kSortTile));
+  const int tiles = persistent_grid(reinterpret_cast<const void*>(onesweep_kernel), kSortThreads,
+                                    0, ceil_div(n_max, kSortTile));
   const bool even = (pass & 1) == 0;
   // pass p reads buffer (p odd ? 1 : 0) and writes the other; pass 0 reads raw keys.
-  const uint64_t* kin = even ? keys0 : keys1;
-  const uint32_t* iin = even ? idx0 : idx1;
-  uint64_t* kout = even ? keys1 : keys0;
-  uint32_t* iout = even ? idx1 : idx0;
-  uint32_t* cur = even ? lb_a : lb_b;
-  uint32_t* nxt = even ? lb_b : lb_a;
   const bool raw = pass == 0 && !compact_input;
-  onesweep_kernel<uint64_t, uint32_t, false><<<tiles, kSortThreads, 0, stream>>>(
-      kin, raw ? nullptr : iin, kout, iout, st, cur, nxt, pass, n_max, compact_input ? 1 : 0,
-      spin_limit, err);
+  const uint32_t* kn_in = nb ? (even ? nb->k0 : nb->k1) : nullptr;
+  const uint64_t* pn_in = nb ? (even ? nb->p0 : nb->p1) : nullptr;
+  uint32_t* kn_out = nb ? (even ? nb->k1 : nb->k0) : nullptr;
+  uint64_t* pn_out = nb ? (even ? nb->p1 : nb->p0) : nullptr;
+  onesweep_kernel<<<tiles, kSortThreads, 0, stream>>>(
+      even ? keys0 : keys1, raw ? nullptr : (even ? idx0 : idx1), even ? keys1 : keys0,
+      even ? idx1 : idx0, kn_in, pn_in, kn_out, pn_out, st, even ? lb_a : lb_b,
+      even ? lb_b : lb_a, pass, n_max, compact_input ? 1 : 0, spin_limit, err);
   return cudaGetLastError();
 }
 
 void warm_sort_config() {
-  persistent_grid(reinterpret_cast<const void*>(onesweep_kernel<uint64_t, uint32_t, false>),
-                  kSortThreads, 0, 1);
-  persistent_grid(reinterpret_cast<const void*>(onesweep_kernel<uint32_t, uint64_t, true>),
-                  kSortThreads, 0, 1);
-}
-
-cudaError_t launch_sort_pass_narrow(State* st, uint32_t* k0, uint64_t* p0, uint32_t* k1,
-                                    uint64_t* p1, uint32_t* lb_a, uint32_t* lb_b, int64_t n_max,
-                                    int pass, uint32_t spin_limit, int* err, cudaStream_t stream) {
-  if (n_max == 0) return cudaSuccess;
-  const int tiles = persistent_grid(
-      reinterpret_cast<const void*>(onesweep_kernel<uint32_t, uint64_t, true>), kSortThreads, 0,
-      ceil_div(n_max, kSortTile));
-  const bool even = (pass & 1) == 0;
-  onesweep_kernel<uint32_t, uint64_t, true><<<tiles, kSortThreads, 0, stream>>>(
-      even ? k0 : k1, even ? p0 : p1, even ? k1 : k0, even ? p1 : p0, st, even ? lb_a : lb_b,
-      even ? lb_b : lb_a, pass, n_max, 0, spin_limit, err);
-  return cudaGetLastError();
+  persistent_grid(reinterpret_cast<const void*>(onesweep_kernel), kSortThreads, 0, 1);
 }
 
 }  // namespace vg
