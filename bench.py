@@ -59,6 +59,28 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x: float, device) -> float:
+    """The slowest replica's value (the job ends when its last rank does); x on one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, device) -> float:
+    """Total over the replicas (points processed by the whole job)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -348,11 +370,8 @@ def run_vg(args, rank, world, local):
         torch.cuda.synchronize()
     vg.lib().vg_set_stage_events(None, 0)
     ms = start.elapsed_time(stop) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.barrier()
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dev)
+    total_points = sum_over_ranks(n, dev)
     err = int(buf.error.item())
     if err:
         raise vg.VGError(err, "timed steps")
@@ -414,10 +433,7 @@ def run_vg(args, rank, world, local):
         stream.synchronize()
         d2h = 8 + v * (8 + 12 + 4)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, dev)
 
     if rank != 0:
         if world > 1:
@@ -435,7 +451,7 @@ def run_vg(args, rank, world, local):
         extra.update(extra_measurements(args, dev))
     launches_per_step = 1 + 1 + 8 + 3
     out = {
-        "metric": "points/s", "value": world * n / (ms / 1000), "unit": "points/s",
+        "metric": "points/s", "value": total_points / (ms / 1000), "unit": "points/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
@@ -453,7 +469,7 @@ def run_vg(args, rank, world, local):
         "sort_passes": passes,
         "layout": "narrow (32-bit keys, packed offsets)" if narrow else "wide (64-bit keys, index)",
         "cpu_baseline": cpu,
-        "e2e": {"value": world * n / e2e_s, "unit": "points/s", "h2d_bytes_per_step": 12 * n,
+        "e2e": {"value": total_points / e2e_s, "unit": "points/s", "h2d_bytes_per_step": 12 * n,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk.summary(),

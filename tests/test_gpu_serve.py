@@ -56,3 +56,29 @@ def test_realtime_trace_latency():
     st = serve.latency_stats(results)
     assert st["requests"] == len(trace)
     assert st["p99_ms"] < 1000.0
+
+
+def test_failed_batch_fails_its_requests_and_server_keeps_serving(monkeypatch):
+    """Host-side fault injection: the first batch's launch raises (as a CUDA launch error
+    would surface); its requests get the exception, later requests are served."""
+    srv = serve.Server(max_points=4 * 160 * 120, max_frames=4, n_slots=2)
+    real_launch = serve._Slot.launch
+    state = {"failed": False}
+
+    def flaky_launch(self, batch):
+        if not state["failed"]:
+            state["failed"] = True
+            raise vg.VGError(vg.Status.CUDA, "injected launch failure")
+        return real_launch(self, batch)
+
+    monkeypatch.setattr(serve._Slot, "launch", flaky_launch)
+    frame = synth.rgbd_frame(160, 120, seed=31)
+    first = srv.submit(0, frame, 0.05)
+    with pytest.raises(vg.VGError):
+        first.result(timeout=60)
+    later = [srv.submit(1, frame, 0.05) for _ in range(6)]
+    results = [f.result(timeout=120) for f in later]
+    srv.close()
+    solo = vg.downsample(torch.from_numpy(frame).cuda(), 0.05)
+    for r in results:
+        assert np.array_equal(r.keys, solo.keys.cpu().numpy().view(np.uint64))
