@@ -63,6 +63,8 @@ def _lib():
             lib.oracle_backward.restype = None
             lib.oracle_centroid_loss.argtypes = [p, i64, p, i64, p]
             lib.oracle_centroid_loss.restype = ctypes.c_double
+            lib.oracle_pose.argtypes = [p, i64, p, p, p]
+            lib.oracle_pose.restype = None
             _LIB = lib
     return _LIB
 
@@ -185,3 +187,23 @@ def downsample_batch(frames, leaves, origins=None):
         o = None if origins is None else origins[f]
         out.append(downsample(x, float(leaves[f]), o))
     return out
+
+
+def pose(xyz, pose_rt=None, z_limits=None) -> np.ndarray:
+    """Reading R12 (Sec. II-C: camera cloud into the global frame, height limit there):
+    p' = R p + t per point in binary32, ((r0 x + r1 y) + r2 z) + t with one rounding per
+    operation; points with p' not finite or z' outside [z_min, z_max] become NaN."""
+    a = _cloud(xyz)
+    out = np.empty_like(a)
+    pr = None if pose_rt is None else np.ascontiguousarray(
+        np.asarray(pose_rt, np.float32).reshape(12))
+    zl = None if z_limits is None else np.ascontiguousarray(
+        np.asarray(z_limits, np.float32).reshape(2))
+    _lib().oracle_pose(_ptr(a), a.shape[0], None if pr is None else _ptr(pr),
+                       None if zl is None else _ptr(zl), _ptr(out))
+    return out
+
+
+def downsample_posed(xyz, leaf: float, pose_rt=None, z_limits=None, origin_xyz=None):
+    """A posed cloud decimated: the plain definition applied to pose(xyz)."""
+    return downsample(pose(xyz, pose_rt, z_limits), leaf, origin_xyz)

@@ -24,7 +24,12 @@
 //   R5  every occupied voxel is output (no minimum count), in ascending key order;
 //   R6  centroid = mean of the raw member points, accumulated in FP64;
 //   R7  pyramid level k+1 = level k merged by key >> 3, count-weighted, in FP64;
-//   R8  backward of L = (1/(3V)) sum_v |c_v - t_v|^2 : dL/dp_i = dL/dc_v(i) / n_v(i).
+//   R8  backward of L = (1/(3V)) sum_v |c_v - t_v|^2 : dL/dp_i = dL/dc_v(i) / n_v(i);
+//   R12 posed clouds (Sec. II-C: camera clouds are taken into the global frame by tf2
+//       and the filter limits the height there): p' = R p + t with R, t row-major
+//       [R|t], each coordinate in binary32 as ((r0 x + r1 y) + r2 z) + t, one rounding
+//       per operation; a point is kept iff p' is finite and z_min <= z' <= z_max; the
+//       kept points are then decimated as any cloud.
 //
 // Build: g++ -O2 -std=c++17 -ffp-contract=off -fno-fast-math -shared -fPIC.
 // Parity status: every function below is pinned by the tests in tests/test_oracle_*.py
@@ -228,6 +233,28 @@ void oracle_backward(const double* grad_centroids, const uint64_t* counts,
 // coordinates with the voxel membership held fixed (point_to_voxel from an
 // oracle_downsample of the FP32 cloud):  L = (1/(3V)) sum_v |c_v - t_v|^2 where
 // c_v is the mean of the member points.  Used for central finite differences.
+// R12: the posed cloud.  Dropped points come out as NaN (R1 then rejects them).
+void oracle_pose(const float* xyz, int64_t n, const float* pose, const float* zlim,
+                 float* out) {
+  const float nan = std::nanf("");
+  for (int64_t i = 0; i < n; ++i) {
+    const float x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
+    float g[3] = {x, y, z};
+    if (pose) {
+      for (int a = 0; a < 3; ++a) {
+        const float* r = pose + 4 * a;
+        float acc = r[0] * x;   // fl(r0 x)
+        acc = acc + r[1] * y;   // fl(acc + fl(r1 y))
+        acc = acc + r[2] * z;   // fl(acc + fl(r2 z))
+        g[a] = acc + r[3];      // fl(acc + t)
+      }
+    }
+    const bool finite = std::isfinite(g[0]) && std::isfinite(g[1]) && std::isfinite(g[2]);
+    const bool in_band = !zlim || (g[2] >= zlim[0] && g[2] <= zlim[1]);
+    for (int a = 0; a < 3; ++a) out[3 * i + a] = finite && in_band ? g[a] : nan;
+  }
+}
+
 double oracle_centroid_loss(const double* xyz, int64_t n, const int32_t* point_to_voxel,
                             int64_t v, const double* targets) {
   std::vector<double> sums(3 * v, 0.0);
