@@ -156,6 +156,32 @@ VG_API vg_status vg_downsample_frames(const float* xyz, int64_t n_total,
                                       size_t workspace_bytes, int flags, vg_stream_t stream);
 
 /*
+ * Posed frames: vg_downsample_frames for clouds given in their sensors' frames.  The
+ * paper's pipeline takes each camera cloud into the global frame (the tf2 step) and the
+ * voxel filter limits the height of the cloud there (Sec. II-C); here both are fused
+ * into the first read of every point, so they cost no extra pass over the cloud:
+ *
+ *   p' = R p + t, each of x', y', z' computed in float32 as ((r0*x + r1*y) + r2*z) + t
+ *   with every product and sum rounded on its own (no fused multiply-add);
+ *   the point is kept iff x', y', z' are finite and z_min <= z' <= z_max.
+ *
+ * Everything else (origin = minimum of the kept points, keys, centroids in the common
+ * frame, outputs, workspace: vg_batch_workspace_bytes) is as in vg_downsample_frames.
+ *
+ *   poses     float32 [n_frames,12] (device) row-major [R|t] of each frame, or NULL for
+ *             the identity.
+ *   z_limits  float32 [n_frames,2] (device) [z_min, z_max] of each frame, or NULL for no
+ *             limit.
+ * Both NULL is exactly vg_downsample_frames.  Misaligned poses/z_limits: VG_ERR_ALIGN.
+ */
+VG_API vg_status vg_downsample_frames_posed(
+    const float* xyz, int64_t n_total, const int64_t* frame_offsets, int n_frames,
+    const float* poses, const float* z_limits, float* origins, const float* leaves,
+    uint64_t* out_keys, float* out_centroids, uint32_t* out_counts, int64_t cap,
+    int64_t* out_frame_offsets, int32_t* out_point_to_voxel, int32_t* out_error, void* workspace,
+    size_t workspace_bytes, int flags, vg_stream_t stream);
+
+/*
  * Batch plan: owns a workspace for up to max_points points in max_frames frames
  * (allocated here, once), the grouping method and grid size, and a CUDA graph of the
  * batched launch sequence.  vg_downsample_batch takes the arguments of

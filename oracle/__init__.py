@@ -65,6 +65,11 @@ def _lib():
             lib.oracle_centroid_loss.restype = ctypes.c_double
             lib.oracle_pose.argtypes = [p, i64, p, p, p]
             lib.oracle_pose.restype = None
+            lib.oracle_voxel_attrs.argtypes = [p, i64, p, ctypes.c_int, i64, p]
+            lib.oracle_voxel_attrs.restype = None
+            lib.oracle_min_count.argtypes = [p, p, p, p, ctypes.c_int, i64, ctypes.c_uint64, p,
+                                             i64]
+            lib.oracle_min_count.restype = i64
             _LIB = lib
     return _LIB
 
@@ -207,3 +212,41 @@ def pose(xyz, pose_rt=None, z_limits=None) -> np.ndarray:
 def downsample_posed(xyz, leaf: float, pose_rt=None, z_limits=None, origin_xyz=None):
     """A posed cloud decimated: the plain definition applied to pose(xyz)."""
     return downsample(pose(xyz, pose_rt, z_limits), leaf, origin_xyz)
+
+
+class AttrDecimation(NamedTuple):
+    keys: np.ndarray          # uint64 [V]
+    centroids: np.ndarray     # float64 [V, 3]
+    counts: np.ndarray        # uint64 [V]
+    attrs: np.ndarray         # float32 [V, C] per-voxel channel means
+    point_to_voxel: np.ndarray  # int32 [N]
+    origin: np.ndarray        # float32 [3]
+
+
+def downsample_attrs(xyz, leaf: float, attrs=None, min_count: int = 1, origin_xyz=None,
+                     pose_rt=None, z_limits=None) -> AttrDecimation:
+    """Readings R13/R14 on top of the (optionally posed) decimation: mean 8-bit
+    attributes per voxel (exact sums, FP64 division, binary32 result) and removal of
+    voxels with fewer than ``min_count`` points."""
+    a = _cloud(xyz)
+    d = downsample_posed(a, leaf, pose_rt, z_limits, origin_xyz) if (
+        pose_rt is not None or z_limits is not None) else downsample(a, leaf, origin_xyz)
+    n, v = a.shape[0], d.keys.shape[0]
+    if attrs is None:
+        at = np.zeros((n, 0), np.uint8)
+    else:
+        at = np.ascontiguousarray(np.asarray(attrs, np.uint8).reshape(n, -1))
+    ch = at.shape[1]
+    p2v = np.ascontiguousarray(d.point_to_voxel.astype(np.int32))
+    out = np.zeros((max(v, 1), max(ch, 1)), np.float32)[:v, :ch].copy()
+    if ch:
+        _lib().oracle_voxel_attrs(_ptr(p2v), n, _ptr(at), ch, v, _ptr(out))
+    keys = d.keys.copy()
+    cents = np.ascontiguousarray(d.centroids.copy())
+    counts = d.counts.copy()
+    if min_count > 1 and v:
+        out = np.ascontiguousarray(out)
+        v = int(_lib().oracle_min_count(_ptr(keys), _ptr(cents), _ptr(counts),
+                                        _ptr(out) if ch else None, ch, v, int(min_count),
+                                        _ptr(p2v), n))
+    return AttrDecimation(keys[:v], cents[:v], counts[:v], out[:v], p2v, d.origin)

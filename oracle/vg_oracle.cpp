@@ -29,7 +29,13 @@
 //       and the filter limits the height there): p' = R p + t with R, t row-major
 //       [R|t], each coordinate in binary32 as ((r0 x + r1 y) + r2 z) + t, one rounding
 //       per operation; a point is kept iff p' is finite and z_min <= z' <= z_max; the
-//       kept points are then decimated as any cloud.
+//       kept points are then decimated as any cloud;
+//   R13 per-voxel attributes (the RGB-D camera's colour, Sec. II-B): the mean of each
+//       8-bit channel over the voxel's points, summed exactly and divided in FP64, then
+//       rounded to binary32;
+//   R14 minimum points per voxel (the PCL voxel filter's option): voxels with fewer
+//       than m points are removed after grouping; the others keep their order, and
+//       their points' point_to_voxel rows follow them (removed voxels' points get -1).
 //
 // Build: g++ -O2 -std=c++17 -ffp-contract=off -fno-fast-math -shared -fPIC.
 // Parity status: every function below is pinned by the tests in tests/test_oracle_*.py
@@ -233,6 +239,43 @@ void oracle_backward(const double* grad_centroids, const uint64_t* counts,
 // coordinates with the voxel membership held fixed (point_to_voxel from an
 // oracle_downsample of the FP32 cloud):  L = (1/(3V)) sum_v |c_v - t_v|^2 where
 // c_v is the mean of the member points.  Used for central finite differences.
+// R13: mean attributes of voxels 0..V-1 from each point's voxel row (p2v, -1 = none).
+void oracle_voxel_attrs(const int32_t* p2v, int64_t n, const uint8_t* attrs, int channels,
+                        int64_t num_voxels, float* out) {
+  std::vector<double> sum(size_t(num_voxels) * channels, 0.0);
+  std::vector<uint64_t> cnt(size_t(num_voxels), 0);
+  for (int64_t i = 0; i < n; ++i) {
+    const int32_t v = p2v[i];
+    if (v < 0) continue;
+    cnt[size_t(v)] += 1;
+    for (int c = 0; c < channels; ++c) sum[size_t(v) * channels + c] += double(attrs[i * channels + c]);
+  }
+  for (int64_t v = 0; v < num_voxels; ++v)
+    for (int c = 0; c < channels; ++c)
+      out[v * channels + c] =
+          cnt[size_t(v)] ? float(sum[size_t(v) * channels + c] / double(cnt[size_t(v)])) : 0.0f;
+}
+
+// R14: removes voxels with fewer than m points, in place and in order; remaps p2v.
+// Returns the new voxel count.
+int64_t oracle_min_count(uint64_t* keys, double* centroids, uint64_t* counts, float* attrs,
+                         int channels, int64_t num_voxels, uint64_t m, int32_t* p2v, int64_t n) {
+  std::vector<int64_t> row(size_t(num_voxels), -1);
+  int64_t w = 0;
+  for (int64_t v = 0; v < num_voxels; ++v) {
+    if (counts[v] < m) continue;
+    row[size_t(v)] = w;
+    keys[w] = keys[v];
+    counts[w] = counts[v];
+    for (int a = 0; a < 3; ++a) centroids[3 * w + a] = centroids[3 * v + a];
+    for (int c = 0; c < channels; ++c) attrs[w * channels + c] = attrs[v * channels + c];
+    ++w;
+  }
+  for (int64_t i = 0; p2v && i < n; ++i)
+    if (p2v[i] >= 0) p2v[i] = int32_t(row[size_t(p2v[i])]);
+  return w;
+}
+
 // R12: the posed cloud.  Dropped points come out as NaN (R1 then rejects them).
 void oracle_pose(const float* xyz, int64_t n, const float* pose, const float* zlim,
                  float* out) {

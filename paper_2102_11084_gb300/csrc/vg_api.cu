@@ -151,7 +151,7 @@ vg_status run_frames(const float* xyz, const FramesArg& fr, bool from_min, const
     TileRec* recs = reinterpret_cast<TileRec*>(ws + L.seg_lb);
     const int64_t nn = n < 1 ? 1 : n;
     uint32_t* k32_0 = reinterpret_cast<uint32_t*>(ws + L.keys0);
-    uint32_t* k32_1 = k32_0 + nn;
+    uint32_t* k32_1 = k32_0 + align_up(size_t(nn), 4);  // 16-byte aligned, like k32_0
     uint64_t* pay_0 = reinterpret_cast<uint64_t*>(ws + L.keys1);
     uint64_t* pay_1 = reinterpret_cast<uint64_t*>(ws + L.idx0);
     int* err = out_error ? reinterpret_cast<int*>(out_error) : &st->error;
@@ -179,7 +179,7 @@ vg_status run_frames(const float* xyz, const FramesArg& fr, bool from_min, const
     }
     if (e == cudaSuccess)
       e = launch_segreduce(st, fs, F, keys0, idx0, keys1, idx1, xyz, recs, n, out, err, stream,
-                           &nb);
+                           &nb, frn.poses);
     mark(stage++, stream);
     return cuda_status(e);
   }
@@ -333,7 +333,22 @@ vg_status vg_downsample_frames(const float* xyz, int64_t n_total, const int64_t*
                                int64_t cap, int64_t* out_frame_offsets,
                                int32_t* out_point_to_voxel, int32_t* out_error, void* workspace,
                                size_t workspace_bytes, int flags, vg_stream_t stream) {
+  return vg_downsample_frames_posed(xyz, n_total, frame_offsets, n_frames, nullptr, nullptr,
+                                    origins, leaves, out_keys, out_centroids, out_counts, cap,
+                                    out_frame_offsets, out_point_to_voxel, out_error, workspace,
+                                    workspace_bytes, flags, stream);
+}
+
+vg_status vg_downsample_frames_posed(const float* xyz, int64_t n_total,
+                                     const int64_t* frame_offsets, int n_frames,
+                                     const float* poses, const float* z_limits, float* origins,
+                                     const float* leaves, uint64_t* out_keys,
+                                     float* out_centroids, uint32_t* out_counts, int64_t cap,
+                                     int64_t* out_frame_offsets, int32_t* out_point_to_voxel,
+                                     int32_t* out_error, void* workspace, size_t workspace_bytes,
+                                     int flags, vg_stream_t stream) {
   if (n_frames < 1 || n_frames > kMaxFrames) return VG_ERR_INVALID_ARG;
+  if (!aligned(poses, 4) || !aligned(z_limits, 4)) return VG_ERR_ALIGN;
   if ((flags & ~(VG_ORIGIN_FROM_MIN | VG_METHOD_MASK | VG_GRID_MASK)) != 0)
     return VG_ERR_INVALID_ARG;
   if ((flags & VG_METHOD_MASK) == VG_METHOD_MASK) return VG_ERR_INVALID_ARG;
@@ -345,7 +360,8 @@ vg_status vg_downsample_frames(const float* xyz, int64_t n_total, const int64_t*
     return VG_ERR_ALIGN;
   const bool from_min = (flags & VG_ORIGIN_FROM_MIN) != 0;
   FramesArg fr{frame_offsets, n_frames, n_total, from_min ? nullptr : origins,
-               from_min ? origins : nullptr, leaves, 0.0f, grid_per_sm_of(flags)};
+               from_min ? origins : nullptr, leaves, 0.0f, grid_per_sm_of(flags), 0, poses,
+               z_limits};
   // V lands in out_frame_offsets[n_frames]; the segmented reduction also writes it there.
   SegOut out{out_keys, out_centroids, out_counts, nullptr, cap, out_frame_offsets + n_frames,
              out_frame_offsets, out_point_to_voxel};

@@ -301,25 +301,94 @@ __device__ __forceinline__ int sort_passes(unsigned long long maxkey) {
 // exclusive prefix of tile `tile`'s value over tiles 0..tile-1.
 __device__ __forceinline__ uint32_t lookback_u32(const uint32_t* status, size_t stride,
                                                  int tile, uint32_t spin_limit, int* err) {
+  // The status words of up to VG_LOOKBACK_WINDOW predecessors are loaded at once (one
+  // round trip to L2 per window instead of per tile) and consumed in tile order until a
+  // prefix or a word not yet published; a window that makes no progress counts as one
+  // poll against spin_limit.
   uint32_t excl = 0;
   int j = tile - 1;
   uint32_t spins = 0;
   while (j >= 0) {
-    const uint32_t s = ld_relaxed(status + size_t(j) * stride);
-    const uint32_t f = s & ~kValueMask;
-    if (f == 0) {
+    uint32_t s[kLookbackWindow];
+#pragma unroll
+    for (int k = 0; k < kLookbackWindow; ++k)
+      s[k] = j - k >= 0 ? ld_relaxed(status + size_t(j - k) * stride) : 0u;
+    int adv = 0;
+    bool found = false, blocked = false;
+#pragma unroll
+    for (int k = 0; k < kLookbackWindow; ++k) {
+      if (!found && !blocked && j - k >= 0) {
+        const uint32_t f = s[k] & ~kValueMask;
+        if (f == 0) {
+          blocked = true;
+        } else {
+          excl += s[k] & kValueMask;
+          ++adv;
+          found = f == kFlagPrefix;
+        }
+      }
+    }
+    if (found) break;
+    j -= adv;
+    if (adv == 0) {
       if (++spins > spin_limit) {
         set_error(err, kErrTimeout);
         break;
       }
       if (spins > 64) __nanosleep(64);
-      continue;
     }
-    excl += s & kValueMask;
-    if (f == kFlagPrefix) break;
-    --j;
   }
   return excl;
+}
+
+// ---- bulk asynchronous copies (TMA unit) completed on a shared-memory mbarrier ------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, uint32_t arrivals) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(arrivals)
+               : "memory");
+}
+// Makes mbarrier initialisation visible to the asynchronous proxy (the bulk-copy unit).
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;\n\tfence.proxy.async.shared::cta;" ::
+                   : "memory");
+}
+// Orders this thread's earlier shared-memory accesses before later bulk copies.
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// One arrival that also announces `bytes` of bulk-copy data for the current phase.
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+// Global -> shared bulk copy; dst, src and bytes must be multiples of 16.
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes,
+                                              unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+// Waits (bounded: `limit` polls) for the phase of parity `parity` to complete.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t parity,
+                                          uint32_t limit) {
+  const uint32_t a = smem_u32(bar);
+  for (uint32_t i = 0; i < limit; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (i > 32) __nanosleep(32);
+  }
+  return false;
 }
 
 // ---- block-wide helpers (256 threads) -------------------------------------------------

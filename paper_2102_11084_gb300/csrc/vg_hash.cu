@@ -73,6 +73,7 @@ __device__ __forceinline__ uint32_t table_add(unsigned long long* tkeys, HashAcc
   return kNoSlot;
 }
 
+template <bool kPosed>
 __global__ __launch_bounds__(kStreamThreads) void hash_insert_kernel(
     const float* __restrict__ xyz, FramesArg fr, int have_extent, State* st, FrameState* fs,
     HashTable tab, uint32_t* __restrict__ point_slot, uint32_t spin_limit, int* err) {
@@ -90,6 +91,8 @@ __global__ __launch_bounds__(kStreamThreads) void hash_insert_kernel(
   uint32_t nvalid = 0;
   unsigned long long kmax = 0;
   bool range_bad = false;
+  Pose P;
+  int pose_f = -1;
   for (uint32_t c = c0; c < c1; ++c) {
     const int f = chunk_frame(sm.cstart, F, c);
     const int64_t start = sm.off[f] + int64_t(c - sm.cstart[f]) * kChunk;
@@ -97,6 +100,14 @@ __global__ __launch_bounds__(kStreamThreads) void hash_insert_kernel(
     const int64_t p0 = start + int64_t(threadIdx.x) * kStreamPoints;
     float v[12];
     load4(xyz, p0, end, xyz_vec && (start & 3) == 0, v);
+    if (kPosed) {
+      if (f != pose_f) {
+        load_pose(fr, f, P);
+        pose_f = f;
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) pose_point(P, v[3 * j], v[3 * j + 1], v[3 * j + 2]);
+    }
     const float o[3] = {sm.org[f][0], sm.org[f][1], sm.org[f][2]};
     const float leaf = sm.leaf[f];
     const float rleaf = fast_leaf(leaf) ? __fdiv_rn(1.0f, leaf) : 0.0f;
@@ -256,8 +267,12 @@ __global__ __launch_bounds__(256) void hash_p2v_kernel(const uint32_t* __restric
 cudaError_t launch_hash_insert(const float* xyz, const FramesArg& fr, bool have_extent, State* st,
                                FrameState* fs, const HashTable& tab, uint32_t* point_slot,
                                uint32_t spin_limit, int* err, cudaStream_t stream) {
-  hash_insert_kernel<<<stream_grid(fr), kStreamThreads, 0, stream>>>(xyz, fr, have_extent ? 1 : 0, st, fs, tab,
-                                                         point_slot, spin_limit, err);
+  if (posed(fr))
+    hash_insert_kernel<true><<<stream_grid(fr), kStreamThreads, 0, stream>>>(
+        xyz, fr, have_extent ? 1 : 0, st, fs, tab, point_slot, spin_limit, err);
+  else
+    hash_insert_kernel<false><<<stream_grid(fr), kStreamThreads, 0, stream>>>(
+        xyz, fr, have_extent ? 1 : 0, st, fs, tab, point_slot, spin_limit, err);
   return cudaGetLastError();
 }
 

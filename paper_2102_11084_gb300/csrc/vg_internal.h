@@ -8,7 +8,7 @@ namespace vg {
 
 // Tile geometry (build-time choices; the defaults are the measured best on GB300).
 #ifndef VG_SORT_ITEMS
-#define VG_SORT_ITEMS 8
+#define VG_SORT_ITEMS 12
 #endif
 #ifndef VG_SORT_MINB
 #define VG_SORT_MINB 4
@@ -41,6 +41,12 @@ constexpr int kMaxFrames = 1024;
 constexpr uint32_t kFlagAggregate = 1u << 30;
 constexpr uint32_t kFlagPrefix = 2u << 30;
 constexpr uint32_t kValueMask = (1u << 30) - 1;
+
+// Predecessor status words a chained-scan wait loads per round trip.
+#ifndef VG_LOOKBACK_WINDOW
+#define VG_LOOKBACK_WINDOW 1
+#endif
+constexpr int kLookbackWindow = VG_LOOKBACK_WINDOW;
 
 // Largest cloud a call accepts: counts live in 30-bit chained-scan values.
 constexpr int64_t kMaxPoints = (int64_t(1) << 30) - 1;
@@ -98,7 +104,13 @@ struct FramesArg {
   float leaf;
   int grid_per_sm;         // blocks per SM of the streaming kernels (0 = default 8)
   int allow_narrow;        // the key kernel may pick the narrow layout (no point_to_voxel)
+  const float* poses;      // device [F,12] row-major [R|t] sensor poses, or nullptr
+  const float* zlims;      // device [F,2] [z_min, z_max] after the pose, or nullptr
 };
+
+// A posed call maps every point into the common frame, p' = R p + t, before anything
+// else reads it, and drops points whose z' leaves [z_min, z_max].
+inline bool posed(const FramesArg& fr) { return fr.poses != nullptr || fr.zlims != nullptr; }
 
 // Grid of the streaming kernels: one block per chunk, at most grid_per_sm blocks per SM.
 int stream_grid(const FramesArg& fr);
@@ -136,8 +148,8 @@ constexpr SortLayout sort_layout(int64_t n, int frames = 1) {
   L.zero_bytes = off;  // state, frames, pass-0 status rows and segment status
   L.lb_b = off;
   off = align_up(off + size_t(L.sort_tiles) * kRadix * sizeof(uint32_t), 256);
-  L.keys0 = off;
-  off = align_up(off + size_t(nn) * sizeof(uint64_t), 256);
+  L.keys0 = off;  // also the two 32-bit key arrays of the narrow layout, 16-byte aligned
+  off = align_up(off + size_t(nn) * sizeof(uint64_t) + 16, 256);
   L.keys1 = off;
   off = align_up(off + size_t(nn) * sizeof(uint64_t), 256);
   L.idx0 = off;
@@ -196,7 +208,7 @@ cudaError_t launch_segreduce(State* st, const FrameState* fs, int nframes,
                              const uint64_t* keys0, const uint32_t* idx0, const uint64_t* keys1,
                              const uint32_t* idx1, const float* xyz, TileRec* recs,
                              int64_t n_max, const SegOut& out, int* err, cudaStream_t stream,
-                             const NarrowBuffers* nb = nullptr);
+                             const NarrowBuffers* nb = nullptr, const float* poses = nullptr);
 // a2, narrow-capable key kernel: writes either 64-bit keys to keys64 (wide) or 32-bit keys
 // and packed offsets (narrow, when allowed and the sort key fits in 32 bits).
 cudaError_t launch_keys_any(const float* xyz, const FramesArg& fr, bool have_extent, State* st,
@@ -244,8 +256,8 @@ constexpr HashLayout hash_layout(int64_t n, int frames = 1) {
   L.zero_bytes = off;
   L.lb_b = off;
   off = align_up(off + size_t(L.sort_tiles) * kRadix * sizeof(uint32_t), 256);
-  L.keys0 = off;
-  off = align_up(off + size_t(nn) * sizeof(uint64_t), 256);
+  L.keys0 = off;  // also the two 32-bit key arrays of the narrow layout, 16-byte aligned
+  off = align_up(off + size_t(nn) * sizeof(uint64_t) + 16, 256);
   L.keys1 = off;
   off = align_up(off + size_t(nn) * sizeof(uint64_t), 256);
   L.idx0 = off;

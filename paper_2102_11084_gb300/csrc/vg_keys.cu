@@ -53,6 +53,7 @@ __device__ __forceinline__ void flush_extent(float mn[3], float mx[3], FrameStat
 }
 
 // a1: per-frame minimum and maximum over the valid points.
+template <bool kPosed>
 __global__ __launch_bounds__(kStreamThreads) void origin_kernel(const float* __restrict__ xyz,
                                                                 FramesArg fr, FrameState* fs,
                                                                 int* err) {
@@ -64,17 +65,23 @@ __global__ __launch_bounds__(kStreamThreads) void origin_kernel(const float* __r
   const bool xyz_vec = (reinterpret_cast<uintptr_t>(xyz) & 15) == 0;
   float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
   int cur = -1;
+  Pose P;
   for (uint32_t c = c0; c < c1; ++c) {
     const int f = chunk_frame(sm.cstart, fr.nframes, c);
     if (f != cur) {
       if (cur >= 0) flush_extent(mn, mx, fs, cur, red);
       cur = f;
+      if (kPosed) load_pose(fr, f, P);
     }
     const int64_t start = sm.off[f] + int64_t(c - sm.cstart[f]) * kChunk;
     const int64_t end = min(start + kChunk, sm.off[f + 1]);
     const int64_t p0 = start + int64_t(threadIdx.x) * kStreamPoints;
     float v[12];
     load4(xyz, p0, end, xyz_vec && (start & 3) == 0, v);
+    if (kPosed) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) pose_point(P, v[3 * j], v[3 * j + 1], v[3 * j + 2]);
+    }
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       if (point_valid(v[3 * j], v[3 * j + 1], v[3 * j + 2])) {
@@ -93,6 +100,7 @@ __global__ __launch_bounds__(kStreamThreads) void origin_kernel(const float* __r
 // digit-0 histogram of the valid keys, the number of valid points and the largest key.
 // Block 0 also publishes every frame's origin and leaf (and the minimum to the caller
 // when the origin is computed) and the key shift.
+template <bool kPosed>
 __global__ __launch_bounds__(kStreamThreads) void key_kernel(
     const float* __restrict__ xyz, FramesArg fr, int have_extent, State* st, FrameState* fs,
     uint64_t* __restrict__ keys, uint32_t* __restrict__ keys32, uint64_t* __restrict__ payload,
@@ -123,6 +131,8 @@ __global__ __launch_bounds__(kStreamThreads) void key_kernel(
     load4(xyz, start + int64_t(threadIdx.x) * kStreamPoints, min(start + kChunk, sm.off[f + 1]),
           xyz_vec && (start & 3) == 0, vn);
   }
+  Pose P;
+  int pose_f = -1;
   for (uint32_t c = c0; c < c1; ++c) {
     const int f = chunk_frame(sm.cstart, F, c);
     const int64_t start = sm.off[f] + int64_t(c - sm.cstart[f]) * kChunk;
@@ -132,6 +142,14 @@ __global__ __launch_bounds__(kStreamThreads) void key_kernel(
     float v[12];
 #pragma unroll
     for (int x = 0; x < 12; ++x) v[x] = vn[x];
+    if (kPosed) {
+      if (f != pose_f) {
+        load_pose(fr, f, P);
+        pose_f = f;
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) pose_point(P, v[3 * j], v[3 * j + 1], v[3 * j + 2]);
+    }
     if (c + 1 < c1) {
       const int fn = chunk_frame(sm.cstart, F, c + 1);
       const int64_t sn = sm.off[fn] + int64_t(c + 1 - sm.cstart[fn]) * kChunk;
@@ -236,7 +254,10 @@ cudaError_t launch_origin(const float* xyz, const FramesArg& fr, State* st, Fram
                           int* err, cudaStream_t stream) {
   (void)st;
   if (fr.n == 0) return cudaSuccess;
-  origin_kernel<<<stream_grid(fr), kStreamThreads, 0, stream>>>(xyz, fr, fs, err);
+  if (posed(fr))
+    origin_kernel<true><<<stream_grid(fr), kStreamThreads, 0, stream>>>(xyz, fr, fs, err);
+  else
+    origin_kernel<false><<<stream_grid(fr), kStreamThreads, 0, stream>>>(xyz, fr, fs, err);
   return cudaGetLastError();
 }
 
@@ -249,8 +270,12 @@ cudaError_t launch_keys_any(const float* xyz, const FramesArg& fr, bool have_ext
                             FrameState* fs, uint64_t* keys64, uint32_t* keys32,
                             uint64_t* payload, int* err, cudaStream_t stream) {
   // Always at least one block: it publishes the origins and leaves the call used.
-  key_kernel<<<stream_grid(fr), kStreamThreads, 0, stream>>>(
-      xyz, fr, have_extent ? 1 : 0, st, fs, keys64, keys32, payload, err);
+  if (posed(fr))
+    key_kernel<true><<<stream_grid(fr), kStreamThreads, 0, stream>>>(
+        xyz, fr, have_extent ? 1 : 0, st, fs, keys64, keys32, payload, err);
+  else
+    key_kernel<false><<<stream_grid(fr), kStreamThreads, 0, stream>>>(
+        xyz, fr, have_extent ? 1 : 0, st, fs, keys64, keys32, payload, err);
   return cudaGetLastError();
 }
 

@@ -10,10 +10,10 @@
 //              leading entries that continue a run begun in an earlier tile (usually
 //              none or a few; the whole tile when it holds no head);
 //   seg_scan   one block: exclusive scan of the head counts = each tile's first row, V;
-//   seg_reduce every run is reduced by the thread holding its head: it reads the run's
-//              entries from shared memory and, if the run crosses the tile end, adds the
-//              leading sums of the following tiles; rows are staged in shared memory and
-//              written out coalesced.
+//   seg_reduce the tile's entries are staged in shared memory and its run heads
+//              compacted in order, so consecutive threads take consecutive voxels: each
+//              sums its run and, if the run crosses the tile end, adds the leading sums
+//              of the following tiles; rows are written out coalesced.
 // Integer sums make the result independent of tiling and of the order of the points.
 // Two layouts: narrow (32-bit keys, packed offsets as payload) and wide (64-bit keys,
 // point index as payload, coordinates gathered; also gives point_to_voxel).  The
@@ -22,6 +22,7 @@
 
 #include "vg_device.cuh"
 #include "vg_internal.h"
+#include "vg_stream.cuh"
 
 namespace vg {
 namespace {
@@ -36,6 +37,7 @@ struct Layout {
 template <bool kNarrow>
 __device__ __forceinline__ void entry_offsets(uint64_t key, uint64_t pay,
                                               const float* __restrict__ xyz,
+                                              const float* __restrict__ poses,
                                               const FrameState* __restrict__ fs,
                                               uint32_t key_shift, const float o1[3],
                                               float leaf1, int q[3]) {
@@ -46,16 +48,25 @@ __device__ __forceinline__ void entry_offsets(uint64_t key, uint64_t pay,
   } else {
     float o[3] = {o1[0], o1[1], o1[2]};
     float leaf = leaf1;
+    const uint32_t f = key_shift < 64 ? key_frame(key, key_shift) : 0u;
     if (key_shift < 64) {
-      const uint32_t f = key_frame(key, key_shift);
       o[0] = fs[f].origin[0];
       o[1] = fs[f].origin[1];
       o[2] = fs[f].origin[2];
       leaf = fs[f].leaf;
     }
     const float* p = xyz + 3 * size_t(uint32_t(pay));
-    const Acc a = point_acc(key_local(key, key_shift), __ldg(p), __ldg(p + 1), __ldg(p + 2), o,
-                            leaf, quant_inv_unit(leaf));
+    float x = __ldg(p), y = __ldg(p + 1), z = __ldg(p + 2);
+    if (poses) {  // the gathered point in the common frame, as the key kernel saw it
+      Pose P;
+      P.rigid = true;
+#pragma unroll
+      for (int i = 0; i < 12; ++i) P.r[i] = __ldg(poses + 12 * f + i);
+      P.zlo = -INFINITY;
+      P.zhi = INFINITY;
+      pose_point(P, x, y, z);
+    }
+    const Acc a = point_acc(key_local(key, key_shift), x, y, z, o, leaf, quant_inv_unit(leaf));
     q[0] = int(a.s[0]);
     q[1] = int(a.s[1]);
     q[2] = int(a.s[2]);
@@ -82,7 +93,8 @@ __device__ __forceinline__ Acc block_sum_acc(Acc a, Acc* tmp) {
 template <bool kNarrow>
 __device__ __forceinline__ void seg_count_body(
     const State* st, const FrameState* __restrict__ fs, const void* k0_, const void* p0_,
-    const void* k1_, const void* p1_, const float* __restrict__ xyz, TileRec* recs) {
+    const void* k1_, const void* p1_, const float* __restrict__ xyz,
+    const float* __restrict__ poses, TileRec* recs) {
   using KeyT = typename Layout<kNarrow>::KeyT;
   using PayT = typename Layout<kNarrow>::PayT;
   __shared__ uint32_t s_heads[kRedThreads / 32];
@@ -140,7 +152,8 @@ __device__ __forceinline__ void seg_count_body(
     for (int li = t; li < fh; li += kRedThreads) {
       const int64_t gi = base + li;
       int q[3];
-      entry_offsets<kNarrow>(uint64_t(K[gi]), uint64_t(P[gi]), xyz, fs, key_shift, o1, leaf1, q);
+      entry_offsets<kNarrow>(uint64_t(K[gi]), uint64_t(P[gi]), xyz, poses, fs, key_shift, o1, leaf1,
+                            q);
       lead.n += 1;
       lead.s[0] += q[0];
       lead.s[1] += q[1];
@@ -195,18 +208,18 @@ template <bool kNarrow>
 __device__ __forceinline__ void seg_reduce_body(
     const State* st, const FrameState* __restrict__ fs, int nframes, const void* k0_,
     const void* p0_, const void* k1_, const void* p1_, const float* __restrict__ xyz,
-    const TileRec* __restrict__ recs, const SegOut& out, int* err) {
+    const float* __restrict__ poses, const TileRec* __restrict__ recs, const SegOut& out,
+    int* err) {
   using KeyT = typename Layout<kNarrow>::KeyT;
   using PayT = typename Layout<kNarrow>::PayT;
-  extern __shared__ __align__(16) unsigned char red_smem[];
+  extern __shared__ __align__(128) unsigned char red_smem[];
   __shared__ uint32_t s_tmp[kRedThreads / 32];
   __shared__ uint64_t s_prev;
   uint64_t* skey = reinterpret_cast<uint64_t*>(red_smem);           // [kRedTile]
-  uint64_t* gkey = skey + kRedTile;                                 // [kRedTile]
-  int* sq = reinterpret_cast<int*>(gkey + kRedTile);                // [3][kRedTile]
+  int* sq = reinterpret_cast<int*>(skey + kRedTile);                // [3][kRedTile]
   uint32_t* sidx = reinterpret_cast<uint32_t*>(sq + 3 * kRedTile);  // [kRedTile]
-  uint32_t* gcnt = sidx + kRedTile;                                 // [kRedTile]
-  float* gcen = reinterpret_cast<float*>(gcnt + kRedTile);          // [3 * kRedTile]
+  uint32_t* hpos = sidx + kRedTile;                                 // [kRedTile + 1]
+  float* gcen = reinterpret_cast<float*>(hpos + kRedTile + 4);      // [3 * kRedTile]
 
   const int t = threadIdx.x;
   const int64_t nitems = st->nitems;
@@ -222,7 +235,7 @@ __device__ __forceinline__ void seg_reduce_body(
     const int64_t base = tile * kRedTile;
     const int cnt = static_cast<int>(nitems - base < kRedTile ? nitems - base : kRedTile);
     const uint32_t vbase = recs[tile].vbase;
-    const uint32_t theads = recs[tile].heads;
+    const int theads = static_cast<int>(recs[tile].heads);
     // all of this thread's loads first (kRedItems in flight), then unpack into shared memory
     uint64_t rk[kRedItems], rp[kRedItems];
 #pragma unroll
@@ -237,7 +250,7 @@ __device__ __forceinline__ void seg_reduce_body(
       if (li < cnt) {
         skey[li] = rk[j];
         int q[3];
-        entry_offsets<kNarrow>(rk[j], rp[j], xyz, fs, key_shift, o1, leaf1, q);
+        entry_offsets<kNarrow>(rk[j], rp[j], xyz, poses, fs, key_shift, o1, leaf1, q);
         sq[li] = q[0];
         sq[kRedTile + li] = q[1];
         sq[2 * kRedTile + li] = q[2];
@@ -247,7 +260,8 @@ __device__ __forceinline__ void seg_reduce_body(
     if (t == 0) s_prev = base > 0 ? uint64_t(K[base - 1]) : ~uint64_t(0);
     __syncthreads();
 
-    // this thread's entries: [t*kRedItems, t*kRedItems + kRedItems)
+    // run heads among this thread's entries [t*kRedItems, t*kRedItems + kRedItems), then
+    // their positions, compacted in order: hpos[r] = first entry of the tile's r-th voxel
     const int first = t * kRedItems;
     uint32_t headmask = 0, mine = 0;
 #pragma unroll
@@ -261,90 +275,277 @@ __device__ __forceinline__ void seg_reduce_body(
       }
     }
     uint32_t unused;
-    const uint32_t rank = block_excl_scan(mine, &unused, s_tmp);  // heads before my entries
-
-    // reduce the runs whose head is here; record point_to_voxel (wide layout)
-    uint32_t cur = vbase + rank - 1;  // voxel of entries before my first head
+    uint32_t r = block_excl_scan(mine, &unused, s_tmp);
 #pragma unroll
-    for (int j = 0; j < kRedItems; ++j) {
-      const int li = first + j;
-      if (li >= cnt) break;
-      if ((headmask >> j) & 1u) {
-        ++cur;
-        const uint64_t key0 = skey[li];
-        Acc run = acc_zero();
-        int e = li;
-        while (e < cnt && skey[e] == key0) {
-          run.n += 1;
-          run.s[0] += sq[e];
-          run.s[1] += sq[kRedTile + e];
-          run.s[2] += sq[2 * kRedTile + e];
-          ++e;
+    for (int j = 0; j < kRedItems; ++j)
+      if ((headmask >> j) & 1u) hpos[r++] = first + j;
+    if (t == 0) hpos[theads] = cnt;
+    __syncthreads();
+
+    // entries before the first head continue the previous tile's last voxel
+    if (!kNarrow && out.p2v) {
+      const int lead_end = static_cast<int>(hpos[0]);
+      for (int li = t; li < lead_end; li += kRedThreads)
+        out.p2v[sidx[li]] = static_cast<int32_t>(vbase) - 1;
+    }
+
+    // one voxel per thread: its run is [hpos[v], hpos[v + 1])
+    for (int v = t; v < theads; v += kRedThreads) {
+      const int e0 = static_cast<int>(hpos[v]), e1 = static_cast<int>(hpos[v + 1]);
+      const uint64_t key0 = skey[e0];
+      const uint32_t cur = vbase + v;
+      Acc run = acc_zero();
+      run.n = uint32_t(e1 - e0);
+      for (int e = e0; e < e1; ++e) {
+        run.s[0] += sq[e];
+        run.s[1] += sq[kRedTile + e];
+        run.s[2] += sq[2 * kRedTile + e];
+      }
+      if (!kNarrow && out.p2v)
+        for (int e = e0; e < e1; ++e) out.p2v[sidx[e]] = static_cast<int32_t>(cur);
+      bool last_run = false;
+      if (e1 == cnt) {  // the run may continue in the following tiles
+        int64_t tt = tile + 1;
+        for (; tt < ntiles; ++tt) {
+          const TileRec& rr = recs[tt];
+          run.n += rr.lead_n;
+          run.s[0] += rr.lead_s[0];
+          run.s[1] += rr.lead_s[1];
+          run.s[2] += rr.lead_s[2];
+          if (rr.heads > 0) break;
         }
-        bool last_run = false;
-        if (e == cnt) {  // the run may continue in the following tiles
-          int64_t tt = tile + 1;
-          for (; tt < ntiles; ++tt) {
-            const TileRec& r = recs[tt];
-            run.n += r.lead_n;
-            run.s[0] += r.lead_s[0];
-            run.s[1] += r.lead_s[1];
-            run.s[2] += r.lead_s[2];
-            if (r.heads > 0) break;
-          }
-          last_run = tt >= ntiles;
+        last_run = tt >= ntiles;
+      }
+      if (int64_t(cur) >= out.cap) {
+        set_error(err, kErrCapacity);
+      } else {
+        const uint64_t local = key_local(key0, key_shift);
+        float o[3] = {o1[0], o1[1], o1[2]};
+        float leaf = leaf1;
+        if (key_shift < 64) {
+          const uint32_t f = key_frame(key0, key_shift);
+          o[0] = fs[f].origin[0];
+          o[1] = fs[f].origin[1];
+          o[2] = fs[f].origin[2];
+          leaf = fs[f].leaf;
         }
-        const uint32_t row = cur - vbase;
-        if (int64_t(cur) >= out.cap) {
-          set_error(err, kErrCapacity);
-        } else {
-          const uint64_t local = key_local(key0, key_shift);
-          float o[3] = {o1[0], o1[1], o1[2]};
-          float leaf = leaf1;
-          if (key_shift < 64) {
-            const uint32_t f = key_frame(key0, key_shift);
-            o[0] = fs[f].origin[0];
-            o[1] = fs[f].origin[1];
-            o[2] = fs[f].origin[2];
-            leaf = fs[f].leaf;
-          }
-          float c[3];
-          acc_centroid(local, run, o, leaf, leaf, c);
-          gkey[row] = local;
-          gcnt[row] = run.n;
-          gcen[3 * row] = c[0];
-          gcen[3 * row + 1] = c[1];
-          gcen[3 * row + 2] = c[2];
-          if (out.sums) {
-            out.sums[3 * size_t(cur)] = run.s[0];
-            out.sums[3 * size_t(cur) + 1] = run.s[1];
-            out.sums[3 * size_t(cur) + 2] = run.s[2];
-          }
-        }
-        if (out.frame_offsets) {
-          const uint32_t fk = key_frame(key0, key_shift);
-          if (base + li > 0) {
-            const uint64_t pk = li == 0 ? s_prev : skey[li - 1];
-            mark_frames(out.frame_offsets, key_frame(pk, key_shift), fk, cur);
-          }
-          if (last_run) mark_frames(out.frame_offsets, fk, uint32_t(nframes), cur + 1);
+        float c[3];
+        acc_centroid(local, run, o, leaf, leaf, c);
+        out.keys[cur] = local;
+        out.counts[cur] = run.n;
+        gcen[3 * v] = c[0];
+        gcen[3 * v + 1] = c[1];
+        gcen[3 * v + 2] = c[2];
+        if (out.sums) {
+          out.sums[3 * size_t(cur)] = run.s[0];
+          out.sums[3 * size_t(cur) + 1] = run.s[1];
+          out.sums[3 * size_t(cur) + 2] = run.s[2];
         }
       }
-      if (!kNarrow && out.p2v) out.p2v[sidx[li]] = static_cast<int32_t>(cur);
+      if (out.frame_offsets) {
+        const uint32_t fk = key_frame(key0, key_shift);
+        if (base + e0 > 0) {
+          const uint64_t pk = e0 == 0 ? s_prev : skey[e0 - 1];
+          mark_frames(out.frame_offsets, key_frame(pk, key_shift), fk, cur);
+        }
+        if (last_run) mark_frames(out.frame_offsets, fk, uint32_t(nframes), cur + 1);
+      }
     }
     __syncthreads();
 
-    // coalesced write-out of this tile's rows [vbase, vbase + theads)
-    const int span = static_cast<int>(theads);
-    for (int r = t; r < span; r += kRedThreads) {
-      if (int64_t(vbase) + r < out.cap) {
-        out.keys[vbase + r] = gkey[r];
-        out.counts[vbase + r] = gcnt[r];
-      }
-    }
-    for (int x = t; x < 3 * span; x += kRedThreads)
+    // coalesced write-out of this tile's centroids [vbase, vbase + theads)
+    for (int x = t; x < 3 * theads; x += kRedThreads)
       if (int64_t(vbase) + x / 3 < out.cap) out.centroids[3 * size_t(vbase) + x] = gcen[x];
     __syncthreads();
+  }
+}
+
+// Narrow layout: the tile's 32-bit keys and packed offsets arrive in shared memory by
+// bulk asynchronous copies (the TMA unit), double-buffered, so the next tile's loads run
+// while this one is reduced; offsets are unpacked where they are summed.
+struct NarrowRedSmem {
+  uint32_t keys[2][kRedTile];
+  unsigned long long pay[2][kRedTile];
+  uint32_t hpos[kRedTile + 4];
+  float gcen[3 * kRedTile];
+  unsigned long long bar[2];
+  TileRec after;  // record of the tile that follows the current one
+};
+
+__device__ __forceinline__ void narrow_issue(NarrowRedSmem& sm, int b, const uint32_t* K,
+                                             const uint64_t* P, int64_t tile) {
+  const int64_t base = tile * kRedTile;
+  mbar_arrive_expect_tx(&sm.bar[b], kRedTile * (sizeof(uint32_t) + sizeof(uint64_t)));
+  bulk_copy_g2s(sm.keys[b], K + base, kRedTile * sizeof(uint32_t), &sm.bar[b]);
+  bulk_copy_g2s(sm.pay[b], P + base, kRedTile * sizeof(uint64_t), &sm.bar[b]);
+}
+
+__device__ __forceinline__ void seg_reduce_narrow(const State* st, const FrameState* __restrict__ fs,
+                                                  int nframes, const uint32_t* __restrict__ K,
+                                                  const uint64_t* __restrict__ P,
+                                                  const TileRec* __restrict__ recs,
+                                                  const SegOut& out, int* err) {
+  extern __shared__ __align__(128) unsigned char red_smem[];
+  NarrowRedSmem& sm = *reinterpret_cast<NarrowRedSmem*>(red_smem);
+  __shared__ uint32_t s_tmp[kRedThreads / 32];
+  const int t = threadIdx.x;
+  const int64_t nitems = st->nitems;
+  const int64_t ntiles = ceil_div(nitems, kRedTile);
+  // Full tiles take the bulk copy (16-byte aligned buffers); a ragged last tile, or
+  // buffers that are not aligned, take plain loads.
+  const bool aligned = ((reinterpret_cast<uintptr_t>(K) | reinterpret_cast<uintptr_t>(P)) & 15) == 0;
+  const int64_t bulk_tiles = aligned ? nitems / kRedTile : 0;
+  const uint32_t key_shift = st->key_shift;
+  const float o1[3] = {fs[0].origin[0], fs[0].origin[1], fs[0].origin[2]};
+  const float leaf1 = fs[0].leaf;
+
+  int64_t tile = blockIdx.x;
+  if (tile >= ntiles) return;
+  if (t == 0) {
+    mbar_init(&sm.bar[0], 1);
+    mbar_init(&sm.bar[1], 1);
+    fence_mbar_init();
+    if (tile < bulk_tiles) narrow_issue(sm, 0, K, P, tile);
+  }
+  __syncthreads();
+  uint32_t phase = 0;  // bit b: parity of buffer b's next completion
+  uint32_t vbase = recs[tile].vbase, theads = recs[tile].heads, lead = recs[tile].lead_n;
+  for (int b = 0; tile < ntiles; tile += gridDim.x, b ^= 1) {
+    const int64_t next = tile + gridDim.x;
+    const int64_t base = tile * kRedTile;
+    const int cnt = static_cast<int>(nitems - base < kRedTile ? nitems - base : kRedTile);
+    if (t == 0 && next < bulk_tiles) {
+      fence_proxy_async();  // this block's reads of the buffer precede the copy into it
+      narrow_issue(sm, b ^ 1, K, P, next);
+    }
+    // records for later: the next tile of this block, and the tile after this one
+    uint32_t nvbase = 0, ntheads = 0, nlead = 0;
+    if (next < ntiles) {
+      nvbase = recs[next].vbase;
+      ntheads = recs[next].heads;
+      nlead = recs[next].lead_n;
+    }
+    TileRec after{};
+    if (t == 0 && tile + 1 < ntiles) after = recs[tile + 1];
+
+    bool ok = true;
+    const uint32_t par = (phase >> b) & 1u;
+    if (tile < bulk_tiles) {
+      ok = mbar_wait(&sm.bar[b], par, kDefaultSpinLimit);
+      phase ^= 1u << b;
+    } else {
+      for (int li = t; li < cnt; li += kRedThreads) {
+        sm.keys[b][li] = K[base + li];
+        sm.pay[b][li] = P[base + li];
+      }
+    }
+    if (__syncthreads_or(!ok)) {  // a copy that never completed: report, drain, stop
+      if (t == 0) {
+        set_error(err, kErrTimeout);
+        mbar_wait(&sm.bar[b], par, kDefaultSpinLimit);
+        if (next < bulk_tiles) mbar_wait(&sm.bar[b ^ 1], (phase >> (b ^ 1)) & 1u, kDefaultSpinLimit);
+      }
+      return;
+    }
+    const uint32_t* kk = sm.keys[b];
+    const unsigned long long* pp = sm.pay[b];
+
+    // run heads among entries [4t, 4t + 4); entry 0 is a head unless the tile opens with
+    // the continuation of an earlier run
+    const int first = t * kRedItems;
+    uint32_t headmask = 0, mine = 0;
+    if (first < cnt) {
+      uint32_t prev = first > 0 ? kk[first - 1] : 0u;
+#pragma unroll
+      for (int j = 0; j < kRedItems; ++j) {
+        const int li = first + j;
+        if (li < cnt) {
+          const uint32_t k = kk[li];
+          const bool head = li == 0 ? (tile == 0 || lead == 0) : k != prev;
+          headmask |= uint32_t(head) << j;
+          mine += head;
+          prev = k;
+        }
+      }
+    }
+    uint32_t unused;
+    uint32_t r = block_excl_scan(mine, &unused, s_tmp);
+#pragma unroll
+    for (int j = 0; j < kRedItems; ++j)
+      if ((headmask >> j) & 1u) sm.hpos[r++] = first + j;
+    if (t == 0) {
+      sm.hpos[theads] = cnt;
+      sm.after = after;
+    }
+    __syncthreads();
+
+    for (int v = t; v < static_cast<int>(theads); v += kRedThreads) {
+      const int e0 = static_cast<int>(sm.hpos[v]), e1 = static_cast<int>(sm.hpos[v + 1]);
+      const uint64_t key0 = kk[e0];
+      const uint32_t cur = vbase + v;
+      Acc run = acc_zero();
+      run.n = uint32_t(e1 - e0);
+      for (int e = e0; e < e1; ++e) {
+        const uint64_t w = pp[e];
+        run.s[0] += unpack_offset(w, 0);
+        run.s[1] += unpack_offset(w, 1);
+        run.s[2] += unpack_offset(w, 2);
+      }
+      bool last_run = false;
+      if (e1 == cnt) {  // the run may continue in the following tiles
+        int64_t tt = tile + 1;
+        for (; tt < ntiles; ++tt) {
+          const TileRec rr = tt == tile + 1 ? sm.after : recs[tt];
+          run.n += rr.lead_n;
+          run.s[0] += rr.lead_s[0];
+          run.s[1] += rr.lead_s[1];
+          run.s[2] += rr.lead_s[2];
+          if (rr.heads > 0) break;
+        }
+        last_run = tt >= ntiles;
+      }
+      if (int64_t(cur) >= out.cap) {
+        set_error(err, kErrCapacity);
+      } else {
+        const uint64_t local = key_local(key0, key_shift);
+        float o[3] = {o1[0], o1[1], o1[2]};
+        float leaf = leaf1;
+        if (key_shift < 64) {
+          const uint32_t f = key_frame(key0, key_shift);
+          o[0] = fs[f].origin[0];
+          o[1] = fs[f].origin[1];
+          o[2] = fs[f].origin[2];
+          leaf = fs[f].leaf;
+        }
+        float c[3];
+        acc_centroid(local, run, o, leaf, leaf, c);
+        out.keys[cur] = local;
+        out.counts[cur] = run.n;
+        sm.gcen[3 * v] = c[0];
+        sm.gcen[3 * v + 1] = c[1];
+        sm.gcen[3 * v + 2] = c[2];
+        if (out.sums) {
+          out.sums[3 * size_t(cur)] = run.s[0];
+          out.sums[3 * size_t(cur) + 1] = run.s[1];
+          out.sums[3 * size_t(cur) + 2] = run.s[2];
+        }
+      }
+      if (out.frame_offsets) {
+        const uint32_t fk = key_frame(key0, key_shift);
+        if (base + e0 > 0) {
+          const uint64_t pk = e0 == 0 ? uint64_t(K[base - 1]) : uint64_t(kk[e0 - 1]);
+          mark_frames(out.frame_offsets, key_frame(pk, key_shift), fk, cur);
+        }
+        if (last_run) mark_frames(out.frame_offsets, fk, uint32_t(nframes), cur + 1);
+      }
+    }
+    __syncthreads();
+    for (int x = t; x < 3 * static_cast<int>(theads); x += kRedThreads)
+      if (int64_t(vbase) + x / 3 < out.cap) out.centroids[3 * size_t(vbase) + x] = sm.gcen[x];
+    __syncthreads();
+    vbase = nvbase;
+    theads = ntheads;
+    lead = nlead;
   }
 }
 
@@ -362,25 +563,32 @@ struct RedPtrs {
 
 __global__ __launch_bounds__(kRedThreads) void seg_count_kernel(
     const State* st, const FrameState* __restrict__ fs, RedPtrs rp, const float* __restrict__ xyz,
-    TileRec* recs) {
+    const float* __restrict__ poses, TileRec* recs) {
   if (st->narrow)
-    seg_count_body<true>(st, fs, rp.nk0, rp.np0, rp.nk1, rp.np1, xyz, recs);
+    seg_count_body<true>(st, fs, rp.nk0, rp.np0, rp.nk1, rp.np1, xyz, poses, recs);
   else
-    seg_count_body<false>(st, fs, rp.wk0, rp.wp0, rp.wk1, rp.wp1, xyz, recs);
+    seg_count_body<false>(st, fs, rp.wk0, rp.wp0, rp.wk1, rp.wp1, xyz, poses, recs);
 }
 
 __global__ __launch_bounds__(kRedThreads, 4) void seg_reduce_kernel(
     const State* st, const FrameState* __restrict__ fs, int nframes, RedPtrs rp,
-    const float* __restrict__ xyz, const TileRec* __restrict__ recs, SegOut out, int* err) {
-  if (st->narrow)
-    seg_reduce_body<true>(st, fs, nframes, rp.nk0, rp.np0, rp.nk1, rp.np1, xyz, recs, out, err);
-  else
-    seg_reduce_body<false>(st, fs, nframes, rp.wk0, rp.wp0, rp.wk1, rp.wp1, xyz, recs, out, err);
+    const float* __restrict__ xyz, const float* __restrict__ poses,
+    const TileRec* __restrict__ recs, SegOut out, int* err) {
+  if (st->narrow) {
+    const bool odd = max(1, sort_passes(st->maxkey)) & 1;
+    seg_reduce_narrow(st, fs, nframes, static_cast<const uint32_t*>(odd ? rp.nk1 : rp.nk0),
+                      static_cast<const uint64_t*>(odd ? rp.np1 : rp.np0), recs, out, err);
+  } else
+    seg_reduce_body<false>(st, fs, nframes, rp.wk0, rp.wp0, rp.wk1, rp.wp1, xyz, poses, recs, out,
+                           err);
 }
 
 // Bytes of dynamic shared memory of seg_reduce_kernel.
-constexpr size_t kRedSmem = size_t(kRedTile) * (2 * sizeof(uint64_t) + 3 * sizeof(int) +
-                                                2 * sizeof(uint32_t) + 3 * sizeof(float));
+constexpr size_t kRedSmemWide = size_t(kRedTile) * (sizeof(uint64_t) + 3 * sizeof(int) +
+                                                    2 * sizeof(uint32_t) + 3 * sizeof(float)) +
+                                4 * sizeof(uint32_t);
+constexpr size_t kRedSmem =
+    kRedSmemWide > sizeof(NarrowRedSmem) ? kRedSmemWide : sizeof(NarrowRedSmem);
 
 }  // namespace
 
@@ -393,19 +601,19 @@ cudaError_t launch_segreduce(State* st, const FrameState* fs, int nframes,
                              const uint64_t* keys0, const uint32_t* idx0, const uint64_t* keys1,
                              const uint32_t* idx1, const float* xyz, TileRec* recs,
                              int64_t n_max, const SegOut& out, int* err, cudaStream_t stream,
-                             const NarrowBuffers* nb) {
+                             const NarrowBuffers* nb, const float* poses) {
   if (n_max == 0) return cudaSuccess;
   RedPtrs rp{keys0, idx0, keys1, idx1, nb ? nb->k0 : nullptr, nb ? nb->p0 : nullptr,
              nb ? nb->k1 : nullptr, nb ? nb->p1 : nullptr};
   const int64_t tiles = ceil_div(n_max, kRedTile);
   const int gc = persistent_grid(reinterpret_cast<const void*>(seg_count_kernel), kRedThreads, 0,
                                  tiles);
-  seg_count_kernel<<<gc, kRedThreads, 0, stream>>>(st, fs, rp, xyz, recs);
+  seg_count_kernel<<<gc, kRedThreads, 0, stream>>>(st, fs, rp, xyz, poses, recs);
   seg_scan_kernel<<<1, 1024, 0, stream>>>(st, recs, out.num_voxels);
   const int gr = persistent_grid(reinterpret_cast<const void*>(seg_reduce_kernel), kRedThreads,
                                  kRedSmem, tiles);
-  seg_reduce_kernel<<<gr, kRedThreads, kRedSmem, stream>>>(st, fs, nframes, rp, xyz, recs, out,
-                                                          err);
+  seg_reduce_kernel<<<gr, kRedThreads, kRedSmem, stream>>>(st, fs, nframes, rp, xyz, poses, recs,
+                                                          out, err);
   return cudaGetLastError();
 }
 

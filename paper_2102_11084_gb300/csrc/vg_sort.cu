@@ -64,18 +64,20 @@ __device__ __forceinline__ void block_excl_scan2(uint32_t a, uint32_t b, uint32_
 struct SortSmem {
   uint32_t warp_hist[kSortThreads / 32][kRadix];
   uint32_t digit_start[kRadix];
-  uint32_t gbase[kRadix];
+  int32_t gofs[kRadix];  // output position of local slot i of digit d: gofs[d] + i
   uint32_t next_hist[kRadix];
   uint32_t scan_tmp[kSortThreads / 32][2];
-  uint64_t sbuf[kSortTile];
-  uint8_t sdig[kSortTile];
+  uint64_t sbuf[kSortTile];  // keys, then payloads, in local (digit) order
+  uint32_t sdst[kSortTile];  // output position of each local slot
   int s_tile;
   uint32_t s_tile_n;
 };
 
 // One radix pass.  KeyT/PayT: (uint64, uint32 point index) for the wide layout, or
 // (uint32, uint64 packed offsets) for the narrow one.  A pass beyond the needed ones
-// returns before taking a tile ticket.
+// returns before taking a tile ticket.  Keys are loaded, ranked and written first; the
+// payloads are loaded only once the keys sit in shared memory (their loads overlap the
+// key write-out), so the ranking holds no payload registers.
 template <typename KeyT, typename PayT, bool kNarrow>
 __device__ __forceinline__ void onesweep_body(
     const KeyT* __restrict__ keys_in, const PayT* __restrict__ pay_in,
@@ -84,24 +86,24 @@ __device__ __forceinline__ void onesweep_body(
     int* err, SortSmem& sm) {
   uint32_t (&warp_hist)[kSortThreads / 32][kRadix] = sm.warp_hist;
   uint32_t* digit_start = sm.digit_start;
-  uint32_t* gbase = sm.gbase;
+  int32_t* gofs = sm.gofs;
   uint32_t* next_hist = sm.next_hist;
   uint32_t (&scan_tmp)[kSortThreads / 32][2] = sm.scan_tmp;
   uint64_t* sbuf = sm.sbuf;
-  uint8_t* sdig = sm.sdig;
+  uint32_t* sdst = sm.sdst;
   int& s_tile = sm.s_tile;
   uint32_t& s_tile_n = sm.s_tile_n;
 
   const int passes = max(1, sort_passes(st->maxkey));
   if (pass >= passes) return;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  // Pass 0 of the sort path reads all n raw entries (invalid rows are dropped: sentinel
-  // key in the wide layout, flagged payload in the narrow one); every other pass, and
-  // pass 0 of compacted input, reads st->nitems entries.
+  // Pass 0 of the sort path reads all n raw entries and drops the invalid rows (sentinel
+  // keys); every other pass, and pass 0 of compacted input, reads st->nitems entries.
   const bool raw = pass == 0 && !compact_input;
   const int64_t n_items = raw ? n_host : int64_t(st->nitems);
   const int64_t ntiles = ceil_div(n_items, kSortTile);
   const int shift = pass * kRadixBits;
+  const bool has_next = shift + kRadixBits < int(8 * sizeof(KeyT));
 
   // The next digit's histogram is accumulated over all tiles of this block and folded
   // into the global one once, at exit.
@@ -116,28 +118,21 @@ __device__ __forceinline__ void onesweep_body(
   // The next pass uses the other status region; every tile clears its own row of it.
   lb_next[size_t(tile) * kRadix + t] = 0;
   const int64_t tile_base = int64_t(tile) * kSortTile;
+  // item j of lane l (warp-striped): tile_base + warp * 32 * kSortItems + j * 32 + l
+  const int64_t my_base = tile_base + warp * (32 * kSortItems) + lane;
 
-  // ---- load (warp-striped: item j of lane l is tile_base + warp*512 + j*32 + l) ----
+  // ---- keys ----
   KeyT key[kSortItems];
-  PayT pay[kSortItems];
   uint32_t vmask = 0;
 #pragma unroll
   for (int j = 0; j < kSortItems; ++j) {
-    const int64_t i = tile_base + warp * (32 * kSortItems) + j * 32 + lane;
+    const int64_t i = my_base + j * 32;
     const bool in = i < n_items;
     key[j] = in ? __ldcs(keys_in + i) : KeyT(0);
     bool ok = in;
-    if (kNarrow) {
-      pay[j] = in ? __ldcs(pay_in + i) : PayT(0);
-      if (raw) ok = ok && !(uint64_t(pay[j]) & kPayloadInvalid);
-    } else {
-      if (raw) {
-        ok = ok && uint64_t(key[j]) != kSentinel;
-        pay[j] = static_cast<PayT>(i);
-      } else {
-        pay[j] = in ? __ldcs(pay_in + i) : PayT(0);
-      }
-    }
+    // raw rows: the sentinel key (all ones, in either width) marks an invalid point; the
+    // narrow layout is chosen only when no valid key can be all ones
+    if (raw) ok = ok && key[j] != KeyT(kSentinel);
     vmask |= uint32_t(ok) << j;
   }
   for (int d = lane; d < kRadix; d += 32) warp_hist[warp][d] = 0;
@@ -191,7 +186,7 @@ __device__ __forceinline__ void onesweep_body(
     st_relaxed(my, kFlagPrefix | ((excl + tile_count) & kValueMask));
   }
   digit_start[t] = local_excl;
-  gbase[t] = global_excl + excl;
+  gofs[t] = static_cast<int32_t>(global_excl + excl) - static_cast<int32_t>(local_excl);
   if (t == 0) s_tile_n = tile_total;
   __syncthreads();
 
@@ -206,13 +201,23 @@ __device__ __forceinline__ void onesweep_body(
     }
   }
   __syncthreads();
+  // payload loads, in flight while the keys are written out
+  PayT pay[kSortItems];
+#pragma unroll
+  for (int j = 0; j < kSortItems; ++j) {
+    const int64_t i = my_base + j * 32;
+    if (!kNarrow && raw)
+      pay[j] = static_cast<PayT>(i);
+    else
+      pay[j] = ((vmask >> j) & 1u) ? __ldcs(pay_in + i) : PayT(0);
+  }
   const uint32_t tile_n = s_tile_n;
-  const bool has_next = shift + kRadixBits < int(8 * sizeof(KeyT));
   for (uint32_t i = t; i < tile_n; i += kSortThreads) {
     const KeyT k = skey[i];
     const uint32_t d = static_cast<uint32_t>(uint64_t(k) >> shift) & (kRadix - 1);
-    sdig[i] = static_cast<uint8_t>(d);
-    __stcg(keys_out + gbase[d] + (i - digit_start[d]), k);
+    const uint32_t dst = static_cast<uint32_t>(gofs[d] + static_cast<int32_t>(i));
+    sdst[i] = dst;
+    __stcg(keys_out + dst, k);
     if (has_next)
       atomicAdd(&next_hist[static_cast<uint32_t>(uint64_t(k) >> (shift + kRadixBits)) & (kRadix - 1)],
                 1u);
@@ -223,14 +228,11 @@ __device__ __forceinline__ void onesweep_body(
   for (int j = 0; j < kSortItems; ++j)
     if ((vmask >> j) & 1u) spay[rank[j]] = pay[j];
   __syncthreads();
-  for (uint32_t i = t; i < tile_n; i += kSortThreads) {
-    const uint32_t d = sdig[i];
-    __stcg(pay_out + gbase[d] + (i - digit_start[d]), spay[i]);
-  }
+  for (uint32_t i = t; i < tile_n; i += kSortThreads) __stcg(pay_out + sdst[i], spay[i]);
   __syncthreads();
   }
   __syncthreads();
-  if (shift + kRadixBits < int(8 * sizeof(KeyT)) && pass + 1 < kMaxPasses && next_hist[t])
+  if (has_next && pass + 1 < kMaxPasses && next_hist[t])
     atomicAdd(&st->hist[pass + 1][t], next_hist[t]);
 }
 

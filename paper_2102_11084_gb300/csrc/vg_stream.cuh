@@ -13,7 +13,43 @@ struct ChunkSmem {
   float org[kMaxFrames][3];
   float leaf[kMaxFrames];
   uint32_t bits[kStreamThreads / 32];
+  unsigned long long kmax[kStreamThreads / 32];
 };
+
+// Pose and height limits of one frame (registers of a posed streaming kernel).
+struct Pose {
+  float r[12];  // row-major [R|t]
+  float zlo, zhi;
+  bool rigid;   // false: identity pose (only the height limits apply)
+};
+
+__device__ __forceinline__ void load_pose(const FramesArg& fr, int f, Pose& P) {
+  P.rigid = fr.poses != nullptr;
+#pragma unroll
+  for (int i = 0; i < 12; ++i) P.r[i] = P.rigid ? __ldg(fr.poses + 12 * f + i) : 0.0f;
+  P.zlo = fr.zlims ? __ldg(fr.zlims + 2 * f) : -INFINITY;
+  P.zhi = fr.zlims ? __ldg(fr.zlims + 2 * f + 1) : INFINITY;
+}
+
+// p' = R p + t in FP32, each product and sum rounded on its own in the order
+// ((r0 x + r1 y) + r2 z) + t (no fused multiply-add); a point whose z' is outside
+// [zlo, zhi] (or not a number) becomes NaN, i.e. invalid.
+__device__ __forceinline__ void pose_point(const Pose& P, float& x, float& y, float& z) {
+  float g[3] = {x, y, z};
+  if (P.rigid) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const float* r = P.r + 4 * a;
+      g[a] = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(r[0], x), __fmul_rn(r[1], y)),
+                                 __fmul_rn(r[2], z)),
+                       r[3]);
+    }
+  }
+  const bool keep = g[2] >= P.zlo && g[2] <= P.zhi;
+  x = keep ? g[0] : NAN;
+  y = keep ? g[1] : NAN;
+  z = keep ? g[2] : NAN;
+}
 
 // Contiguous chunk range of this block.
 __device__ __forceinline__ void block_range(uint32_t T, uint32_t* c0, uint32_t* c1) {
@@ -32,6 +68,7 @@ __device__ __forceinline__ uint32_t frame_prologue(const FramesArg& fr, bool hav
   const int F = fr.nframes;
   // per-frame origin and leaf; bits of the largest key of each frame
   uint32_t bits = 0;
+  unsigned long long kmax = 0;  // largest per-frame key bound (Morton code of the maxima)
   bool bad_leaf = false;
   for (int f = threadIdx.x; f < F; f += kStreamThreads) {
     const float leaf = fr.leaves ? fr.leaves[f] : fr.leaf;
@@ -63,16 +100,28 @@ __device__ __forceinline__ uint32_t frame_prologue(const FramesArg& fr, bool hav
       const uint64_t m = ok ? morton3(ii[0], ii[1], ii[2]) : ~0ull >> 1;
       const uint32_t b = m ? 64u - __clzll(static_cast<long long>(m)) : 0u;
       bits = b > bits ? b : bits;
+      kmax = m > kmax ? m : kmax;
     }
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int off = 16; off; off >>= 1) bits = max(bits, __shfl_xor_sync(kFullMask, bits, off));
-  if (lane == 0) sm.bits[warp] = bits;
+  for (int off = 16; off; off >>= 1) {
+    bits = max(bits, __shfl_xor_sync(kFullMask, bits, off));
+    const unsigned long long o = __shfl_xor_sync(kFullMask, kmax, off);
+    kmax = o > kmax ? o : kmax;
+  }
+  if (lane == 0) {
+    sm.bits[warp] = bits;
+    sm.kmax[warp] = kmax;
+  }
   if (__syncthreads_or(bad_leaf) && threadIdx.x == 0 && blockIdx.x == 0)
     set_error(err, kErrInvalidArg);
   uint32_t maxbits = 0;
-  for (int w = 0; w < kStreamThreads / 32; ++w) maxbits = max(maxbits, sm.bits[w]);
+  unsigned long long maxkey = 0;
+  for (int w = 0; w < kStreamThreads / 32; ++w) {
+    maxbits = max(maxbits, sm.bits[w]);
+    maxkey = sm.kmax[w] > maxkey ? sm.kmax[w] : maxkey;
+  }
   uint32_t key_shift = 64, total_bits = maxbits;
   if (F > 1) {
     key_shift = maxbits;
@@ -80,8 +129,12 @@ __device__ __forceinline__ uint32_t frame_prologue(const FramesArg& fr, bool hav
     total_bits = key_shift + fbits;
     if (total_bits > 63 && threadIdx.x == 0 && blockIdx.x == 0) set_error(err, kErrRange);
   }
-  // The narrow layout needs the largest key known in advance (the extents) and <= 32 bits.
-  const bool nar = fr.allow_narrow && have_extent && total_bits <= 32;
+  // The narrow layout needs the largest key known in advance (the extents), below
+  // 0xffffffff: a 32-bit key of all ones then marks an invalid row by itself.  Morton codes
+  // grow with each index, so the code of the per-axis maxima bounds every key of a frame.
+  const uint64_t key_bound =
+      F > 1 ? ((uint64_t(F - 1) << key_shift) | ((uint64_t(1) << key_shift) - 1)) : maxkey;
+  const bool nar = fr.allow_narrow && have_extent && total_bits <= 32 && key_bound < 0xffffffffull;
   if (narrow) *narrow = nar;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     st->key_shift = key_shift;

@@ -19,6 +19,9 @@ them:
 * ``batch_frames`` -- 64 frames of uneven size (each a seeded subset, in pixel
   order, of a 1280 x 720 frame) with a per-frame leaf from {0.02, 0.05, 0.1} m.
 * ``serving_trace`` -- Poisson arrivals of 640 x 480 frames from many sensors.
+* ``sensor_poses`` -- camera-to-map poses [R|t] of a depth camera on a mobile robot
+  (optical axis horizontal, random heading, lens 0.8-1.2 m above the floor, position
+  inside the 40 x 40 m map) and the height band kept in the map frame.
 
 All randomness comes from numpy's PCG64 with explicit seeds.
 """
@@ -248,3 +251,24 @@ def random_cloud(n: int, seed: int = 0, *, extent: float = 2.0, nan_frac: float 
         pts[idx[k:k + j], rng.integers(3, size=j)] = np.where(rng.uniform(size=j) < 0.5,
                                                                np.inf, -np.inf)
     return pts
+
+
+def sensor_poses(n_frames: int, seed: int = 2, *, band=(0.05, 2.0)):
+    """Camera-to-map poses, float32 [F, 3, 4] row-major [R|t], and height bands [F, 2].
+
+    The camera's optical frame (x right, y down, z forward) is mounted level on a robot
+    at a random heading: map = Rz(yaw) @ M @ optical + t, with M taking forward to map x,
+    right to map -y and down to map -z; t = (x, y, h), x, y uniform in [0, 40] m and the
+    lens height h uniform in [0.8, 1.2] m.  Every frame keeps heights ``band`` (metres
+    above the floor, in the map frame)."""
+    rng = _rng(seed)
+    M = np.array([[0.0, 0.0, 1.0], [-1.0, 0.0, 0.0], [0.0, -1.0, 0.0]])
+    out = np.zeros((n_frames, 3, 4), np.float32)
+    for f in range(n_frames):
+        yaw = rng.uniform(0.0, 2.0 * np.pi)
+        c, s_ = np.cos(yaw), np.sin(yaw)
+        rz = np.array([[c, -s_, 0.0], [s_, c, 0.0], [0.0, 0.0, 1.0]])
+        out[f, :, :3] = rz @ M
+        out[f, :, 3] = (rng.uniform(0, 40), rng.uniform(0, 40), rng.uniform(0.8, 1.2))
+    bands = np.tile(np.asarray(band, np.float32), (n_frames, 1))
+    return out, bands

@@ -13,6 +13,7 @@ import threading
 from enum import IntEnum
 from typing import NamedTuple, Optional
 
+import numpy as np
 import torch
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -72,6 +73,12 @@ _SIGS = {
                               ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int,
                               ctypes.c_void_p], ctypes.c_int),
+    "vg_downsample_frames_posed": ([ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int,
+                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p], ctypes.c_int),
     "vg_plan_create": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_int], ctypes.c_int),
     "vg_plan_destroy": ([ctypes.c_void_p], ctypes.c_int),
     "vg_plan_configure": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_int], ctypes.c_int),
@@ -214,13 +221,21 @@ class Decimation(NamedTuple):
 
 
 def downsample(xyz: torch.Tensor, leaf: float, origin: Optional[torch.Tensor] = None, *,
-               method="sort", point_to_voxel: bool = False,
+               method="sort", point_to_voxel: bool = False, pose=None, z_limits=None,
                stream: Optional[torch.cuda.Stream] = None) -> Decimation:
     """Voxel-grid decimation of one cloud: centroid per occupied voxel, key order.
 
-    ``origin`` None means the per-axis minimum of the valid points.  Synchronises the
-    stream once to read V and the device error word.
+    ``origin`` None means the per-axis minimum of the valid points.  ``pose`` ([3,4]
+    [R|t]) and ``z_limits`` ([z_min, z_max]) first take the cloud into the common frame
+    and drop points outside the height band (vg_downsample_frames_posed).  Synchronises
+    the stream once to read V and the device error word.
     """
+    if pose is not None or z_limits is not None:
+        fr = downsample_frames([xyz], [leaf], None if origin is None else [origin],
+                               method=method, point_to_voxel=point_to_voxel,
+                               poses=None if pose is None else [pose],
+                               z_limits=None if z_limits is None else [z_limits], stream=stream)
+        return Decimation(fr.keys, fr.centroids, fr.counts, fr.origins[0], fr.point_to_voxel)
     xyz = _cuda_cloud(xyz)
     n = xyz.shape[0]
     org = None
@@ -313,15 +328,31 @@ def _frame_inputs(frames, leaves, origins, device):
     return _cuda_cloud(xyz), off_t, F, lv, og
 
 
+def _per_frame(values, F: int, width: int, device) -> Optional[torch.Tensor]:
+    if values is None:
+        return None
+    if isinstance(values, (list, tuple)) and values and isinstance(values[0], torch.Tensor):
+        values = torch.stack([v.to(device=device, dtype=torch.float32).reshape(-1)
+                              for v in values])
+    elif not isinstance(values, torch.Tensor):
+        values = np.asarray([np.asarray(v, np.float32) for v in values], np.float32)
+    return torch.as_tensor(values, dtype=torch.float32).reshape(F, width).to(device).contiguous()
+
+
 def downsample_frames(frames, leaves, origins=None, *, method="sort", point_to_voxel=False,
-                      grid_per_sm: int = 0, stream: Optional[torch.cuda.Stream] = None) -> Frames:
+                      grid_per_sm: int = 0, poses=None, z_limits=None,
+                      stream: Optional[torch.cuda.Stream] = None) -> Frames:
     """vg_downsample_frames: every frame decimated as it would be alone, in one call.
 
     ``frames`` is a list of float32 [N_f, 3] CUDA tensors or a tuple (xyz [N,3], offsets).
-    ``origins`` None means each frame's minimum.  Synchronises once to read the offsets.
+    ``origins`` None means each frame's minimum.  ``poses`` ([F,3,4] sensor poses [R|t])
+    and ``z_limits`` ([F,2]) make it vg_downsample_frames_posed.  Synchronises once to
+    read the offsets.
     """
     dev = frames[0].device if len(frames) else torch.device("cuda")
     xyz, off_t, F, lv, og = _frame_inputs(frames, leaves, origins, dev)
+    pz = _per_frame(poses, F, 12, dev)
+    zl = _per_frame(z_limits, F, 2, dev)
     n = xyz.shape[0]
     flags = method_flag(method) | (ORIGIN_FROM_MIN if origins is None else 0) | \
         (int(grid_per_sm) << GRID_SHIFT)
@@ -334,15 +365,46 @@ def downsample_frames(frames, leaves, origins=None, *, method="sort", point_to_v
     p2v = torch.empty(cap, dtype=torch.int32, device=dev) if point_to_voxel else None
     ws = torch.empty(max(int(lib().vg_batch_workspace_bytes(n, F, flags)), 256), dtype=torch.uint8,
                      device=dev)
-    st = lib().vg_downsample_frames(
-        _ptr(xyz), n, _ptr(off_t), F, _ptr(og), _ptr(lv), _ptr(keys), _ptr(cents), _ptr(counts), n,
-        _ptr(out_off), _ptr(p2v), _ptr(err), _ptr(ws), ws.numel(), flags, _stream_ptr(stream))
+    if pz is None and zl is None:
+        st = lib().vg_downsample_frames(
+            _ptr(xyz), n, _ptr(off_t), F, _ptr(og), _ptr(lv), _ptr(keys), _ptr(cents),
+            _ptr(counts), n, _ptr(out_off), _ptr(p2v), _ptr(err), _ptr(ws), ws.numel(), flags,
+            _stream_ptr(stream))
+    else:
+        st = lib().vg_downsample_frames_posed(
+            _ptr(xyz), n, _ptr(off_t), F, _ptr(pz), _ptr(zl), _ptr(og), _ptr(lv), _ptr(keys),
+            _ptr(cents), _ptr(counts), n, _ptr(out_off), _ptr(p2v), _ptr(err), _ptr(ws),
+            ws.numel(), flags, _stream_ptr(stream))
     _check(st, "vg_downsample_frames")
     (stream or torch.cuda.current_stream()).synchronize()
     _check(int(err.item()), "vg_downsample_frames (device)")
     offs = out_off.cpu().tolist()
     v = offs[-1]
     return Frames(keys[:v], cents[:v], counts[:v], offs, og, p2v[:n] if point_to_voxel else None)
+
+
+def frames_into(xyz: torch.Tensor, frame_offsets: torch.Tensor, n_frames: int,
+                origins: torch.Tensor, leaves: torch.Tensor, out_keys: torch.Tensor,
+                out_centroids: torch.Tensor, out_counts: torch.Tensor,
+                out_frame_offsets: torch.Tensor, out_error: torch.Tensor,
+                workspace: torch.Tensor, *, origin_from_min: bool = True, method="sort",
+                poses: Optional[torch.Tensor] = None, z_limits: Optional[torch.Tensor] = None,
+                point_to_voxel: Optional[torch.Tensor] = None,
+                stream: Optional[torch.cuda.Stream] = None) -> None:
+    """Launch vg_downsample_frames (or _posed, when poses/z_limits are given) into
+    preallocated device buffers; asynchronous, no host sync."""
+    xyz = _cuda_cloud(xyz)
+    flags = method_flag(method) | (ORIGIN_FROM_MIN if origin_from_min else 0)
+    args = (_ptr(origins), _ptr(leaves), _ptr(out_keys), _ptr(out_centroids), _ptr(out_counts),
+            out_keys.shape[0], _ptr(out_frame_offsets), _ptr(point_to_voxel), _ptr(out_error),
+            _ptr(workspace), workspace.numel(), flags, _stream_ptr(stream))
+    if poses is None and z_limits is None:
+        st = lib().vg_downsample_frames(_ptr(xyz), xyz.shape[0], _ptr(frame_offsets),
+                                        int(n_frames), *args)
+    else:
+        st = lib().vg_downsample_frames_posed(_ptr(xyz), xyz.shape[0], _ptr(frame_offsets),
+                                              int(n_frames), _ptr(poses), _ptr(z_limits), *args)
+    _check(st, "vg_downsample_frames")
 
 
 class Plan:

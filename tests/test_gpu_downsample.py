@@ -163,3 +163,24 @@ def test_fused_map_full_size_sampled():
     want = sums[pick] / cnt[pick, None]
     err = np.abs(to_np(res.centroids)[pick].astype(np.float64) - want).max()
     assert err <= 1e-5, err
+
+
+@pytest.mark.parametrize("top,hi", [((2047, 2047, 1023), (2048, 2048, 1024)),
+                                    ((2046, 2047, 1023), (2047, 2048, 1024))])
+def test_all_ones_32bit_key(top, hi):
+    """A voxel whose 32-bit Morton key is all ones (first case) sits next to invalid rows,
+    whose sort key is all ones too; one just below it (second case) lets the extents pick
+    the 32-bit sort layout.  Both must drop exactly the invalid rows."""
+    leaf = 2.0 ** -6
+    rng = np.random.Generator(np.random.PCG64(11))
+    idx = rng.integers(0, hi, size=(6000, 3))
+    idx[:40] = top
+    xyz = ((idx + rng.uniform(0.1, 0.9, size=idx.shape)) * leaf).astype(np.float32)
+    xyz[40 + rng.choice(5960, 400, replace=False)] = np.nan
+    ref = oracle.downsample(xyz, leaf, np.zeros(3, np.float32))
+    res = run(xyz, leaf, origin=(0.0, 0.0, 0.0))
+    assert_decimation_equal(res, ref)
+    ix, iy, iz = top
+    want = sum(((ix >> b) & 1) << (3 * b) | ((iy >> b) & 1) << (3 * b + 1) |
+               ((iz >> b) & 1) << (3 * b + 2) for b in range(11))
+    assert int(ref.keys[-1]) == want and int(ref.counts[-1]) == 40
