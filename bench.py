@@ -270,6 +270,28 @@ def extra_measurements(args, dev):
                           "voxels": int(hb.num_voxels.item())}
     out["rgbd_1280x720_sweep"] = sweep
 
+    # voxel extras on the same frame at 0.02 m: RGB means per voxel and/or min 2 points
+    nh = hd.shape[0]
+    rgb = torch.randint(0, 256, (nh, 3), dtype=torch.uint8, device=dev,
+                        generator=torch.Generator(device=dev).manual_seed(7))
+    one = torch.tensor([0, nh], dtype=torch.int64, device=dev)
+    lf = torch.tensor([0.02], dtype=torch.float32, device=dev)
+    og = torch.zeros((1, 3), dtype=torch.float32, device=dev)
+    o_at = torch.empty((nh, 3), dtype=torch.float32, device=dev)
+    o_off = torch.zeros(2, dtype=torch.int64, device=dev)
+    ext = {}
+    for name, kw in (("plain", {}), ("rgb_means", {"attrs": rgb, "out_attrs": o_at}),
+                     ("min_count_2", {"min_count": 2}),
+                     ("rgb_means_min_count_2", {"attrs": rgb, "out_attrs": o_at,
+                                                "min_count": 2})):
+        exs = vg.extras(kw.get("attrs"), kw.get("out_attrs"), kw.get("min_count", 1))
+        wsx = torch.empty(max(vg.ex_workspace_bytes(nh, 1, vg.METHOD_SORT, exs), 256),
+                          dtype=torch.uint8, device=dev)
+        ms = _time_ms(lambda: vg.frames_into(hd, one, 1, og, lf, hb.keys, hb.centroids,
+                                             hb.counts, o_off, hb.error, wsx, **kw), 50)
+        ext[name] = {"ms": ms, "points_per_s": nh / (ms / 1e3), "voxels": int(o_off[1].item())}
+    out["rgbd_1280x720_leaf0.02_extras"] = ext
+
     # backward of the mean squared centroid loss, 307,200 points, leaf 0.05 m
     res = vg.downsample(x, 0.05, point_to_voxel=True)
     g = torch.randn_like(res.centroids)

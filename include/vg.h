@@ -182,6 +182,40 @@ VG_API vg_status vg_downsample_frames_posed(
     size_t workspace_bytes, int flags, vg_stream_t stream);
 
 /*
+ * Voxel extras: per-voxel attributes and a minimum point count, on top of posed frames.
+ * The paper's camera is an RGB-D sensor (Sec. II-B), so a voxel can carry the mean
+ * colour of its points next to their centroid; the PCL voxel filter that the paper
+ * replaces can also drop voxels holding fewer than a given number of points.
+ *
+ *   attrs          uint8 [n_total, attr_channels] (device), row i belongs to point i, or
+ *                  NULL for none.  1 <= attr_channels <= 4 when attrs is given.
+ *   out_attrs      float32 [cap, attr_channels] (device): each voxel's channel means,
+ *                  sum over its points (exact) / count, divided in FP64 and rounded to
+ *                  float32.  Needs the sort path (VG_METHOD_HASH: VG_ERR_INVALID_ARG).
+ *   min_count      voxels with fewer points are removed after grouping (0 or 1 keeps
+ *                  them all); the kept voxels keep their order, out_frame_offsets and
+ *                  the voxel count refer to them, and points of removed voxels get -1 in
+ *                  out_point_to_voxel.
+ * The workspace must hold vg_downsample_ex_workspace_bytes(n_total, n_frames, flags,
+ * extras) bytes.  extras == NULL is exactly vg_downsample_frames_posed.
+ */
+typedef struct vg_voxel_extras {
+  const uint8_t* attrs;
+  int attr_channels;
+  float* out_attrs;
+  uint32_t min_count;
+} vg_voxel_extras;
+
+VG_API size_t vg_downsample_ex_workspace_bytes(int64_t n_total, int n_frames, int flags,
+                                               const vg_voxel_extras* extras);
+VG_API vg_status vg_downsample_frames_ex(
+    const float* xyz, int64_t n_total, const int64_t* frame_offsets, int n_frames,
+    const float* poses, const float* z_limits, float* origins, const float* leaves,
+    uint64_t* out_keys, float* out_centroids, uint32_t* out_counts, int64_t cap,
+    int64_t* out_frame_offsets, int32_t* out_point_to_voxel, const vg_voxel_extras* extras,
+    int32_t* out_error, void* workspace, size_t workspace_bytes, int flags, vg_stream_t stream);
+
+/*
  * Batch plan: owns a workspace for up to max_points points in max_frames frames
  * (allocated here, once), the grouping method and grid size, and a CUDA graph of the
  * batched launch sequence.  vg_downsample_batch takes the arguments of

@@ -55,6 +55,7 @@ void warm_launch_config() {
   num_sms();
   warm_sort_config();
   warm_reduce_config();
+  warm_filter_config();
 }
 
 int persistent_grid(const void* kernel, int threads, size_t dyn_smem, int64_t work_tiles) {
@@ -137,7 +138,7 @@ vg_status run_frames(const float* xyz, const FramesArg& fr, bool from_min, const
   if (method == VG_METHOD_SORT) {
     // The narrow layout (no gather) needs the extents up front and no point_to_voxel.
     FramesArg frn = fr;
-    frn.allow_narrow = out.p2v == nullptr;
+    frn.allow_narrow = out.p2v == nullptr && out.attrs_in == nullptr;
     const bool have_extent = from_min || F > 1 || frn.allow_narrow;
     const SortLayout L = sort_layout(n, F);
     State* st = reinterpret_cast<State*>(ws + L.state);
@@ -347,8 +348,38 @@ vg_status vg_downsample_frames_posed(const float* xyz, int64_t n_total,
                                      int64_t* out_frame_offsets, int32_t* out_point_to_voxel,
                                      int32_t* out_error, void* workspace, size_t workspace_bytes,
                                      int flags, vg_stream_t stream) {
+  return vg_downsample_frames_ex(xyz, n_total, frame_offsets, n_frames, poses, z_limits, origins,
+                                 leaves, out_keys, out_centroids, out_counts, cap,
+                                 out_frame_offsets, out_point_to_voxel, nullptr, out_error,
+                                 workspace, workspace_bytes, flags, stream);
+}
+
+size_t vg_downsample_ex_workspace_bytes(int64_t n_total, int n_frames, int flags,
+                                        const vg_voxel_extras* extras) {
+  if (n_total < 0 || n_frames < 1 || n_frames > kMaxFrames) return 0;
+  const size_t base = frames_workspace_bytes(n_total, n_frames, flags);
+  if (!extras || extras->min_count <= 1) return base;
+  return filter_layout(n_total, base).total;
+}
+
+vg_status vg_downsample_frames_ex(const float* xyz, int64_t n_total,
+                                  const int64_t* frame_offsets, int n_frames, const float* poses,
+                                  const float* z_limits, float* origins, const float* leaves,
+                                  uint64_t* out_keys, float* out_centroids, uint32_t* out_counts,
+                                  int64_t cap, int64_t* out_frame_offsets,
+                                  int32_t* out_point_to_voxel, const vg_voxel_extras* extras,
+                                  int32_t* out_error, void* workspace, size_t workspace_bytes,
+                                  int flags, vg_stream_t stream) {
   if (n_frames < 1 || n_frames > kMaxFrames) return VG_ERR_INVALID_ARG;
   if (!aligned(poses, 4) || !aligned(z_limits, 4)) return VG_ERR_ALIGN;
+  const uint8_t* attrs = extras ? extras->attrs : nullptr;
+  const int channels = attrs ? extras->attr_channels : 0;
+  if (attrs) {
+    if (channels < 1 || channels > 4 || !extras->out_attrs) return VG_ERR_INVALID_ARG;
+    if (method_of(flags) == VG_METHOD_HASH) return VG_ERR_INVALID_ARG;
+    if (!aligned(extras->out_attrs, 4)) return VG_ERR_ALIGN;
+  }
+  const bool filtered = extras && extras->min_count > 1;
   if ((flags & ~(VG_ORIGIN_FROM_MIN | VG_METHOD_MASK | VG_GRID_MASK)) != 0)
     return VG_ERR_INVALID_ARG;
   if ((flags & VG_METHOD_MASK) == VG_METHOD_MASK) return VG_ERR_INVALID_ARG;
@@ -364,9 +395,21 @@ vg_status vg_downsample_frames_posed(const float* xyz, int64_t n_total,
                z_limits};
   // V lands in out_frame_offsets[n_frames]; the segmented reduction also writes it there.
   SegOut out{out_keys, out_centroids, out_counts, nullptr, cap, out_frame_offsets + n_frames,
-             out_frame_offsets, out_point_to_voxel};
-  return run_frames(xyz, fr, from_min, out, out_error, workspace, workspace_bytes, flags,
-                    reinterpret_cast<cudaStream_t>(stream));
+             out_frame_offsets, out_point_to_voxel, attrs, channels,
+             attrs ? extras->out_attrs : nullptr};
+  const size_t base = frames_workspace_bytes(n_total, n_frames, flags);
+  FilterLayout FL{};
+  if (filtered) {
+    FL = filter_layout(n_total, base);
+    if (!workspace || workspace_bytes < FL.total) return VG_ERR_WORKSPACE;
+  }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  s = run_frames(xyz, fr, from_min, out, out_error, workspace, workspace_bytes, flags, st);
+  if (s != VG_OK || !filtered) return s;
+  char* ws = static_cast<char*>(workspace);
+  int* err = out_error ? reinterpret_cast<int*>(out_error) : &reinterpret_cast<State*>(ws)->error;
+  return cuda_status(launch_filter(ws, FL, cap < n_total ? cap : n_total, extras->min_count, out,
+                                   n_frames, n_total, spin_limit(), err, st));
 }
 
 size_t vg_pyramid_workspace_bytes(int64_t n_points, int levels, int flags) {

@@ -91,6 +91,7 @@ struct alignas(8) TileRec {
   uint32_t lead_n;
   uint32_t pad;
   long long lead_s[3];
+  unsigned long long lead_a[4];  // attribute channel sums of the leading entries
 };
 
 // Frames of one call.  A single cloud is one frame [0, n) with offsets == nullptr.
@@ -203,12 +204,24 @@ struct SegOut {
   int64_t* num_voxels;
   int64_t* frame_offsets;  // optional [F+1] per-frame output offsets
   int32_t* p2v;
+  const uint8_t* attrs_in;  // optional [n, channels] per-point attributes (wide layout)
+  int channels;
+  float* attrs_out;         // [cap, channels] per-voxel means
 };
 cudaError_t launch_segreduce(State* st, const FrameState* fs, int nframes,
                              const uint64_t* keys0, const uint32_t* idx0, const uint64_t* keys1,
                              const uint32_t* idx1, const float* xyz, TileRec* recs,
                              int64_t n_max, const SegOut& out, int* err, cudaStream_t stream,
                              const NarrowBuffers* nb = nullptr, const float* poses = nullptr);
+// Minimum-count filter (vg_filter.cu): its scratch follows the grouping method's layout.
+struct FilterLayout {
+  size_t ticket, status, remap, zero_bytes, total;
+};
+FilterLayout filter_layout(int64_t cap, size_t base);
+cudaError_t launch_filter(char* ws, const FilterLayout& L, int64_t cap, uint32_t min_count,
+                          const SegOut& out, int nframes, int64_t n_points, uint32_t spin_limit,
+                          int* err, cudaStream_t stream);
+void warm_filter_config();
 // a2, narrow-capable key kernel: writes either 64-bit keys to keys64 (wide) or 32-bit keys
 // and packed offsets (narrow, when allowed and the sort key fits in 32 bits).
 cudaError_t launch_keys_any(const float* xyz, const FramesArg& fr, bool have_extent, State* st,

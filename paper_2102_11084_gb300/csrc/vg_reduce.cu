@@ -90,11 +90,34 @@ __device__ __forceinline__ Acc block_sum_acc(Acc a, Acc* tmp) {
   return r;
 }
 
+// Block-wide sums of four 64-bit counters (kRedThreads threads); result valid in thread 0.
+__device__ __forceinline__ void block_sum_u64x4(unsigned long long a[4],
+                                                unsigned long long (*tmp)[4]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+#pragma unroll
+    for (int off = 16; off; off >>= 1) a[c] += __shfl_xor_sync(kFullMask, a[c], off);
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) tmp[warp][c] = a[c];
+  __syncthreads();
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      a[c] = 0;
+      for (int w = 0; w < kRedThreads / 32; ++w) a[c] += tmp[w][c];
+    }
+}
+
 template <bool kNarrow>
 __device__ __forceinline__ void seg_count_body(
     const State* st, const FrameState* __restrict__ fs, const void* k0_, const void* p0_,
     const void* k1_, const void* p1_, const float* __restrict__ xyz,
-    const float* __restrict__ poses, TileRec* recs) {
+    const float* __restrict__ poses, const uint8_t* __restrict__ attrs, int channels,
+    TileRec* recs) {
+  __shared__ unsigned long long s_attr[kRedThreads / 32][4];
   using KeyT = typename Layout<kNarrow>::KeyT;
   using PayT = typename Layout<kNarrow>::PayT;
   __shared__ uint32_t s_heads[kRedThreads / 32];
@@ -160,6 +183,16 @@ __device__ __forceinline__ void seg_count_body(
       lead.s[2] += q[2];
     }
     lead = block_sum_acc(lead, s_acc);
+    unsigned long long la[4] = {0, 0, 0, 0};
+    if (!kNarrow && attrs) {  // attribute sums of the same leading entries (wide layout)
+      for (int li = t; li < fh; li += kRedThreads) {
+        const uint8_t* a = attrs + size_t(uint32_t(P[base + li])) * channels;
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          if (c < channels) la[c] += a[c];
+      }
+      block_sum_u64x4(la, s_attr);
+    }
     if (t == 0) {
       TileRec r;
       r.heads = th;
@@ -169,6 +202,7 @@ __device__ __forceinline__ void seg_count_body(
       r.lead_s[0] = lead.s[0];
       r.lead_s[1] = lead.s[1];
       r.lead_s[2] = lead.s[2];
+      for (int c = 0; c < 4; ++c) r.lead_a[c] = la[c];
       recs[tile] = r;
     }
     __syncthreads();
@@ -303,6 +337,15 @@ __device__ __forceinline__ void seg_reduce_body(
       }
       if (!kNarrow && out.p2v)
         for (int e = e0; e < e1; ++e) out.p2v[sidx[e]] = static_cast<int32_t>(cur);
+      unsigned long long asum[4] = {0, 0, 0, 0};
+      const bool with_attrs = !kNarrow && out.attrs_in != nullptr;
+      if (with_attrs)
+        for (int e = e0; e < e1; ++e) {
+          const uint8_t* a = out.attrs_in + size_t(sidx[e]) * out.channels;
+#pragma unroll
+          for (int c = 0; c < 4; ++c)
+            if (c < out.channels) asum[c] += a[c];
+        }
       bool last_run = false;
       if (e1 == cnt) {  // the run may continue in the following tiles
         int64_t tt = tile + 1;
@@ -312,10 +355,19 @@ __device__ __forceinline__ void seg_reduce_body(
           run.s[0] += rr.lead_s[0];
           run.s[1] += rr.lead_s[1];
           run.s[2] += rr.lead_s[2];
+          if (with_attrs)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) asum[c] += rr.lead_a[c];
           if (rr.heads > 0) break;
         }
         last_run = tt >= ntiles;
       }
+      if (with_attrs && int64_t(cur) < out.cap)  // exact sums, one FP64 division each
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          if (c < out.channels)
+            out.attrs_out[size_t(cur) * out.channels + c] = __double2float_rn(
+                __ddiv_rn(static_cast<double>(asum[c]), static_cast<double>(run.n)));
       if (int64_t(cur) >= out.cap) {
         set_error(err, kErrCapacity);
       } else {
@@ -563,11 +615,13 @@ struct RedPtrs {
 
 __global__ __launch_bounds__(kRedThreads) void seg_count_kernel(
     const State* st, const FrameState* __restrict__ fs, RedPtrs rp, const float* __restrict__ xyz,
-    const float* __restrict__ poses, TileRec* recs) {
+    const float* __restrict__ poses, const uint8_t* __restrict__ attrs, int channels,
+    TileRec* recs) {
   if (st->narrow)
-    seg_count_body<true>(st, fs, rp.nk0, rp.np0, rp.nk1, rp.np1, xyz, poses, recs);
+    seg_count_body<true>(st, fs, rp.nk0, rp.np0, rp.nk1, rp.np1, xyz, poses, nullptr, 0, recs);
   else
-    seg_count_body<false>(st, fs, rp.wk0, rp.wp0, rp.wk1, rp.wp1, xyz, poses, recs);
+    seg_count_body<false>(st, fs, rp.wk0, rp.wp0, rp.wk1, rp.wp1, xyz, poses, attrs, channels,
+                          recs);
 }
 
 __global__ __launch_bounds__(kRedThreads, 4) void seg_reduce_kernel(
@@ -608,7 +662,8 @@ cudaError_t launch_segreduce(State* st, const FrameState* fs, int nframes,
   const int64_t tiles = ceil_div(n_max, kRedTile);
   const int gc = persistent_grid(reinterpret_cast<const void*>(seg_count_kernel), kRedThreads, 0,
                                  tiles);
-  seg_count_kernel<<<gc, kRedThreads, 0, stream>>>(st, fs, rp, xyz, poses, recs);
+  seg_count_kernel<<<gc, kRedThreads, 0, stream>>>(st, fs, rp, xyz, poses, out.attrs_in,
+                                                   out.channels, recs);
   seg_scan_kernel<<<1, 1024, 0, stream>>>(st, recs, out.num_voxels);
   const int gr = persistent_grid(reinterpret_cast<const void*>(seg_reduce_kernel), kRedThreads,
                                  kRedSmem, tiles);

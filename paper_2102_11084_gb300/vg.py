@@ -79,6 +79,15 @@ _SIGS = {
                                     ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                     ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p], ctypes.c_int),
+    "vg_downsample_ex_workspace_bytes": ([ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_void_p], ctypes.c_size_t),
+    "vg_downsample_frames_ex": ([ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int,
+                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                 ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                 ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int,
+                                 ctypes.c_void_p], ctypes.c_int),
     "vg_plan_create": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_int], ctypes.c_int),
     "vg_plan_destroy": ([ctypes.c_void_p], ctypes.c_int),
     "vg_plan_configure": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_int], ctypes.c_int),
@@ -218,24 +227,31 @@ class Decimation(NamedTuple):
     counts: torch.Tensor          # int32 [V]
     origin: torch.Tensor          # float32 [3]
     point_to_voxel: Optional[torch.Tensor]  # int32 [N], -1 = invalid point
+    attrs: Optional[torch.Tensor] = None    # float32 [V, C] per-voxel attribute means
 
 
 def downsample(xyz: torch.Tensor, leaf: float, origin: Optional[torch.Tensor] = None, *,
                method="sort", point_to_voxel: bool = False, pose=None, z_limits=None,
+               attrs=None, min_count: int = 1,
                stream: Optional[torch.cuda.Stream] = None) -> Decimation:
     """Voxel-grid decimation of one cloud: centroid per occupied voxel, key order.
 
     ``origin`` None means the per-axis minimum of the valid points.  ``pose`` ([3,4]
     [R|t]) and ``z_limits`` ([z_min, z_max]) first take the cloud into the common frame
-    and drop points outside the height band (vg_downsample_frames_posed).  Synchronises
-    the stream once to read V and the device error word.
+    and drop points outside the height band; ``attrs`` (uint8 [N, C], C <= 4) adds
+    per-voxel attribute means and ``min_count`` removes voxels with fewer points
+    (vg_downsample_frames_ex).  Synchronises the stream once to read V and the device
+    error word.
     """
-    if pose is not None or z_limits is not None:
+    if pose is not None or z_limits is not None or attrs is not None or min_count > 1:
         fr = downsample_frames([xyz], [leaf], None if origin is None else [origin],
                                method=method, point_to_voxel=point_to_voxel,
                                poses=None if pose is None else [pose],
-                               z_limits=None if z_limits is None else [z_limits], stream=stream)
-        return Decimation(fr.keys, fr.centroids, fr.counts, fr.origins[0], fr.point_to_voxel)
+                               z_limits=None if z_limits is None else [z_limits],
+                               attrs=None if attrs is None else [attrs], min_count=min_count,
+                               stream=stream)
+        return Decimation(fr.keys, fr.centroids, fr.counts, fr.origins[0], fr.point_to_voxel,
+                          fr.attrs)
     xyz = _cuda_cloud(xyz)
     n = xyz.shape[0]
     org = None
@@ -295,11 +311,18 @@ class Frames(NamedTuple):
     offsets: list                 # host list of F+1 row offsets
     origins: torch.Tensor         # float32 [F, 3]
     point_to_voxel: Optional[torch.Tensor]  # int32 [N_total], global rows
+    attrs: Optional[torch.Tensor] = None    # float32 [V_total, C] per-voxel attribute means
 
     def frame(self, f: int) -> Decimation:
         a, b = self.offsets[f], self.offsets[f + 1]
         return Decimation(self.keys[a:b], self.centroids[a:b], self.counts[a:b], self.origins[f],
-                          None)
+                          None, None if self.attrs is None else self.attrs[a:b])
+
+
+class VoxelExtras(ctypes.Structure):
+    """vg_voxel_extras of include/vg.h."""
+    _fields_ = [("attrs", ctypes.c_void_p), ("attr_channels", ctypes.c_int),
+                ("out_attrs", ctypes.c_void_p), ("min_count", ctypes.c_uint32)]
 
 
 def _is_cat_form(frames) -> bool:
@@ -324,7 +347,7 @@ def _frame_inputs(frames, leaves, origins, device):
     off_t = torch.tensor(offs, dtype=torch.int64, device=device)
     lv = torch.as_tensor(leaves, dtype=torch.float32).reshape(F).to(device)
     og = (torch.zeros((F, 3), dtype=torch.float32, device=device) if origins is None else
-          torch.as_tensor(origins, dtype=torch.float32).reshape(F, 3).to(device).contiguous())
+          _per_frame(origins, F, 3, device))
     return _cuda_cloud(xyz), off_t, F, lv, og
 
 
@@ -340,19 +363,29 @@ def _per_frame(values, F: int, width: int, device) -> Optional[torch.Tensor]:
 
 
 def downsample_frames(frames, leaves, origins=None, *, method="sort", point_to_voxel=False,
-                      grid_per_sm: int = 0, poses=None, z_limits=None,
+                      grid_per_sm: int = 0, poses=None, z_limits=None, attrs=None,
+                      min_count: int = 1,
                       stream: Optional[torch.cuda.Stream] = None) -> Frames:
     """vg_downsample_frames: every frame decimated as it would be alone, in one call.
 
     ``frames`` is a list of float32 [N_f, 3] CUDA tensors or a tuple (xyz [N,3], offsets).
     ``origins`` None means each frame's minimum.  ``poses`` ([F,3,4] sensor poses [R|t])
-    and ``z_limits`` ([F,2]) make it vg_downsample_frames_posed.  Synchronises once to
-    read the offsets.
+    and ``z_limits`` ([F,2]) take each frame into the common frame and cut its height;
+    ``attrs`` (uint8 [N_f, C] per frame, or [N, C] with the tuple form, C <= 4) gives
+    per-voxel attribute means; ``min_count`` removes voxels with fewer points
+    (vg_downsample_frames_ex).  Synchronises once to read the offsets.
     """
     dev = frames[0].device if len(frames) else torch.device("cuda")
     xyz, off_t, F, lv, og = _frame_inputs(frames, leaves, origins, dev)
     pz = _per_frame(poses, F, 12, dev)
     zl = _per_frame(z_limits, F, 2, dev)
+    at = None
+    if attrs is not None:
+        at = attrs if isinstance(attrs, torch.Tensor) else torch.cat(
+            [torch.as_tensor(a).reshape(int(f.shape[0]), -1) for a, f in zip(attrs, frames)])
+        at = at.to(device=dev, dtype=torch.uint8).contiguous()
+        if at.dim() != 2 or at.shape[0] != xyz.shape[0] or not 1 <= at.shape[1] <= 4:
+            raise ValueError("attrs must be uint8 [N, C] with 1 <= C <= 4")
     n = xyz.shape[0]
     flags = method_flag(method) | (ORIGIN_FROM_MIN if origins is None else 0) | \
         (int(grid_per_sm) << GRID_SHIFT)
@@ -363,24 +396,33 @@ def downsample_frames(frames, leaves, origins=None, *, method="sort", point_to_v
     out_off = torch.zeros(F + 1, dtype=torch.int64, device=dev)
     err = torch.zeros(1, dtype=torch.int32, device=dev)
     p2v = torch.empty(cap, dtype=torch.int32, device=dev) if point_to_voxel else None
-    ws = torch.empty(max(int(lib().vg_batch_workspace_bytes(n, F, flags)), 256), dtype=torch.uint8,
-                     device=dev)
-    if pz is None and zl is None:
+    out_at = (torch.empty((cap, at.shape[1]), dtype=torch.float32, device=dev)
+              if at is not None else None)
+    ex = None
+    if at is not None or min_count > 1:
+        ex = VoxelExtras(None if at is None else at.data_ptr(), 0 if at is None else at.shape[1],
+                         None if out_at is None else out_at.data_ptr(), int(min_count))
+    wsb = (lib().vg_downsample_ex_workspace_bytes(n, F, flags, ctypes.byref(ex)) if ex else
+           lib().vg_batch_workspace_bytes(n, F, flags))
+    ws = torch.empty(max(int(wsb), 256), dtype=torch.uint8, device=dev)
+    if pz is None and zl is None and ex is None:
         st = lib().vg_downsample_frames(
             _ptr(xyz), n, _ptr(off_t), F, _ptr(og), _ptr(lv), _ptr(keys), _ptr(cents),
             _ptr(counts), n, _ptr(out_off), _ptr(p2v), _ptr(err), _ptr(ws), ws.numel(), flags,
             _stream_ptr(stream))
     else:
-        st = lib().vg_downsample_frames_posed(
+        st = lib().vg_downsample_frames_ex(
             _ptr(xyz), n, _ptr(off_t), F, _ptr(pz), _ptr(zl), _ptr(og), _ptr(lv), _ptr(keys),
-            _ptr(cents), _ptr(counts), n, _ptr(out_off), _ptr(p2v), _ptr(err), _ptr(ws),
-            ws.numel(), flags, _stream_ptr(stream))
+            _ptr(cents), _ptr(counts), n, _ptr(out_off), _ptr(p2v),
+            ctypes.byref(ex) if ex else None, _ptr(err), _ptr(ws), ws.numel(), flags,
+            _stream_ptr(stream))
     _check(st, "vg_downsample_frames")
     (stream or torch.cuda.current_stream()).synchronize()
     _check(int(err.item()), "vg_downsample_frames (device)")
     offs = out_off.cpu().tolist()
     v = offs[-1]
-    return Frames(keys[:v], cents[:v], counts[:v], offs, og, p2v[:n] if point_to_voxel else None)
+    return Frames(keys[:v], cents[:v], counts[:v], offs, og, p2v[:n] if point_to_voxel else None,
+                  None if out_at is None else out_at[:v])
 
 
 def frames_into(xyz: torch.Tensor, frame_offsets: torch.Tensor, n_frames: int,
@@ -390,21 +432,40 @@ def frames_into(xyz: torch.Tensor, frame_offsets: torch.Tensor, n_frames: int,
                 workspace: torch.Tensor, *, origin_from_min: bool = True, method="sort",
                 poses: Optional[torch.Tensor] = None, z_limits: Optional[torch.Tensor] = None,
                 point_to_voxel: Optional[torch.Tensor] = None,
-                stream: Optional[torch.cuda.Stream] = None) -> None:
-    """Launch vg_downsample_frames (or _posed, when poses/z_limits are given) into
-    preallocated device buffers; asynchronous, no host sync."""
+                attrs: Optional[torch.Tensor] = None, out_attrs: Optional[torch.Tensor] = None,
+                min_count: int = 1, stream: Optional[torch.cuda.Stream] = None) -> None:
+    """Launch vg_downsample_frames (or _ex, when poses, z_limits, attrs or min_count are
+    given) into preallocated device buffers; asynchronous, no host sync.  The workspace
+    must hold ex_workspace_bytes(...) for attrs/min_count."""
     xyz = _cuda_cloud(xyz)
     flags = method_flag(method) | (ORIGIN_FROM_MIN if origin_from_min else 0)
-    args = (_ptr(origins), _ptr(leaves), _ptr(out_keys), _ptr(out_centroids), _ptr(out_counts),
-            out_keys.shape[0], _ptr(out_frame_offsets), _ptr(point_to_voxel), _ptr(out_error),
-            _ptr(workspace), workspace.numel(), flags, _stream_ptr(stream))
-    if poses is None and z_limits is None:
+    head = (_ptr(origins), _ptr(leaves), _ptr(out_keys), _ptr(out_centroids), _ptr(out_counts),
+            out_keys.shape[0], _ptr(out_frame_offsets), _ptr(point_to_voxel))
+    tail = (_ptr(out_error), _ptr(workspace), workspace.numel(), flags, _stream_ptr(stream))
+    ex = extras(attrs, out_attrs, min_count)
+    if poses is None and z_limits is None and ex is None:
         st = lib().vg_downsample_frames(_ptr(xyz), xyz.shape[0], _ptr(frame_offsets),
-                                        int(n_frames), *args)
+                                        int(n_frames), *head, *tail)
     else:
-        st = lib().vg_downsample_frames_posed(_ptr(xyz), xyz.shape[0], _ptr(frame_offsets),
-                                              int(n_frames), _ptr(poses), _ptr(z_limits), *args)
+        st = lib().vg_downsample_frames_ex(_ptr(xyz), xyz.shape[0], _ptr(frame_offsets),
+                                           int(n_frames), _ptr(poses), _ptr(z_limits), *head,
+                                           ctypes.byref(ex) if ex else None, *tail)
     _check(st, "vg_downsample_frames")
+
+
+def extras(attrs: Optional[torch.Tensor] = None, out_attrs: Optional[torch.Tensor] = None,
+           min_count: int = 1) -> Optional[VoxelExtras]:
+    """The vg_voxel_extras of a call, or None when it asks for nothing extra."""
+    if attrs is None and min_count <= 1:
+        return None
+    return VoxelExtras(None if attrs is None else attrs.data_ptr(),
+                       0 if attrs is None else int(attrs.shape[1]),
+                       None if out_attrs is None else out_attrs.data_ptr(), int(min_count))
+
+
+def ex_workspace_bytes(n_total: int, n_frames: int, flags: int, ex: Optional[VoxelExtras]) -> int:
+    return int(lib().vg_downsample_ex_workspace_bytes(
+        int(n_total), int(n_frames), int(flags), ctypes.byref(ex) if ex else None))
 
 
 class Plan:
