@@ -250,3 +250,15 @@ def downsample_attrs(xyz, leaf: float, attrs=None, min_count: int = 1, origin_xy
                                         _ptr(out) if ch else None, ch, v, int(min_count),
                                         _ptr(p2v), n))
     return AttrDecimation(keys[:v], cents[:v], counts[:v], out[:v], p2v, d.origin)
+
+
+def map_contents(frames, leaf: float, origin_xyz, poses=None, z_limits=None) -> Decimation:
+    """A voxel map after inserting ``frames`` (each optionally posed and height-cut): by
+    definition the decimation of all their points together on the map's lattice."""
+    clouds = []
+    for f, x in enumerate(frames):
+        p = None if poses is None else poses[f]
+        z = None if z_limits is None else z_limits[f]
+        clouds.append(pose(x, p, z) if (p is not None or z is not None) else _cloud(x))
+    allp = np.concatenate(clouds) if clouds else np.zeros((0, 3), np.float32)
+    return downsample(allp, leaf, origin_xyz)
