@@ -257,7 +257,31 @@ def extra_measurements(args, dev):
         "posed_points_per_s": total / (ms_posed / 1e3), "overhead": ms_posed / ms_plain - 1.0,
         "voxels_plain": v_plain, "voxels_posed": int(bb["out_frame_offsets"][F].item()),
         "band_m": [float(b) for b in bands[0]]}
-    del frames, bufs, xyz, bb, fargs, wsf
+
+    # persistent voxel map: the 64 posed frames merged into one map (one insert call after
+    # a clear), then the whole map extracted in key order
+    mp = vg.VoxelMap(4_000_000, (-20.0, -20.0, -5.0), 0.05, device=dev)
+    sp = vg._stream_ptr(None)
+
+    def map_insert():
+        vg.lib().vg_map_clear(mp._h, sp)
+        vg.lib().vg_map_insert(mp._h, vg._ptr(xyz), total, vg._ptr(offs), F, vg._ptr(pz),
+                               vg._ptr(zl), vg._ptr(mp.error), sp)
+    ms_ins = _time_ms(map_insert, 20)
+    mk = torch.empty(8_000_000, dtype=torch.int64, device=dev)
+    mc = torch.empty((8_000_000, 3), dtype=torch.float32, device=dev)
+    mn = torch.empty(8_000_000, dtype=torch.int32, device=dev)
+    mv = torch.zeros(1, dtype=torch.int64, device=dev)
+    ms_ext = _time_ms(lambda: vg.lib().vg_map_extract(
+        mp._h, vg._ptr(mk), vg._ptr(mc), vg._ptr(mn), mk.shape[0], vg._ptr(mv),
+        vg._ptr(mp.error), sp), 20)
+    if int(mp.error.item()):
+        raise vg.VGError(int(mp.error.item()), "voxel map")
+    out["voxel_map_64_posed_frames"] = {
+        "points": total, "insert_ms": ms_ins, "insert_points_per_s": total / (ms_ins / 1e3),
+        "extract_ms": ms_ext, "voxels": int(mv.item()), "leaf_m": 0.05, "slots": 8_388_608}
+    mp.close()
+    del frames, bufs, xyz, bb, fargs, wsf, mk, mc, mn
 
     # 1280x720 frame: 4-level pyramid from 0.01 m, and the leaf sweep
     hd = torch.from_numpy(synth.rgbd_frame(1280, 720, seed=0, cx=639.5, cy=359.5)).to(dev)
@@ -510,7 +534,7 @@ def run_vg(args, rank, world, local):
         del buf
         torch.cuda.empty_cache()
         extra.update(extra_measurements(args, dev))
-    launches_per_step = 1 + 1 + 8 + 3
+    launches_per_step = 1 + 1 + 8 + 3  # extent, keys, 8 radix passes, count + scan + reduce
     out = {
         "metric": "points/s", "value": total_points / (ms / 1000), "unit": "points/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,

@@ -216,6 +216,44 @@ VG_API vg_status vg_downsample_frames_ex(
     int32_t* out_error, void* workspace, size_t workspace_bytes, int flags, vg_stream_t stream);
 
 /*
+ * Persistent voxel map.  In the paper's pipeline every filtered camera cloud is merged
+ * into a global map (STVL marks the cells of its OpenVDB grid, Sec. II-C).  A vg_map is
+ * that map kept on the GPU: an open-addressing table in device memory, keyed by the
+ * 63-bit Morton key of the voxel (R4) on one fixed lattice (origin, leaf), holding each
+ * voxel's point count and fixed-point offset sums.  Inserting frames one call at a time
+ * and extracting gives exactly what one vg_downsample of all the inserted points with
+ * that origin would give (same keys, counts and centroid bits), whatever the order and
+ * grouping of the inserts.
+ *
+ *   vg_map_create    allocates the table for about `capacity` voxels (2x slots, power
+ *                    of two) and the scratch of the extraction, once; origin is host
+ *                    float32[3], leaf finite > 0.  No other call allocates.
+ *   vg_map_insert    adds the valid points of a batch of frames (layout as in
+ *                    vg_downsample_frames; frame_offsets NULL means one frame of
+ *                    n_total points), each taken through its pose and height band
+ *                    first when poses / z_limits are given (see
+ *                    vg_downsample_frames_posed).  A point whose voxel index leaves
+ *                    [0, 2^21) on an axis records VG_ERR_RANGE and is skipped; a full
+ *                    table records VG_ERR_CAPACITY; both in *out_error (device int32,
+ *                    set, never cleared, by the call's kernels; may be NULL).
+ *   vg_map_extract   writes every voxel of the map in ascending key order: keys,
+ *                    centroids, counts (device, capacity cap), *out_num_voxels (device).
+ *                    The map is unchanged.
+ *   vg_map_clear     empties the map (asynchronous on the stream).
+ * All calls are asynchronous on `stream`; calls on one map must not overlap on the GPU.
+ */
+typedef struct vg_map vg_map;
+VG_API vg_status vg_map_create(vg_map** map, int64_t capacity, const float* origin, float leaf);
+VG_API vg_status vg_map_destroy(vg_map* map);
+VG_API vg_status vg_map_clear(vg_map* map, vg_stream_t stream);
+VG_API vg_status vg_map_insert(vg_map* map, const float* xyz, int64_t n_total,
+                               const int64_t* frame_offsets, int n_frames, const float* poses,
+                               const float* z_limits, int32_t* out_error, vg_stream_t stream);
+VG_API vg_status vg_map_extract(vg_map* map, uint64_t* out_keys, float* out_centroids,
+                                uint32_t* out_counts, int64_t cap, int64_t* out_num_voxels,
+                                int32_t* out_error, vg_stream_t stream);
+
+/*
  * Batch plan: owns a workspace for up to max_points points in max_frames frames
  * (allocated here, once), the grouping method and grid size, and a CUDA graph of the
  * batched launch sequence.  vg_downsample_batch takes the arguments of

@@ -107,6 +107,7 @@ struct FramesArg {
   int allow_narrow;        // the key kernel may pick the narrow layout (no point_to_voxel)
   const float* poses;      // device [F,12] row-major [R|t] sensor poses, or nullptr
   const float* zlims;      // device [F,2] [z_min, z_max] after the pose, or nullptr
+  int merge_frames;        // 1: every frame keys into one voxel space (no frame id)
 };
 
 // A posed call maps every point into the common frame, p' = R p + t, before anything

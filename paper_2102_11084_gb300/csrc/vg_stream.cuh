@@ -123,7 +123,7 @@ __device__ __forceinline__ uint32_t frame_prologue(const FramesArg& fr, bool hav
     maxkey = sm.kmax[w] > maxkey ? sm.kmax[w] : maxkey;
   }
   uint32_t key_shift = 64, total_bits = maxbits;
-  if (F > 1) {
+  if (F > 1 && !fr.merge_frames) {
     key_shift = maxbits;
     const uint32_t fbits = 32u - __clz(static_cast<int>(F - 1));
     total_bits = key_shift + fbits;
@@ -133,7 +133,8 @@ __device__ __forceinline__ uint32_t frame_prologue(const FramesArg& fr, bool hav
   // 0xffffffff: a 32-bit key of all ones then marks an invalid row by itself.  Morton codes
   // grow with each index, so the code of the per-axis maxima bounds every key of a frame.
   const uint64_t key_bound =
-      F > 1 ? ((uint64_t(F - 1) << key_shift) | ((uint64_t(1) << key_shift) - 1)) : maxkey;
+      key_shift < 64 ? ((uint64_t(F - 1) << key_shift) | ((uint64_t(1) << key_shift) - 1))
+                     : maxkey;
   const bool nar = fr.allow_narrow && have_extent && total_bits <= 32 && key_bound < 0xffffffffull;
   if (narrow) *narrow = nar;
   if (blockIdx.x == 0 && threadIdx.x == 0) {

@@ -88,6 +88,16 @@ _SIGS = {
                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                  ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int,
                                  ctypes.c_void_p], ctypes.c_int),
+    "vg_map_create": ([ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_float],
+                      ctypes.c_int),
+    "vg_map_destroy": ([ctypes.c_void_p], ctypes.c_int),
+    "vg_map_clear": ([ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "vg_map_insert": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                       ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                       ctypes.c_void_p], ctypes.c_int),
+    "vg_map_extract": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                        ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+                       ctypes.c_int),
     "vg_plan_create": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_int], ctypes.c_int),
     "vg_plan_destroy": ([ctypes.c_void_p], ctypes.c_int),
     "vg_plan_configure": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_int], ctypes.c_int),
@@ -466,6 +476,73 @@ def extras(attrs: Optional[torch.Tensor] = None, out_attrs: Optional[torch.Tenso
 def ex_workspace_bytes(n_total: int, n_frames: int, flags: int, ex: Optional[VoxelExtras]) -> int:
     return int(lib().vg_downsample_ex_workspace_bytes(
         int(n_total), int(n_frames), int(flags), ctypes.byref(ex) if ex else None))
+
+
+class VoxelMap:
+    """vg_map: a device-resident voxel map on one fixed lattice (origin, leaf) that frames
+    are merged into.  Extracting gives what one decimation of every inserted point with
+    that origin would give."""
+
+    def __init__(self, capacity: int, origin, leaf: float, device="cuda"):
+        self.device = torch.device(device)
+        self.origin = np.ascontiguousarray(np.asarray(origin, np.float32).reshape(3))
+        self.leaf = float(leaf)
+        self.capacity = int(capacity)
+        self.error = torch.zeros(1, dtype=torch.int32, device=self.device)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(lib().vg_map_create(ctypes.byref(h), self.capacity,
+                                       self.origin.ctypes.data_as(ctypes.c_void_p),
+                                       ctypes.c_float(self.leaf)), "vg_map_create")
+        self._h = h
+
+    def insert(self, frames, poses=None, z_limits=None,
+               stream: Optional[torch.cuda.Stream] = None) -> None:
+        """Adds the valid points of one cloud ([N,3] CUDA tensor), a list of clouds or an
+        (xyz, offsets) tuple; asynchronous."""
+        if isinstance(frames, torch.Tensor):
+            frames = [frames]
+        xyz, off_t, F, _, _ = _frame_inputs(frames, [self.leaf] * (
+            len(frames) if not _is_cat_form(frames) else len(frames[1]) - 1), None, self.device)
+        pz = _per_frame(poses, F, 12, self.device)
+        zl = _per_frame(z_limits, F, 2, self.device)
+        self._keep = (xyz, off_t, pz, zl)  # alive until the launch has read them
+        _check(lib().vg_map_insert(self._h, _ptr(xyz), xyz.shape[0], _ptr(off_t), F, _ptr(pz),
+                                   _ptr(zl), _ptr(self.error), _stream_ptr(stream)),
+               "vg_map_insert")
+
+    def extract(self, cap: Optional[int] = None,
+                stream: Optional[torch.cuda.Stream] = None) -> Decimation:
+        """Every voxel of the map in ascending key order (synchronises once)."""
+        cap = self.capacity * 2 if cap is None else int(cap)
+        d = self.device
+        keys = torch.empty(max(cap, 1), dtype=torch.int64, device=d)
+        cents = torch.empty((max(cap, 1), 3), dtype=torch.float32, device=d)
+        counts = torch.empty(max(cap, 1), dtype=torch.int32, device=d)
+        nv = torch.zeros(1, dtype=torch.int64, device=d)
+        _check(lib().vg_map_extract(self._h, _ptr(keys), _ptr(cents), _ptr(counts), cap, _ptr(nv),
+                                    _ptr(self.error), _stream_ptr(stream)), "vg_map_extract")
+        (stream or torch.cuda.current_stream(d)).synchronize()
+        _check(int(self.error.item()), "vg_map (device)")
+        v = int(nv.item())
+        return Decimation(keys[:v], cents[:v], counts[:v],
+                          torch.from_numpy(self.origin.copy()).to(d), None)
+
+    def clear(self, stream: Optional[torch.cuda.Stream] = None) -> None:
+        _check(lib().vg_map_clear(self._h, _stream_ptr(stream)), "vg_map_clear")
+        self.error.zero_()
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            torch.cuda.synchronize(self.device)
+            lib().vg_map_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Plan:
