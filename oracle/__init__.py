@@ -70,6 +70,10 @@ def _lib():
             lib.oracle_min_count.argtypes = [p, p, p, p, ctypes.c_int, i64, ctypes.c_uint64, p,
                                              i64]
             lib.oracle_min_count.restype = i64
+            lib.oracle_neighbor_counts.argtypes = [p, i64, p, p, ctypes.c_float, p]
+            lib.oracle_neighbor_counts.restype = None
+            lib.oracle_thin.argtypes = [p, i64, p, ctypes.c_float, ctypes.c_float, i64, i64, p, p]
+            lib.oracle_thin.restype = i64
             _LIB = lib
     return _LIB
 
@@ -262,3 +266,34 @@ def map_contents(frames, leaf: float, origin_xyz, poses=None, z_limits=None) -> 
         clouds.append(pose(x, p, z) if (p is not None or z is not None) else _cloud(x))
     allp = np.concatenate(clouds) if clouds else np.zeros((0, 3), np.float32)
     return downsample(allp, leaf, origin_xyz)
+
+
+def neighbor_counts(xyz, ijk, alive, r: float) -> np.ndarray:
+    """Reading R16, one count: for every remaining point, the other remaining points of
+    the 27 surrounding cells within distance r (squared distance in binary32)."""
+    a = _cloud(xyz)
+    n = a.shape[0]
+    ij = np.ascontiguousarray(np.asarray(ijk, np.int64).reshape(n, 3))
+    al = np.ascontiguousarray(np.asarray(alive, np.uint8).reshape(n))
+    out = np.zeros(max(n, 1), np.int64)
+    _lib().oracle_neighbor_counts(_ptr(a), n, _ptr(ij), _ptr(al), ctypes.c_float(r), _ptr(out))
+    return out[:n]
+
+
+def thin(xyz, cell: float, threshold: int, priority, *, radius=None, batch: int = 1000,
+         origin_xyz=None):
+    """Reading R16: the paper's neighbour-count thinning loop (Algorithm 1) with the
+    random choice of deleted points replaced by the lowest given priorities.  Returns
+    (keep bool [N], passes of the loop, status)."""
+    a = _cloud(xyz)
+    n = a.shape[0]
+    o = origin(a)[0] if origin_xyz is None else np.ascontiguousarray(
+        np.asarray(origin_xyz, np.float32).reshape(3))
+    pr = np.ascontiguousarray(np.asarray(priority, np.uint32).reshape(n))
+    keep = np.zeros(max(n, 1), np.uint8)
+    r = float(cell) if radius is None else float(radius)
+    res = int(_lib().oracle_thin(_ptr(a), n, _ptr(o), ctypes.c_float(cell), ctypes.c_float(r),
+                                 int(threshold), int(batch), _ptr(pr), _ptr(keep)))
+    if res < 0:
+        return keep[:n].astype(bool), 0, -res
+    return keep[:n].astype(bool), res, STATUS_OK

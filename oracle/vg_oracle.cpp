@@ -36,6 +36,16 @@
 //   R14 minimum points per voxel (the PCL voxel filter's option): voxels with fewer
 //       than m points are removed after grouping; the others keep their order, and
 //       their points' point_to_voxel rows follow them (removed voxels' points get -1).
+//   R16 neighbour-count thinning (Sec. II-C, Algorithm 1, its loop; Eq. 1 distance):
+//       the valid points live in the cells of the lattice (origin, cell edge) (R2/R3);
+//       repeat: every remaining point counts the other remaining points j in its own
+//       and the 26 surrounding cells with d2 = ((dx*dx + dy*dy) + dz*dz) <= r*r in
+//       binary32 (dx = x_j - x_i), and is marked when the count exceeds the threshold;
+//       if more than K points are marked, the K marked points of lowest priority are
+//       deleted (priority: a caller-given distinct rank per point, standing in for the
+//       paper's random choice) and the loop repeats; otherwise every marked point is
+//       deleted and the loop ends.  r <= cell edge makes the 27 cells hold every
+//       neighbour.
 //
 // Build: g++ -O2 -std=c++17 -ffp-contract=off -fno-fast-math -shared -fPIC.
 // Parity status: every function below is pinned by the tests in tests/test_oracle_*.py
@@ -274,6 +284,66 @@ int64_t oracle_min_count(uint64_t* keys, double* centroids, uint64_t* counts, fl
   for (int64_t i = 0; p2v && i < n; ++i)
     if (p2v[i] >= 0) p2v[i] = int32_t(row[size_t(p2v[i])]);
   return w;
+}
+
+// R16: neighbour counts of the remaining points (alive[i] != 0), the plain 27-cell search.
+void oracle_neighbor_counts(const float* xyz, int64_t n, const int64_t* ijk,
+                            const uint8_t* alive, float r, int64_t* counts) {
+  std::map<std::array<int64_t, 3>, std::vector<int64_t>> cells;
+  for (int64_t i = 0; i < n; ++i)
+    if (alive[i]) cells[{ijk[3 * i], ijk[3 * i + 1], ijk[3 * i + 2]}].push_back(i);
+  const float r2 = r * r;
+  for (int64_t i = 0; i < n; ++i) {
+    counts[i] = 0;
+    if (!alive[i]) continue;
+    for (int64_t dx = -1; dx <= 1; ++dx)
+      for (int64_t dy = -1; dy <= 1; ++dy)
+        for (int64_t dz = -1; dz <= 1; ++dz) {
+          auto it = cells.find({ijk[3 * i] + dx, ijk[3 * i + 1] + dy, ijk[3 * i + 2] + dz});
+          if (it == cells.end()) continue;
+          for (int64_t j : it->second) {
+            if (j == i) continue;
+            const float ex = xyz[3 * j] - xyz[3 * i];
+            const float ey = xyz[3 * j + 1] - xyz[3 * i + 1];
+            const float ez = xyz[3 * j + 2] - xyz[3 * i + 2];
+            float d2 = ex * ex;
+            d2 = d2 + ey * ey;
+            d2 = d2 + ez * ez;
+            if (d2 <= r2) ++counts[i];
+          }
+        }
+  }
+}
+
+// R16: the thinning loop.  keep[i] = 1 for the points that remain; returns the number of
+// passes of the loop, or -status when a voxel index leaves [0, 2^21).
+int64_t oracle_thin(const float* xyz, int64_t n, const float* origin, float cell, float r,
+                    int64_t threshold, int64_t batch, const uint32_t* priority, uint8_t* keep) {
+  std::vector<int64_t> ijk(size_t(3 * (n > 0 ? n : 1)), 0);
+  for (int64_t i = 0; i < n; ++i) {
+    keep[i] = 0;
+    if (!point_is_valid(xyz + 3 * i)) continue;
+    for (int a = 0; a < 3; ++a)
+      if (!axis_index(xyz[3 * i + a], origin[a], cell, &ijk[size_t(3 * i + a)]))
+        return -kStatusRange;
+    keep[i] = 1;
+  }
+  std::vector<int64_t> counts(size_t(n > 0 ? n : 1));
+  int64_t passes = 0;
+  for (;;) {
+    ++passes;
+    oracle_neighbor_counts(xyz, n, ijk.data(), keep, r, counts.data());
+    std::vector<std::pair<uint32_t, int64_t>> marked;  // (priority, point)
+    for (int64_t i = 0; i < n; ++i)
+      if (keep[i] && counts[size_t(i)] > threshold) marked.push_back({priority[i], i});
+    if (int64_t(marked.size()) > batch) {
+      std::sort(marked.begin(), marked.end());
+      for (int64_t k = 0; k < batch; ++k) keep[marked[size_t(k)].second] = 0;
+      continue;
+    }
+    for (const auto& m : marked) keep[m.second] = 0;
+    return passes;
+  }
 }
 
 // R12: the posed cloud.  Dropped points come out as NaN (R1 then rejects them).
