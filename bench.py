@@ -316,6 +316,23 @@ def extra_measurements(args, dev):
         ext[name] = {"ms": ms, "points_per_s": nh / (ms / 1e3), "voxels": int(o_off[1].item())}
     out["rgbd_1280x720_leaf0.02_extras"] = ext
 
+    # the paper's own neighbour-count thinning loop on the 640x480 frame: cell = radius
+    # 0.05 m, threshold 20, batches of 1000 (host-synchronised once per pass and per
+    # select round, so timed on the host clock around whole calls)
+    pr = torch.from_numpy(np.random.Generator(np.random.PCG64(5)).permutation(n)
+                          .astype(np.uint32).view(np.int32)).to(dev)
+    vg.thin(x, 0.05, 20, pr)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    reps = 5
+    for _ in range(reps):
+        th = vg.thin(x, 0.05, 20, pr)
+    torch.cuda.synchronize()
+    ms_thin = (time.perf_counter() - t0) / reps * 1e3
+    out["thin_640x480_cell0.05_t20_b1000"] = {"ms": ms_thin, "passes": th.passes,
+                                               "kept": th.num_kept,
+                                               "ms_per_pass": ms_thin / max(th.passes, 1)}
+
     # backward of the mean squared centroid loss, 307,200 points, leaf 0.05 m
     res = vg.downsample(x, 0.05, point_to_voxel=True)
     g = torch.randn_like(res.centroids)

@@ -254,6 +254,37 @@ VG_API vg_status vg_map_extract(vg_map* map, uint64_t* out_keys, float* out_cent
                                 int32_t* out_error, vg_stream_t stream);
 
 /*
+ * Neighbour-count thinning: the paper's own filter loop (Sec. II-C, Algorithm 1).  The
+ * valid points are placed in the cells (edge `cell`, origin as in vg_downsample) of a
+ * regular grid; then, pass after pass, every remaining point counts the other
+ * remaining points in its own and the 26 surrounding cells within distance `radius`
+ * (Eq. 1; squared distance in float32 as ((dx*dx + dy*dy) + dz*dz) with dx = x_j - x_i,
+ * compared with radius*radius) and is marked when the count exceeds `threshold`.  When
+ * more than `batch` points are marked, the `batch` marked points of lowest `priority`
+ * (ties by point index) are deleted and the loop goes on; otherwise every marked point
+ * is deleted and the loop ends.  The paper deletes a random batch of 1000; priority
+ * stands in for that random choice (pass a random permutation for the paper's
+ * behaviour).
+ *
+ *   xyz, n         as vg_downsample; origin float32[3] (device), read or written as
+ *                  there (VG_ORIGIN_FROM_MIN).
+ *   cell, radius   finite, 0 < radius <= cell (so the 27 cells hold every neighbour).
+ *   threshold      >= 0; batch >= 1.
+ *   priority       uint32 [n] (device).
+ *   out_keep       uint8 [n] (device): 1 for the points that remain, 0 otherwise
+ *                  (invalid points included); *out_num_kept (device int64) their number.
+ *   out_passes     host int32 or NULL: passes of the loop.
+ * Workspace: vg_thin_workspace_bytes(n) bytes.  The call synchronises the stream once per
+ * pass and once per round of the batch selection (8 bits a round).
+ */
+VG_API size_t vg_thin_workspace_bytes(int64_t n_points);
+VG_API vg_status vg_thin(const float* xyz, int64_t n, float* origin, float cell, float radius,
+                         int64_t threshold, int64_t batch, const uint32_t* priority,
+                         uint8_t* out_keep, int64_t* out_num_kept, int32_t* out_passes,
+                         int32_t* out_error, void* workspace, size_t workspace_bytes, int flags,
+                         vg_stream_t stream);
+
+/*
  * Batch plan: owns a workspace for up to max_points points in max_frames frames
  * (allocated here, once), the grouping method and grid size, and a CUDA graph of the
  * batched launch sequence.  vg_downsample_batch takes the arguments of

@@ -98,6 +98,11 @@ _SIGS = {
     "vg_map_extract": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                         ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
                        ctypes.c_int),
+    "vg_thin_workspace_bytes": ([ctypes.c_int64], ctypes.c_size_t),
+    "vg_thin": ([ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_float, ctypes.c_float,
+                 ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                 ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p], ctypes.c_int),
     "vg_plan_create": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_int], ctypes.c_int),
     "vg_plan_destroy": ([ctypes.c_void_p], ctypes.c_int),
     "vg_plan_configure": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_int], ctypes.c_int),
@@ -476,6 +481,45 @@ def extras(attrs: Optional[torch.Tensor] = None, out_attrs: Optional[torch.Tenso
 def ex_workspace_bytes(n_total: int, n_frames: int, flags: int, ex: Optional[VoxelExtras]) -> int:
     return int(lib().vg_downsample_ex_workspace_bytes(
         int(n_total), int(n_frames), int(flags), ctypes.byref(ex) if ex else None))
+
+
+class Thinned(NamedTuple):
+    keep: torch.Tensor            # bool [N]: the points that remain
+    num_kept: int
+    passes: int                   # passes of the loop
+    origin: torch.Tensor          # float32 [3]
+
+
+def thin(xyz: torch.Tensor, cell: float, threshold: int, priority: torch.Tensor, *,
+         radius: Optional[float] = None, batch: int = 1000,
+         origin: Optional[torch.Tensor] = None,
+         stream: Optional[torch.cuda.Stream] = None) -> Thinned:
+    """vg_thin: the paper's neighbour-count thinning loop (radius defaults to the cell
+    edge; ``priority`` uint32 [N] on the device orders the deleted batches)."""
+    xyz = _cuda_cloud(xyz)
+    n = xyz.shape[0]
+    dev = xyz.device
+    pr = priority.to(device=dev, dtype=torch.int32).contiguous() if priority.dtype != torch.int32 \
+        else priority.contiguous()
+    if pr.numel() != n:
+        raise ValueError("priority must have one entry per point")
+    org = (torch.zeros(3, dtype=torch.float32, device=dev) if origin is None else
+           torch.as_tensor(origin, dtype=torch.float32, device=dev).reshape(3).contiguous())
+    keep = torch.zeros(max(n, 1), dtype=torch.uint8, device=dev)
+    kept = torch.zeros(1, dtype=torch.int64, device=dev)
+    err = torch.zeros(1, dtype=torch.int32, device=dev)
+    ws = torch.empty(max(int(lib().vg_thin_workspace_bytes(n)), 256), dtype=torch.uint8,
+                     device=dev)
+    passes = ctypes.c_int32(0)
+    st = lib().vg_thin(_ptr(xyz), n, _ptr(org), ctypes.c_float(cell),
+                       ctypes.c_float(cell if radius is None else radius), int(threshold),
+                       int(batch), _ptr(pr), _ptr(keep), _ptr(kept), ctypes.byref(passes),
+                       _ptr(err), _ptr(ws), ws.numel(), ORIGIN_FROM_MIN if origin is None else 0,
+                       _stream_ptr(stream))
+    _check(st, "vg_thin")
+    (stream or torch.cuda.current_stream()).synchronize()
+    _check(int(err.item()), "vg_thin (device)")
+    return Thinned(keep[:n].bool(), int(kept.item()), int(passes.value), org)
 
 
 class VoxelMap:
