@@ -13,6 +13,9 @@ namespace vg {
 #ifndef VG_SORT_MINB
 #define VG_SORT_MINB 4
 #endif
+#ifndef VG_SORT_EARLY_TICKET
+#define VG_SORT_EARLY_TICKET 1
+#endif
 
 // Radix sort geometry (8-bit digits, 256 threads x VG_SORT_ITEMS keys per tile).
 constexpr int kRadixBits = 8;
@@ -145,8 +148,8 @@ constexpr SortLayout sort_layout(int64_t n, int frames = 1) {
   off = align_up(off + size_t(ff) * sizeof(FrameState), 256);
   L.lb_a = off;
   off = align_up(off + size_t(L.sort_tiles) * kRadix * sizeof(uint32_t), 256);
-  L.seg_lb = off;
-  off = align_up(off + size_t(L.seg_tiles) * sizeof(TileRec), 256);
+  L.seg_lb = off;  // per-tile records, then the tiles' head counts as a compact array
+  off = align_up(off + size_t(L.seg_tiles) * (sizeof(TileRec) + sizeof(uint32_t)), 256);
   L.zero_bytes = off;  // state, frames, pass-0 status rows and segment status
   L.lb_b = off;
   off = align_up(off + size_t(L.sort_tiles) * kRadix * sizeof(uint32_t), 256);

@@ -9,7 +9,8 @@
 //   seg_count  run heads per tile (keys only), and the fixed-point sum of the tile's
 //              leading entries that continue a run begun in an earlier tile (usually
 //              none or a few; the whole tile when it holds no head);
-//   seg_scan   one block: exclusive scan of the head counts = each tile's first row, V;
+//   seg_scan   one block: exclusive scan of the head counts (from a compact array) =
+//              each tile's first row, and V;
 //   seg_reduce the tile's entries are staged in shared memory and its run heads
 //              compacted in order, so consecutive threads take consecutive voxels: each
 //              sums its run and, if the run crosses the tile end, adds the leading sums
@@ -116,7 +117,7 @@ __device__ __forceinline__ void seg_count_body(
     const State* st, const FrameState* __restrict__ fs, const void* k0_, const void* p0_,
     const void* k1_, const void* p1_, const float* __restrict__ xyz,
     const float* __restrict__ poses, const uint8_t* __restrict__ attrs, int channels,
-    TileRec* recs) {
+    TileRec* recs, uint32_t* tile_heads) {
   __shared__ unsigned long long s_attr[kRedThreads / 32][4];
   using KeyT = typename Layout<kNarrow>::KeyT;
   using PayT = typename Layout<kNarrow>::PayT;
@@ -204,31 +205,37 @@ __device__ __forceinline__ void seg_count_body(
       r.lead_s[2] = lead.s[2];
       for (int c = 0; c < 4; ++c) r.lead_a[c] = la[c];
       recs[tile] = r;
+      tile_heads[tile] = th;
     }
     __syncthreads();
   }
 }
 
 // One block of 1024 threads: exclusive scan of the tiles' head counts into vbase, and V.
-// Thread t owns a contiguous run of ceil(ntiles/1024) tiles, so its loads are all in
-// flight at once; one block-wide scan of the 1024 run totals joins them.
-__global__ __launch_bounds__(1024) void seg_scan_kernel(const State* st, TileRec* recs,
-                                                        int64_t* num_voxels) {
+// The counts come from a compact array, 4096 per round: coalesced loads, one block-wide
+// scan per round, a running carry between rounds.
+__global__ __launch_bounds__(1024) void seg_scan_kernel(const State* st,
+                                                        const uint32_t* __restrict__ tile_heads,
+                                                        TileRec* recs, int64_t* num_voxels) {
   __shared__ uint32_t s_tmp[32];
   const int64_t ntiles = ceil_div(int64_t(st->nitems), kRedTile);
-  const int64_t per = ceil_div(ntiles, 1024);
-  const int64_t t0 = int64_t(threadIdx.x) * per;
-  const int64_t t1 = t0 + per < ntiles ? t0 + per : ntiles;
-  uint32_t sum = 0;
-  for (int64_t i = t0; i < t1; ++i) sum += recs[i].heads;
-  uint32_t total;
-  uint32_t run = block_excl_scan(sum, &total, s_tmp);
-  for (int64_t i = t0; i < t1; ++i) {
-    const uint32_t h = recs[i].heads;
-    recs[i].vbase = run;
-    run += h;
+  uint32_t carry = 0;
+  for (int64_t base = 0; base < ntiles; base += 4 * 1024) {
+    const int64_t i0 = base + 4 * int64_t(threadIdx.x);
+    uint32_t h[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) h[j] = i0 + j < ntiles ? tile_heads[i0 + j] : 0u;
+    uint32_t total;
+    uint32_t run = carry + block_excl_scan(h[0] + h[1] + h[2] + h[3], &total, s_tmp);
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (i0 + j < ntiles) {
+        recs[i0 + j].vbase = run;
+        run += h[j];
+      }
+    carry += total;
   }
-  if (threadIdx.x == 0) *num_voxels = total;
+  if (threadIdx.x == 0) *num_voxels = carry;
 }
 
 // Output offsets of frames (f_prev, f_new] start at voxel v.
@@ -483,7 +490,8 @@ __device__ __forceinline__ void seg_reduce_narrow(const State* st, const FrameSt
     bool ok = true;
     const uint32_t par = (phase >> b) & 1u;
     if (tile < bulk_tiles) {
-      ok = mbar_wait(&sm.bar[b], par, kDefaultSpinLimit);
+      // one warp polls; the barrier below passes the completed copy on to the others
+      if (t < 32) ok = mbar_wait(&sm.bar[b], par, kDefaultSpinLimit);
       phase ^= 1u << b;
     } else {
       for (int li = t; li < cnt; li += kRedThreads) {
@@ -616,12 +624,13 @@ struct RedPtrs {
 __global__ __launch_bounds__(kRedThreads) void seg_count_kernel(
     const State* st, const FrameState* __restrict__ fs, RedPtrs rp, const float* __restrict__ xyz,
     const float* __restrict__ poses, const uint8_t* __restrict__ attrs, int channels,
-    TileRec* recs) {
+    TileRec* recs, uint32_t* tile_heads) {
   if (st->narrow)
-    seg_count_body<true>(st, fs, rp.nk0, rp.np0, rp.nk1, rp.np1, xyz, poses, nullptr, 0, recs);
+    seg_count_body<true>(st, fs, rp.nk0, rp.np0, rp.nk1, rp.np1, xyz, poses, nullptr, 0, recs,
+                         tile_heads);
   else
     seg_count_body<false>(st, fs, rp.wk0, rp.wp0, rp.wk1, rp.wp1, xyz, poses, attrs, channels,
-                          recs);
+                          recs, tile_heads);
 }
 
 __global__ __launch_bounds__(kRedThreads, 4) void seg_reduce_kernel(
@@ -662,9 +671,10 @@ cudaError_t launch_segreduce(State* st, const FrameState* fs, int nframes,
   const int64_t tiles = ceil_div(n_max, kRedTile);
   const int gc = persistent_grid(reinterpret_cast<const void*>(seg_count_kernel), kRedThreads, 0,
                                  tiles);
+  uint32_t* tile_heads = reinterpret_cast<uint32_t*>(recs + tiles);  // after the records
   seg_count_kernel<<<gc, kRedThreads, 0, stream>>>(st, fs, rp, xyz, poses, out.attrs_in,
-                                                   out.channels, recs);
-  seg_scan_kernel<<<1, 1024, 0, stream>>>(st, recs, out.num_voxels);
+                                                   out.channels, recs, tile_heads);
+  seg_scan_kernel<<<1, 1024, 0, stream>>>(st, tile_heads, recs, out.num_voxels);
   const int gr = persistent_grid(reinterpret_cast<const void*>(seg_reduce_kernel), kRedThreads,
                                  kRedSmem, tiles);
   seg_reduce_kernel<<<gr, kRedThreads, kRedSmem, stream>>>(st, fs, nframes, rp, xyz, poses, recs,
