@@ -262,3 +262,104 @@ def latency_stats(results) -> dict:
             "p99_ms": float(np.percentile(lat, 99)), "max_ms": float(lat.max()),
             "valid_points": pts,
             "mean_batch_frames": float(np.mean([res.batch_frames for _, res in results]))}
+
+
+class CloudPipeline:
+    """Decimates a sequence of large host clouds with the copies overlapped.
+
+    ``depth`` device slots, each with its own stream, input buffer, outputs, workspace
+    and pinned host rows.  Cloud k goes to slot k % depth: host-to-device copy, one
+    vg_downsample, then -- once the host has read its voxel count -- the copy of its V
+    rows back, all on the slot's stream.  While cloud k's rows travel back, later clouds
+    are copied in and decimated on the other slots, so a sequence runs at the pace of
+    its slowest stage instead of the sum of the three.
+
+    ``run(clouds)`` yields, in order, (keys uint64 [V], centroids float32 [V, 3],
+    counts uint32 [V]) numpy views of pinned host memory; a view stays valid until the
+    pipeline takes ``depth`` more clouds.  Every cloud's result is the plain call's,
+    bit for bit.
+    """
+
+    def __init__(self, max_points: int, leaf: float, *, depth: int = 3, method: str = "sort",
+                 device="cuda"):
+        self.leaf = float(leaf)
+        self.method = method
+        self.max_points = int(max_points)
+        dev = torch.device(device)
+        self.device = dev
+        flags = vg.method_flag(method)
+        self.slots = []
+        for _ in range(max(2, int(depth))):
+            s = {"stream": torch.cuda.Stream(device=dev),
+                 "xyz": torch.empty((self.max_points, 3), dtype=torch.float32, device=dev),
+                 "buf": vg.alloc_buffers(self.max_points, dev, flags=flags),
+                 "keys": torch.empty(self.max_points, dtype=torch.int64).pin_memory(),
+                 "cents": torch.empty((self.max_points, 3), dtype=torch.float32).pin_memory(),
+                 "counts": torch.empty(self.max_points, dtype=torch.int32).pin_memory(),
+                 "nv": torch.zeros(1, dtype=torch.int64).pin_memory(),
+                 "err": torch.zeros(1, dtype=torch.int32).pin_memory(),
+                 "counted": torch.cuda.Event(), "done": torch.cuda.Event(), "v": 0,
+                 "state": "free"}
+            self.slots.append(s)
+
+    def _launch(self, s, host: torch.Tensor):
+        n = host.shape[0]
+        if n > self.max_points:
+            raise ValueError("cloud larger than the pipeline's max_points")
+        with torch.cuda.stream(s["stream"]):
+            s["xyz"][:n].copy_(host, non_blocking=True)
+            vg.downsample_into(s["xyz"][:n], self.leaf, s["buf"], origin_from_min=True,
+                               method=self.method, stream=s["stream"])
+            s["nv"].copy_(s["buf"].num_voxels, non_blocking=True)
+            s["err"].copy_(s["buf"].error, non_blocking=True)
+            s["counted"].record(s["stream"])
+        s["state"] = "counting"
+
+    def _copy_back(self, s):
+        s["counted"].synchronize()
+        if int(s["err"][0]):
+            raise vg.VGError(int(s["err"][0]), "pipeline cloud")
+        v = int(s["nv"][0])
+        s["v"] = v
+        b = s["buf"]
+        with torch.cuda.stream(s["stream"]):
+            s["keys"][:v].copy_(b.keys[:v], non_blocking=True)
+            s["cents"][:v].copy_(b.centroids[:v], non_blocking=True)
+            s["counts"][:v].copy_(b.counts[:v], non_blocking=True)
+            s["done"].record(s["stream"])
+        s["state"] = "copying"
+
+    def _result(self, s):
+        s["done"].synchronize()
+        v = s["v"]
+        s["state"] = "free"
+        return (s["keys"].numpy()[:v].view(np.uint64), s["cents"].numpy()[:v],
+                s["counts"].numpy()[:v].view(np.uint32))
+
+    def run(self, clouds):
+        """clouds: iterable of float32 [N, 3] CPU tensors (pinned for overlap)."""
+        order = collections.deque()
+        k = 0
+        for host in clouds:
+            s = self.slots[k % len(self.slots)]
+            if s["state"] != "free":  # the slot's previous cloud must be handed out first
+                while order:
+                    o = order.popleft()
+                    if o["state"] == "counting":
+                        self._copy_back(o)
+                    yield self._result(o)
+                    if o is s:
+                        break
+            self._launch(s, host)
+            # the oldest cloud still counting can now start its copy back
+            for o in order:
+                if o["state"] == "counting":
+                    self._copy_back(o)
+                    break
+            order.append(s)
+            k += 1
+        while order:
+            o = order.popleft()
+            if o["state"] == "counting":
+                self._copy_back(o)
+            yield self._result(o)
