@@ -39,7 +39,7 @@ REFERENCE_SAMPLE = 250_000    # --impl reference: points per step
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--steps", type=int, default=200)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="vg", choices=["vg", "reference"])
     p.add_argument("--n", type=int, default=N_POINTS)
@@ -98,26 +98,43 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.proc = None
         self.gpu = gpu_index
+        self.stamped = []
+
+    def _read(self):
+        for line in self.proc.stdout:
+            if line.strip():
+                self.stamped.append((time.perf_counter(), line))
 
     def __enter__(self):
+        import threading
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
                  "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
+        if self.proc is not None:
+            self.reader = threading.Thread(target=self._read, daemon=True)
+            self.reader.start()
+            t_wait = time.perf_counter() + 5.0  # the sampler is running before timing starts
+            while not self.stamped and time.perf_counter() < t_wait and self.proc.poll() is None:
+                time.sleep(0.01)
+        self.t0 = time.perf_counter()
         return self
 
     def __exit__(self, *a):
+        self.t1 = time.perf_counter()
         self.lines = []
         if self.proc is not None:
             self.proc.terminate()
             try:
-                out, _ = self.proc.communicate(timeout=5)
+                self.proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
-                out, _ = self.proc.communicate()
-            self.lines = [l for l in out.splitlines() if l.strip()]
+                self.proc.wait()
+            self.reader.join(timeout=5)
+            inside = [l for ts, l in self.stamped if self.t0 <= ts <= self.t1 + 0.05]
+            self.lines = inside or [l for _, l in self.stamped[-1:]]
 
     def summary(self):
         if not getattr(self, "lines", None):
@@ -366,7 +383,9 @@ def run_reference(args, rank, world):
     import oracle
     from paper_2102_11084_gb300 import synth
     xyz = synth.fused_map(args.n, seed=0)
-    sample = np.ascontiguousarray(xyz[:REFERENCE_SAMPLE])
+    # bounded work: the whole run stays near a minute of CPU time whatever --steps is
+    per_step = max(20_000, REFERENCE_SAMPLE * 50 // max(args.steps + args.warmup, 50))
+    sample = np.ascontiguousarray(xyz[:per_step])
     for _ in range(args.warmup):
         oracle.downsample(sample, args.leaf)
     times = []
@@ -375,8 +394,8 @@ def run_reference(args, rank, world):
         oracle.downsample(sample, args.leaf)
         times.append(time.perf_counter() - t0)
     ms = 1000 * statistics.mean(times)
-    value = REFERENCE_SAMPLE / (ms / 1000)
-    sample_desc = f"first {REFERENCE_SAMPLE} points of the workload cloud per step, 1 thread"
+    value = sample.shape[0] / (ms / 1000)
+    sample_desc = f"first {sample.shape[0]} points of the workload cloud per step, 1 thread"
     print(json.dumps({
         "impl": "reference", "metric": "points/s", "value": value, "unit": "points/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
