@@ -157,10 +157,15 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# the sources of the kernels the bench step launches (their traffic is profiled)
+STEP_KERNEL_SOURCES = ("vg_device.cuh", "vg_internal.h", "vg_keys.cu", "vg_reduce.cu",
+                       "vg_sort.cu", "vg_stream.cuh")
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2102_11084_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in STEP_KERNEL_SOURCES:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]

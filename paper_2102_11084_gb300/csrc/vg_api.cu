@@ -6,6 +6,8 @@
 #include <cmath>
 #include <cstring>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/vg.h"
 #include "vg_api_internal.h"
 #include "vg_internal.h"
@@ -90,6 +92,13 @@ void mark(int k, cudaStream_t stream) {
     cudaEventRecord(static_cast<cudaEvent_t>(g_events[k]), stream);
 }
 
+// NVTX range around a call's host-side launch sequence (seen by NVTX-aware profilers;
+// free when none is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+
 bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
 vg_status cuda_status(cudaError_t e) { return e == cudaSuccess ? VG_OK : VG_ERR_CUDA; }
@@ -129,6 +138,7 @@ vg_status run_frames(const float* xyz, const FramesArg& fr, bool from_min, const
   const int64_t n = fr.n;
   const int F = fr.nframes;
   const int method = method_of(flags);
+  const NvtxRange range(method == VG_METHOD_HASH ? "vg: decimate (hash)" : "vg: decimate (sort)");
   const size_t need = frames_workspace_bytes(n, F, flags);
   if (!workspace || workspace_bytes < need) return VG_ERR_WORKSPACE;
   char* ws = static_cast<char*>(workspace);

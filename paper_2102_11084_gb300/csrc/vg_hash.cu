@@ -110,8 +110,8 @@ __global__ __launch_bounds__(kStreamThreads) void hash_insert_kernel(
     }
     const float o[3] = {sm.org[f][0], sm.org[f][1], sm.org[f][2]};
     const float leaf = sm.leaf[f];
-    const float rleaf = fast_leaf(leaf) ? __fdiv_rn(1.0f, leaf) : 0.0f;
-    const float inv_unit = quant_inv_unit(leaf);
+    const float rleaf = sm.rleaf[f];
+    const float inv_unit = sm.inv_unit[f];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       uint64_t local = 0;

@@ -13,6 +13,9 @@ namespace vg {
 #ifndef VG_SORT_MINB
 #define VG_SORT_MINB 4
 #endif
+#ifndef VG_RED_DIRECT_CENTROIDS
+#define VG_RED_DIRECT_CENTROIDS 0
+#endif
 #ifndef VG_SORT_EARLY_TICKET
 #define VG_SORT_EARLY_TICKET 1
 #endif

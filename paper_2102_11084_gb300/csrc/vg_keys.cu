@@ -57,7 +57,12 @@ template <bool kPosed>
 __global__ __launch_bounds__(kStreamThreads) void origin_kernel(const float* __restrict__ xyz,
                                                                 FramesArg fr, FrameState* fs,
                                                                 int* err) {
-  __shared__ ChunkSmem sm;
+  // only the frame/chunk map (no per-frame origin or leaf is needed here)
+  __shared__ struct {
+    int64_t off[kMaxFrames + 1];
+    uint32_t cstart[kMaxFrames + 1];
+    uint32_t tmp[kStreamThreads / 32];
+  } sm;
   __shared__ float red[kStreamThreads / 32][6];
   const uint32_t T = build_chunk_map(fr, sm.off, sm.cstart, sm.tmp, err);
   uint32_t c0, c1;
@@ -158,10 +163,10 @@ __global__ __launch_bounds__(kStreamThreads) void key_kernel(
     }
     const float o[3] = {sm.org[f][0], sm.org[f][1], sm.org[f][2]};
     const float leaf = sm.leaf[f];
-    const float rleaf = fast_leaf(leaf) ? __fdiv_rn(1.0f, leaf) : 0.0f;
+    const float rleaf = sm.rleaf[f];
     uint64_t k[4];
     uint64_t pay[4];
-    const float inv_unit = quant_inv_unit(leaf);
+    const float inv_unit = sm.inv_unit[f];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       uint32_t ijk[3];

@@ -581,9 +581,15 @@ __device__ __forceinline__ void seg_reduce_narrow(const State* st, const FrameSt
         acc_centroid(local, run, o, leaf, leaf, c);
         out.keys[cur] = local;
         out.counts[cur] = run.n;
+#if VG_RED_DIRECT_CENTROIDS
+        out.centroids[3 * size_t(cur)] = c[0];
+        out.centroids[3 * size_t(cur) + 1] = c[1];
+        out.centroids[3 * size_t(cur) + 2] = c[2];
+#else
         sm.gcen[3 * v] = c[0];
         sm.gcen[3 * v + 1] = c[1];
         sm.gcen[3 * v + 2] = c[2];
+#endif
         if (out.sums) {
           out.sums[3 * size_t(cur)] = run.s[0];
           out.sums[3 * size_t(cur) + 1] = run.s[1];
@@ -599,9 +605,11 @@ __device__ __forceinline__ void seg_reduce_narrow(const State* st, const FrameSt
         if (last_run) mark_frames(out.frame_offsets, fk, uint32_t(nframes), cur + 1);
       }
     }
+#if !VG_RED_DIRECT_CENTROIDS
     __syncthreads();
     for (int x = t; x < 3 * static_cast<int>(theads); x += kRedThreads)
       if (int64_t(vbase) + x / 3 < out.cap) out.centroids[3 * size_t(vbase) + x] = sm.gcen[x];
+#endif
     __syncthreads();
     vbase = nvbase;
     theads = ntheads;

@@ -12,6 +12,8 @@ struct ChunkSmem {
   uint32_t tmp[kStreamThreads / 32];
   float org[kMaxFrames][3];
   float leaf[kMaxFrames];
+  float rleaf[kMaxFrames];  // fl(1/leaf) when the fast index applies, else 0
+  float inv_unit[kMaxFrames];  // the fixed-point scale of the frame's offsets
   uint32_t bits[kStreamThreads / 32];
   unsigned long long kmax[kStreamThreads / 32];
 };
@@ -85,6 +87,8 @@ __device__ __forceinline__ uint32_t frame_prologue(const FramesArg& fr, bool hav
       sm.org[f][a] = o[a];
     }
     sm.leaf[f] = leaf;
+    sm.rleaf[f] = fast_leaf(leaf) ? __fdiv_rn(1.0f, leaf) : 0.0f;
+    sm.inv_unit[f] = quant_inv_unit(leaf);
     if (blockIdx.x == 0) {
       for (int a = 0; a < 3; ++a) {
         fs[f].origin[a] = o[a];

@@ -647,7 +647,29 @@ class Plan:
             _stream_ptr(stream), ms)
         _check(st, "vg_plan_tune")
         names = [f"{m}@{g}" for m in ("sort", "hash") for g in (4, 8, 16)]
-        return dict(zip(names, list(ms)))
+        self.last_tuning = dict(zip(names, list(ms)))
+        return self.last_tuning
+
+    def save_tuning(self, path: str, workload: str = "") -> None:
+        """Writes the plan's chosen method and grid (and the timings that chose them) to a
+        JSON file, so that a later process can skip the tuning runs."""
+        import json
+        rec = {"max_frames": self.max_frames, "max_points": self.max_points,
+               "workload": workload, "device": torch.cuda.get_device_name(),
+               **{k: v for k, v in self.get().items() if k != "workspace_bytes"},
+               "candidates_ms": getattr(self, "last_tuning", None)}
+        with open(path, "w") as f:
+            json.dump(rec, f, indent=1)
+
+    def load_tuning(self, path: str) -> dict:
+        """Applies a choice written by save_tuning (same plan sizes required)."""
+        import json
+        with open(path) as f:
+            rec = json.load(f)
+        if rec.get("max_frames") != self.max_frames or rec.get("max_points") != self.max_points:
+            raise ValueError("tuning was recorded for a plan of other sizes")
+        self.configure(rec["method"], int(rec["grid_per_sm"]))
+        return rec
 
 
 # ---- pyramid (step a6) -----------------------------------------------------------------

@@ -124,6 +124,27 @@ def test_plan_graph_replay_and_tuner():
     plan.close()
 
 
+def test_plan_tuning_persists(tmp_path):
+    frames, leaves = small_batch(seed=5, frames=6)
+    b = _plan_buffers(frames, leaves)
+    plan = vg.Plan(8, b["xyz"].shape[0])
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        plan.tune(**b, reps=1, stream=s)
+    chosen = plan.get()
+    path = str(tmp_path / "tuning.json")
+    plan.save_tuning(path, workload="small batch")
+    other = vg.Plan(8, b["xyz"].shape[0])
+    other.configure("hash" if chosen["method"] == "sort" else "sort", 4)
+    rec = other.load_tuning(path)
+    assert other.get()["method"] == chosen["method"] == rec["method"]
+    assert other.get()["grid_per_sm"] == chosen["grid_per_sm"]
+    with pytest.raises(ValueError):
+        vg.Plan(9, b["xyz"].shape[0]).load_tuning(path)
+    plan.close()
+    other.close()
+
+
 def test_batch_64_frames_full_size():
     """The 64-frame uneven batch (20k-921k points per 1280x720 frame, leaf per frame from
     {0.02, 0.05, 0.1}): every frame bit-equal to its solo call, four sampled frames
