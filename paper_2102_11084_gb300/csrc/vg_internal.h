@@ -13,8 +13,8 @@ namespace vg {
 #ifndef VG_SORT_MINB
 #define VG_SORT_MINB 4
 #endif
-#ifndef VG_RED_DIRECT_CENTROIDS
-#define VG_RED_DIRECT_CENTROIDS 0
+#ifndef VG_RED_MINB
+#define VG_RED_MINB 4
 #endif
 #ifndef VG_SORT_EARLY_TICKET
 #define VG_SORT_EARLY_TICKET 1

@@ -14,7 +14,8 @@
 //   seg_reduce the tile's entries are staged in shared memory and its run heads
 //              compacted in order, so consecutive threads take consecutive voxels: each
 //              sums its run and, if the run crosses the tile end, adds the leading sums
-//              of the following tiles; rows are written out coalesced.
+//              of the following tiles, and writes its row (consecutive threads write
+//              consecutive rows).
 // Integer sums make the result independent of tiling and of the order of the points.
 // Two layouts: narrow (32-bit keys, packed offsets as payload) and wide (64-bit keys,
 // point index as payload, coordinates gathered; also gives point_to_voxel).  The
@@ -260,7 +261,6 @@ __device__ __forceinline__ void seg_reduce_body(
   int* sq = reinterpret_cast<int*>(skey + kRedTile);                // [3][kRedTile]
   uint32_t* sidx = reinterpret_cast<uint32_t*>(sq + 3 * kRedTile);  // [kRedTile]
   uint32_t* hpos = sidx + kRedTile;                                 // [kRedTile + 1]
-  float* gcen = reinterpret_cast<float*>(hpos + kRedTile + 4);      // [3 * kRedTile]
 
   const int t = threadIdx.x;
   const int64_t nitems = st->nitems;
@@ -392,9 +392,9 @@ __device__ __forceinline__ void seg_reduce_body(
         acc_centroid(local, run, o, leaf, leaf, c);
         out.keys[cur] = local;
         out.counts[cur] = run.n;
-        gcen[3 * v] = c[0];
-        gcen[3 * v + 1] = c[1];
-        gcen[3 * v + 2] = c[2];
+        out.centroids[3 * size_t(cur)] = c[0];
+        out.centroids[3 * size_t(cur) + 1] = c[1];
+        out.centroids[3 * size_t(cur) + 2] = c[2];
         if (out.sums) {
           out.sums[3 * size_t(cur)] = run.s[0];
           out.sums[3 * size_t(cur) + 1] = run.s[1];
@@ -411,11 +411,6 @@ __device__ __forceinline__ void seg_reduce_body(
       }
     }
     __syncthreads();
-
-    // coalesced write-out of this tile's centroids [vbase, vbase + theads)
-    for (int x = t; x < 3 * theads; x += kRedThreads)
-      if (int64_t(vbase) + x / 3 < out.cap) out.centroids[3 * size_t(vbase) + x] = gcen[x];
-    __syncthreads();
   }
 }
 
@@ -426,7 +421,6 @@ struct NarrowRedSmem {
   uint32_t keys[2][kRedTile];
   unsigned long long pay[2][kRedTile];
   uint32_t hpos[kRedTile + 4];
-  float gcen[3 * kRedTile];
   unsigned long long bar[2];
   TileRec after;  // record of the tile that follows the current one
 };
@@ -581,15 +575,9 @@ __device__ __forceinline__ void seg_reduce_narrow(const State* st, const FrameSt
         acc_centroid(local, run, o, leaf, leaf, c);
         out.keys[cur] = local;
         out.counts[cur] = run.n;
-#if VG_RED_DIRECT_CENTROIDS
         out.centroids[3 * size_t(cur)] = c[0];
         out.centroids[3 * size_t(cur) + 1] = c[1];
         out.centroids[3 * size_t(cur) + 2] = c[2];
-#else
-        sm.gcen[3 * v] = c[0];
-        sm.gcen[3 * v + 1] = c[1];
-        sm.gcen[3 * v + 2] = c[2];
-#endif
         if (out.sums) {
           out.sums[3 * size_t(cur)] = run.s[0];
           out.sums[3 * size_t(cur) + 1] = run.s[1];
@@ -605,11 +593,6 @@ __device__ __forceinline__ void seg_reduce_narrow(const State* st, const FrameSt
         if (last_run) mark_frames(out.frame_offsets, fk, uint32_t(nframes), cur + 1);
       }
     }
-#if !VG_RED_DIRECT_CENTROIDS
-    __syncthreads();
-    for (int x = t; x < 3 * static_cast<int>(theads); x += kRedThreads)
-      if (int64_t(vbase) + x / 3 < out.cap) out.centroids[3 * size_t(vbase) + x] = sm.gcen[x];
-#endif
     __syncthreads();
     vbase = nvbase;
     theads = ntheads;
@@ -641,7 +624,7 @@ __global__ __launch_bounds__(kRedThreads) void seg_count_kernel(
                           recs, tile_heads);
 }
 
-__global__ __launch_bounds__(kRedThreads, 4) void seg_reduce_kernel(
+__global__ __launch_bounds__(kRedThreads, VG_RED_MINB) void seg_reduce_kernel(
     const State* st, const FrameState* __restrict__ fs, int nframes, RedPtrs rp,
     const float* __restrict__ xyz, const float* __restrict__ poses,
     const TileRec* __restrict__ recs, SegOut out, int* err) {
@@ -656,7 +639,7 @@ __global__ __launch_bounds__(kRedThreads, 4) void seg_reduce_kernel(
 
 // Bytes of dynamic shared memory of seg_reduce_kernel.
 constexpr size_t kRedSmemWide = size_t(kRedTile) * (sizeof(uint64_t) + 3 * sizeof(int) +
-                                                    2 * sizeof(uint32_t) + 3 * sizeof(float)) +
+                                                    2 * sizeof(uint32_t)) +
                                 4 * sizeof(uint32_t);
 constexpr size_t kRedSmem =
     kRedSmemWide > sizeof(NarrowRedSmem) ? kRedSmemWide : sizeof(NarrowRedSmem);
