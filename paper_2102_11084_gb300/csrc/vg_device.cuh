@@ -373,6 +373,11 @@ __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
+// Hint: bring [p, p + bytes) into L2 (bulk prefetch; p and bytes multiples of 16).
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 // Waits (bounded: `limit` polls) for the phase of parity `parity` to complete.
 __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t parity,
                                           uint32_t limit) {

@@ -16,6 +16,12 @@ namespace vg {
 #ifndef VG_RED_MINB
 #define VG_RED_MINB 4
 #endif
+#ifndef VG_KEY_MINB  // blocks/SM of the (unposed) key kernel: 4 fits 64 registers
+#define VG_KEY_MINB 4
+#endif
+#ifndef VG_SORT_PREFETCH
+#define VG_SORT_PREFETCH 1
+#endif
 #ifndef VG_SORT_EARLY_TICKET
 #define VG_SORT_EARLY_TICKET 1
 #endif

@@ -6,6 +6,8 @@
 // leaf, keyed by a 63-bit Morton code.  Both kernels stream xyz once with 16-byte loads
 // (4 points = 3 float4 per lane) over chunks of 1024 points that never cross a frame,
 // each block walking a contiguous run of chunks; they are HBM-bound.
+#include <type_traits>
+
 #include "vg_device.cuh"
 #include "vg_internal.h"
 #include "vg_stream.cuh"
@@ -101,33 +103,25 @@ __global__ __launch_bounds__(kStreamThreads) void origin_kernel(const float* __r
   if (cur >= 0) flush_extent(mn, mx, fs, cur, red);
 }
 
-// a2: sort key per point (kKeySentinel for invalid or out-of-range rows), plus the
-// digit-0 histogram of the valid keys, the number of valid points and the largest key.
-// Block 0 also publishes every frame's origin and leaf (and the minimum to the caller
-// when the origin is computed) and the key shift.
-template <bool kPosed>
-__global__ __launch_bounds__(kStreamThreads) void key_kernel(
-    const float* __restrict__ xyz, FramesArg fr, int have_extent, State* st, FrameState* fs,
-    uint64_t* __restrict__ keys, uint32_t* __restrict__ keys32, uint64_t* __restrict__ payload,
-    int* err) {
-  __shared__ ChunkSmem sm;
-  __shared__ uint32_t hist[kRadix];
-  __shared__ unsigned long long wmax[kStreamThreads / 32];
-  __shared__ uint32_t wcount[kStreamThreads / 32];
+// The streaming loop of the key kernel over this block's chunks.  kNarrow: 32-bit keys
+// (every key fits, checked from the extents) and packed corner offsets as payload;
+// otherwise 64-bit keys only.  Accumulates the digit-0 histogram, #valid and the largest
+// key.
+template <bool kPosed, bool kNarrow>
+__device__ __forceinline__ void key_loop(const float* __restrict__ xyz, const FramesArg& fr,
+                                         const ChunkSmem& sm, uint32_t c0, uint32_t c1,
+                                         uint32_t key_shift, uint64_t* __restrict__ keys,
+                                         uint32_t* __restrict__ keys32,
+                                         uint64_t* __restrict__ payload, uint32_t* hist,
+                                         uint32_t& nvalid, unsigned long long& kmax_out,
+                                         bool& range_bad) {
+  using KeyT = typename std::conditional<kNarrow, uint32_t, uint64_t>::type;
   const int F = fr.nframes;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int d = threadIdx.x; d < kRadix; d += kStreamThreads) hist[d] = 0;
-  const uint32_t T = build_chunk_map(fr, sm.off, sm.cstart, sm.tmp, err);
-  bool narrow = false;
-  const uint32_t key_shift = frame_prologue(fr, have_extent != 0, st, fs, T, sm, err, &narrow);
-  narrow = narrow && keys32 && payload;
-  uint32_t c0, c1;
-  block_range(T, &c0, &c1);
   const bool xyz_vec = (reinterpret_cast<uintptr_t>(xyz) & 15) == 0;
-  const bool key_vec = (reinterpret_cast<uintptr_t>(keys) & 15) == 0;
-  uint32_t nvalid = 0;
-  unsigned long long kmax = 0;
-  bool range_bad = false;
+  const bool key_vec = kNarrow ? (reinterpret_cast<uintptr_t>(keys32) & 15) == 0
+                               : (reinterpret_cast<uintptr_t>(keys) & 15) == 0;
+  const bool pay_vec = !kNarrow || (reinterpret_cast<uintptr_t>(payload) & 15) == 0;
+  KeyT kmax = 0;
   // software pipeline: the next chunk's points are loaded while this one is computed
   float vn[12];
   if (c0 < c1) {
@@ -164,27 +158,31 @@ __global__ __launch_bounds__(kStreamThreads) void key_kernel(
     const float o[3] = {sm.org[f][0], sm.org[f][1], sm.org[f][2]};
     const float leaf = sm.leaf[f];
     const float rleaf = sm.rleaf[f];
-    uint64_t k[4];
-    uint64_t pay[4];
     const float inv_unit = sm.inv_unit[f];
+    KeyT k[4];
+    uint64_t pay[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       uint32_t ijk[3];
       const bool ok = point_index(v[3 * j], v[3 * j + 1], v[3 * j + 2], o, leaf, rleaf, ijk,
                                   &range_bad);
-      // narrow layout: every key is below 2^32 (checked from the extents), so the indices
-      // have at most 11 bits and the interleave runs on 32-bit words
-      const uint64_t local =
-          narrow ? uint64_t(spread3_32(ijk[0]) | (spread3_32(ijk[1]) << 1) |
-                            (spread3_32(ijk[2]) << 2))
-                 : morton3(ijk[0], ijk[1], ijk[2]);
-      k[j] = ok ? key_compose(static_cast<uint32_t>(f), local, key_shift) : kKeySentinel;
+      if (kNarrow) {
+        // the indices have at most 11 bits: the interleave runs on 32-bit words
+        const uint32_t local = spread3_32(ijk[0]) | (spread3_32(ijk[1]) << 1) |
+                               (spread3_32(ijk[2]) << 2);
+        k[j] = ok ? static_cast<KeyT>(key_compose(static_cast<uint32_t>(f), local, key_shift))
+                  : static_cast<KeyT>(kKeySentinel);
+      } else {
+        k[j] = ok ? key_compose(static_cast<uint32_t>(f), morton3(ijk[0], ijk[1], ijk[2]),
+                                key_shift)
+                  : kKeySentinel;
+      }
       pay[j] = kPayloadInvalid;
       if (ok) {
         ++nvalid;
         kmax = k[j] > kmax ? k[j] : kmax;
-        atomicAdd(&hist[k[j] & (kRadix - 1)], 1u);
-        if (narrow) {
+        atomicAdd(&hist[uint32_t(k[j]) & (kRadix - 1)], 1u);
+        if (kNarrow) {
           int qq[3];
 #pragma unroll
           for (int a = 0; a < 3; ++a)
@@ -193,8 +191,8 @@ __global__ __launch_bounds__(kStreamThreads) void key_kernel(
         }
       }
     }
-    if (narrow) {
-      if (key_vec && vec && p0 + 4 <= end) {
+    if (kNarrow) {
+      if (key_vec && pay_vec && vec && p0 + 4 <= end) {
         __stcg(reinterpret_cast<uint4*>(keys32 + p0),
                make_uint4(uint32_t(k[0]), uint32_t(k[1]), uint32_t(k[2]), uint32_t(k[3])));
         ulonglong2* dst = reinterpret_cast<ulonglong2*>(payload + p0);
@@ -210,14 +208,47 @@ __global__ __launch_bounds__(kStreamThreads) void key_kernel(
       }
     } else if (key_vec && vec && p0 + 4 <= end) {
       ulonglong2* dst = reinterpret_cast<ulonglong2*>(keys + p0);
-      __stcg(dst, make_ulonglong2(k[0], k[1]));
-      __stcg(dst + 1, make_ulonglong2(k[2], k[3]));
+      __stcg(dst, make_ulonglong2(uint64_t(k[0]), uint64_t(k[1])));
+      __stcg(dst + 1, make_ulonglong2(uint64_t(k[2]), uint64_t(k[3])));
     } else {
 #pragma unroll
       for (int j = 0; j < 4; ++j)
-        if (p0 + j < end) keys[p0 + j] = k[j];
+        if (p0 + j < end) keys[p0 + j] = uint64_t(k[j]);
     }
   }
+  kmax_out = kmax;
+}
+
+// a2: sort key per point (kKeySentinel for invalid or out-of-range rows), plus the
+// digit-0 histogram of the valid keys, the number of valid points and the largest key.
+// Block 0 also publishes every frame's origin and leaf (and the minimum to the caller
+// when the origin is computed) and the key shift.
+template <bool kPosed>
+__global__ __launch_bounds__(kStreamThreads, kPosed ? 1 : VG_KEY_MINB) void key_kernel(
+    const float* __restrict__ xyz, FramesArg fr, int have_extent, State* st, FrameState* fs,
+    uint64_t* __restrict__ keys, uint32_t* __restrict__ keys32, uint64_t* __restrict__ payload,
+    int* err) {
+  __shared__ ChunkSmem sm;
+  __shared__ uint32_t hist[kRadix];
+  __shared__ unsigned long long wmax[kStreamThreads / 32];
+  __shared__ uint32_t wcount[kStreamThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int d = threadIdx.x; d < kRadix; d += kStreamThreads) hist[d] = 0;
+  const uint32_t T = build_chunk_map(fr, sm.off, sm.cstart, sm.tmp, err);
+  bool narrow = false;
+  const uint32_t key_shift = frame_prologue(fr, have_extent != 0, st, fs, T, sm, err, &narrow);
+  narrow = narrow && keys32 && payload;
+  uint32_t c0, c1;
+  block_range(T, &c0, &c1);
+  uint32_t nvalid = 0;
+  unsigned long long kmax = 0;
+  bool range_bad = false;
+  if (narrow)
+    key_loop<kPosed, true>(xyz, fr, sm, c0, c1, key_shift, keys, keys32, payload, hist, nvalid,
+                           kmax, range_bad);
+  else
+    key_loop<kPosed, false>(xyz, fr, sm, c0, c1, key_shift, keys, keys32, payload, hist, nvalid,
+                            kmax, range_bad);
   if (__any_sync(kFullMask, range_bad) && lane == 0) set_error(err, kErrRange);
 #pragma unroll
   for (int off = 16; off; off >>= 1) {

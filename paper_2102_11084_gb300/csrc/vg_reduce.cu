@@ -174,6 +174,8 @@ __device__ __forceinline__ void seg_count_body(
     if (fh > cnt) fh = cnt;
     // leading entries [0, fh): the continuation of a run begun before this tile
     Acc lead = acc_zero();
+    // (fh is the same in every thread: the block skips the sums when the tile opens with
+    // a head, as most tiles do)
     for (int li = t; li < fh; li += kRedThreads) {
       const int64_t gi = base + li;
       int q[3];
@@ -184,9 +186,9 @@ __device__ __forceinline__ void seg_count_body(
       lead.s[1] += q[1];
       lead.s[2] += q[2];
     }
-    lead = block_sum_acc(lead, s_acc);
+    if (fh > 0) lead = block_sum_acc(lead, s_acc);
     unsigned long long la[4] = {0, 0, 0, 0};
-    if (!kNarrow && attrs) {  // attribute sums of the same leading entries (wide layout)
+    if (!kNarrow && attrs && fh > 0) {  // attribute sums of the same leading entries
       for (int li = t; li < fh; li += kRedThreads) {
         const uint8_t* a = attrs + size_t(uint32_t(P[base + li])) * channels;
 #pragma unroll

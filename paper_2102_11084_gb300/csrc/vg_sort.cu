@@ -236,6 +236,18 @@ __device__ __forceinline__ void onesweep_body(
                 1u);
   }
   __syncthreads();
+#if VG_SORT_EARLY_TICKET && VG_SORT_PREFETCH
+  // the next tile's keys and payloads start their way into L2 while this one scatters
+  if (t == 0 && next_tile < ntiles) {
+    const int64_t b = int64_t(next_tile) * kSortTile;
+    const int64_t m = n_items - b < kSortTile ? n_items - b : kSortTile;
+    const uint32_t kb = static_cast<uint32_t>(m * sizeof(KeyT)) & ~15u;
+    const uint32_t pb = static_cast<uint32_t>(m * sizeof(PayT)) & ~15u;
+    if (kb && ((reinterpret_cast<uintptr_t>(keys_in + b) & 15) == 0)) prefetch_l2(keys_in + b, kb);
+    if (pb && !(raw && !kNarrow) && ((reinterpret_cast<uintptr_t>(pay_in + b) & 15) == 0))
+      prefetch_l2(pay_in + b, pb);
+  }
+#endif
   PayT* spay = reinterpret_cast<PayT*>(sbuf);
 #pragma unroll
   for (int j = 0; j < kSortItems; ++j)
