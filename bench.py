@@ -158,8 +158,8 @@ class ClockSampler:
 
 
 # the sources of the kernels the bench step launches (their traffic is profiled)
-STEP_KERNEL_SOURCES = ("vg_device.cuh", "vg_internal.h", "vg_keys.cu", "vg_reduce.cu",
-                       "vg_sort.cu", "vg_stream.cuh")
+STEP_KERNEL_SOURCES = ("vg_bucket.cu", "vg_device.cuh", "vg_internal.h", "vg_keys.cu",
+                       "vg_reduce.cu", "vg_sort.cu", "vg_stream.cuh")
 
 
 def kernel_source_hash():
@@ -442,8 +442,9 @@ def run_vg(args, rank, world, local):
     stream = torch.cuda.current_stream(dev)
 
     # stage events (profiling hook of the C ABI): one set per timed step
-    # sort path: extent/origin, keys, 8 radix passes (the needed ones do work), reduction
-    n_stages = 11
+    # sort path: extent/origin, keys, 8 radix passes (the needed ones do work), the bucket
+    # tail (only with method "sort_bucket"; an empty stage here) and the segmented reduction
+    n_stages = 12
     import ctypes
 
     def call():
@@ -488,28 +489,33 @@ def run_vg(args, rank, world, local):
     nvalid = int(np.isfinite(xyz_np).all(axis=1).sum())
 
     # per-stage device times (ms, mean over steps)
-    stage_names = ["origin", "keys"] + [f"sort_pass{p}" for p in range(8)] + ["segreduce"]
+    stage_names = (["origin", "keys"] + [f"sort_pass{p}" for p in range(8)] +
+                   ["bucket_tail", "segreduce"])
     stage_ms = np.zeros(n_stages)
     for s in ev_sets:
         for i in range(n_stages):
             stage_ms[i] += s[i].elapsed_time(s[i + 1])
     stage_ms /= args.steps
-    passes = int(np.ceil(max(1, int(buf.keys[V - 1].item()).bit_length()) / 8)) if V else 1
-    narrow = passes <= 4  # the key kernel picks 32-bit keys when the largest key fits
-    # algorithmic bytes per launch of each kernel (narrow: 4 B key + 8 B packed offsets)
+    # passes that did work (the others return at once, in a few microseconds)
+    passes = max(1, int((stage_ms[2:10] > 0.02).sum()))
+    narrow = int(buf.keys[V - 1].item()).bit_length() <= 32 if V else True
+    bucket = stage_ms[10] > stage_ms[11]  # the narrow layout's bucket tail ran
+    # algorithmic bytes per launch of each kernel (narrow: 4 B key + 8 B packed offsets;
+    # every output row: 8 B key + 12 B centroid + 4 B count)
     algo = {
         "origin": 12.0 * n,
         "keys": 12.0 * n + 12.0 * n,
         "sort_pass": 24.0 * nvalid,
-        "segreduce": (12.0 if narrow else 24.0) * nvalid + 16.0 * V,
+        "bucket_tail": 12.0 * nvalid + 24.0 * V,
+        "segreduce": ((4.0 + 12.0) if narrow else (8.0 + 24.0)) * nvalid + 24.0 * V,
     }
     sort_ms = stage_ms[2:2 + passes]
-    seg_ms = stage_ms[10]
+    tail = "bucket_tail" if bucket else "segreduce"
     kern = {
         "origin": (stage_ms[0], algo["origin"], 1),
         "keys": (stage_ms[1], algo["keys"], 1),
         "sort_pass": (float(sort_ms.mean()), algo["sort_pass"], passes),
-        "segreduce": (seg_ms, algo["segreduce"], 1),
+        tail: (float(stage_ms[10] if bucket else stage_ms[11]), algo[tail], 1),
     }
     dom = max(kern, key=lambda k: kern[k][0] * kern[k][2])
     peaks, peak_src = measured_peaks()
@@ -517,7 +523,7 @@ def run_vg(args, rank, world, local):
     d_ms, d_bytes, _ = kern[dom]
     achieved = d_bytes / (d_ms / 1000) / 1e9
     traffic = profiled_traffic(dom, {"origin": n, "keys": n, "sort_pass": nvalid,
-                                     "segreduce": nvalid}[dom])
+                                     "bucket_tail": nvalid, "segreduce": nvalid}[dom])
     path_bytes = 12.0 * n + 16.0 * V
     path_gbs = path_bytes / (ms / 1000) / 1e9
 
@@ -589,6 +595,11 @@ def run_vg(args, rank, world, local):
         ms01 = _time_ms(lambda: vg.downsample_into(xyz, 0.1, buf, origin_from_min=True), 10)
         extra["fused_map_50M_leaf0.1"] = {"ms": ms01, "points_per_s": n / (ms01 / 1e3),
                                           "voxels": int(buf.num_voxels.item())}
+        # the opt-in bucket tail on the same cloud (top digits global, buckets on chip)
+        msb = _time_ms(lambda: vg.downsample_into(xyz, args.leaf, buf, origin_from_min=True,
+                                                  method="sort_bucket"), 10)
+        extra["fused_map_50M_sort_bucket"] = {"ms": msb, "points_per_s": n / (msb / 1e3),
+                                              "voxels": int(buf.num_voxels.item())}
         del buf
         torch.cuda.empty_cache()
         extra.update(extra_measurements(args, dev))
@@ -611,6 +622,9 @@ def run_vg(args, rank, world, local):
         "stages_ms": {nm: float(v) for nm, v in zip(stage_names, stage_ms)},
         "sort_passes": passes,
         "layout": "narrow (32-bit keys, packed offsets)" if narrow else "wide (64-bit keys, index)",
+        "grouping": ("top key digits in global radix passes, every bucket of the low digits "
+                     "sorted and reduced in one block's shared memory") if bucket else
+                    "every key digit in global radix passes, segmented reduction",
         "cpu_baseline": cpu,
         "e2e": {"value": total_points / e2e_s, "unit": "points/s", "h2d_bytes_per_step": 12 * n,
                 "d2h_bytes_per_step": d2h_pipe, "ms_per_step": e2e_s * 1e3,

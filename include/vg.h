@@ -72,6 +72,10 @@ typedef enum {
 #define VG_METHOD_SORT 16    /* radix sort of every point + segmented reduction        */
 #define VG_METHOD_HASH 32    /* hash-table accumulation + radix sort of the voxels     */
 #define VG_METHOD_MASK 48
+#define VG_SORT_BUCKETS 2    /* SORT, narrow layout: only the top key digits in global
+                                radix passes, every bucket of the rest sorted and reduced
+                                in one block's shared memory (same rows; by default every
+                                digit takes a global pass)                               */
 #define VG_USE_GRAPH 64      /* vg_downsample_batch: capture / replay a CUDA graph      */
 #define VG_GRID_SHIFT 8      /* vg_downsample_frames: blocks per SM of the streaming    */
 #define VG_GRID_MASK (0xff << VG_GRID_SHIFT) /* kernels (0 = default 8)                */
@@ -114,9 +118,10 @@ VG_API size_t vg_downsample_workspace_bytes(int64_t n_points, int flags);
  *   out_error      int32 scalar or NULL: device error word (see conventions).
  *   workspace      scratch of at least vg_downsample_workspace_bytes(n, flags) bytes,
  *                  256-byte aligned; its contents on entry do not matter.
- *   flags          VG_ORIGIN_FROM_MIN | one VG_METHOD_*.  SORT and HASH give identical
- *                  results; HASH needs more workspace and wins when voxels hold many
- *                  points.
+ *   flags          VG_ORIGIN_FROM_MIN | one VG_METHOD_* (| VG_SORT_BUCKETS with SORT).
+ *                  SORT and HASH give identical results; HASH needs more workspace and
+ *                  wins when voxels hold many points.  VG_SORT_BUCKETS changes how the
+ *                  narrow layout sorts, not the rows.
  *   stream         CUDA stream for every launch.
  */
 VG_API vg_status vg_downsample(const float* xyz, int64_t n, float* origin, float leaf,
@@ -324,7 +329,9 @@ VG_API vg_status vg_plan_tune(vg_plan* plan, const float* xyz, int64_t n_total,
  * out_centroids / out_counts, with out_level_offsets int64 [levels+1] (device).  Keys and
  * counts of level k equal vg_downsample at leaf 2^k * leaf exactly; centroids agree within
  * the library's tolerance.  cap_total >= levels * n always suffices.  Single cloud,
- * sort method, 1 <= levels <= VG_MAX_LEVELS.  point_to_voxel refers to level 0.
+ * sort method, 1 <= levels <= VG_MAX_LEVELS.  point_to_voxel refers to level 0.  flags:
+ * VG_ORIGIN_FROM_MIN | VG_SORT_BUCKETS (level 0's grouping; anything else is
+ * VG_ERR_INVALID_ARG).
  */
 VG_API size_t vg_pyramid_workspace_bytes(int64_t n_points, int levels, int flags);
 VG_API vg_status vg_pyramid(const float* xyz, int64_t n, float* origin, float leaf, int levels,

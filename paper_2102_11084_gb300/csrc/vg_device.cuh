@@ -297,6 +297,19 @@ __device__ __forceinline__ int sort_passes(unsigned long long maxkey) {
   return (bits + kRadixBits - 1) / kRadixBits;
 }
 
+// Radix passes a call runs: every significant digit of the largest key (at least one,
+// which also drops the invalid rows), or in the bucket tail only the digits above the
+// bucket shift.
+__device__ __forceinline__ int pass_count(const State* st) {
+  if (st->narrow && st->bucket) {
+    const uint32_t mk = static_cast<uint32_t>(st->maxkey);
+    const int bits = mk ? 32 - __clz(static_cast<int>(mk)) : 0;
+    const int top = bits > int(st->bshift) ? bits - int(st->bshift) : 0;
+    return max(1, (top + kRadixBits - 1) / kRadixBits);
+  }
+  return max(1, sort_passes(st->maxkey));
+}
+
 // Bounded chained-scan wait on a tile status word (flag | 30-bit value).  Returns the
 // exclusive prefix of tile `tile`'s value over tiles 0..tile-1.
 __device__ __forceinline__ uint32_t lookback_u32(const uint32_t* status, size_t stride,

@@ -35,6 +35,17 @@ constexpr int kSortItems = VG_SORT_ITEMS;
 constexpr int kSortTile = kSortThreads * kSortItems;
 constexpr int kSortMinBlocks = VG_SORT_MINB;
 
+// Bucket tail of the narrow layout: the radix passes sort only the top L <= 16 key bits
+// (the bucket, key >> bshift); one block then sorts each bucket by its low bshift <= 16
+// bits in shared memory and reduces it.  512 threads x 16 items: buckets of up to 8192
+// points stay on chip, larger ones take a chunked path through global scratch.
+constexpr int kBucketMaxBits = 16;
+constexpr int kBucketSlots = 1 << kBucketMaxBits;
+constexpr int kLocalThreads = 512;
+constexpr int kLocalItems = 16;
+constexpr int kLocalCap = kLocalThreads * kLocalItems;
+constexpr int kLocalTarget = 4096;  // average points per bucket the bucket width aims at
+
 // Segmented reduction geometry (256 threads x 4 sorted entries per tile).
 constexpr int kRedThreads = 256;
 constexpr int kRedItems = 4;
@@ -91,6 +102,13 @@ struct alignas(256) State {
   uint32_t nchunks;           // chunks of the frame decomposition
   uint32_t narrow;            // 1: 32-bit sort keys + packed-offset payload (no gather)
   int32_t error;              // internal error word when the caller passes none
+  uint32_t bucket;            // 1: narrow layout with the bucket tail (top passes only)
+  uint32_t bshift;            // bucket = key >> bshift (bits sorted on chip)
+  uint32_t njobs;             // non-empty buckets (bucket tail)
+  uint32_t job_ctr;           // ticket counter of the bucket tail
+  uint32_t bmax;              // largest bucket (points)
+  uint32_t nbig;              // buckets larger than one block (sorted by a pre-pass)
+  uint32_t big_ctr;           // ticket counter of that pre-pass
   uint32_t tile_ctr[kMaxPasses + 8];
   uint32_t hist[kMaxPasses][kRadix];
 };
@@ -120,6 +138,7 @@ struct FramesArg {
   const float* poses;      // device [F,12] row-major [R|t] sensor poses, or nullptr
   const float* zlims;      // device [F,2] [z_min, z_max] after the pose, or nullptr
   int merge_frames;        // 1: every frame keys into one voxel space (no frame id)
+  int bucket_tail;         // 1: a narrow layout takes the bucket tail (see kBucketMaxBits)
 };
 
 // A posed call maps every point into the common frame, p' = R p + t, before anything
@@ -139,7 +158,8 @@ constexpr int64_t max_chunks(int64_t n, int frames) { return ceil_div(n, kChunk)
 // (32-bit keys, 64-bit packed offsets) aliases the same bytes: keys32 ping-pong in keys0,
 // payload ping-pong in keys1 and in idx0..idx1.
 struct SortLayout {
-  size_t state, frames, keys0, keys1, idx0, idx1, lb_a, lb_b, seg_lb, total;
+  size_t state, frames, keys0, keys1, idx0, idx1, lb_a, lb_b, seg_lb, bcount, bstat, bjob,
+      total;
   size_t zero_bytes;  // bytes from `state` that must be zero at call start
   int64_t sort_tiles, seg_tiles;
 };
@@ -159,7 +179,13 @@ constexpr SortLayout sort_layout(int64_t n, int frames = 1) {
   off = align_up(off + size_t(L.sort_tiles) * kRadix * sizeof(uint32_t), 256);
   L.seg_lb = off;  // per-tile records, then the tiles' head counts as a compact array
   off = align_up(off + size_t(L.seg_tiles) * (sizeof(TileRec) + sizeof(uint32_t)), 256);
-  L.zero_bytes = off;  // state, frames, pass-0 status rows and segment status
+  L.bcount = off;  // points per bucket (bucket tail)
+  off = align_up(off + size_t(kBucketSlots) * sizeof(uint32_t), 256);
+  L.bstat = off;  // chained-scan status per bucket job
+  off = align_up(off + size_t(kBucketSlots) * sizeof(uint32_t), 256);
+  L.zero_bytes = off;  // state, frames, pass-0 status rows, segment and bucket counters
+  L.bjob = off;  // per job: first point, points, largest key (3 x u32), then the list
+  off = align_up(off + size_t(kBucketSlots) * 4 * sizeof(uint32_t), 256);  // of large jobs
   L.lb_b = off;
   off = align_up(off + size_t(L.sort_tiles) * kRadix * sizeof(uint32_t), 256);
   L.keys0 = off;  // also the two 32-bit key arrays of the narrow layout, 16-byte aligned
@@ -206,7 +232,8 @@ constexpr int kNarrowPasses = 4;
 cudaError_t launch_sort_pass(State* st, uint64_t* keys0, uint32_t* idx0, uint64_t* keys1,
                              uint32_t* idx1, uint32_t* lb_a, uint32_t* lb_b, int64_t n_max,
                              int pass, bool compact_input, uint32_t spin_limit, int* err,
-                             cudaStream_t stream, const NarrowBuffers* nb = nullptr);
+                             cudaStream_t stream, const NarrowBuffers* nb = nullptr,
+                             uint32_t* bcount = nullptr);
 // a4 + a5: reduce-by-key of the sorted table into key-ordered voxels.
 struct SegOut {
   uint64_t* keys;
@@ -226,6 +253,13 @@ cudaError_t launch_segreduce(State* st, const FrameState* fs, int nframes,
                              const uint32_t* idx1, const float* xyz, TileRec* recs,
                              int64_t n_max, const SegOut& out, int* err, cudaStream_t stream,
                              const NarrowBuffers* nb = nullptr, const float* poses = nullptr);
+// Bucket tail of the narrow layout (vg_bucket.cu): jobs from the bucket counts of the last
+// radix pass, then every bucket sorted by its low key bits on chip and reduced.
+cudaError_t launch_bucket_tail(State* st, const FrameState* fs, int nframes,
+                               const NarrowBuffers& nb, const uint32_t* bcount, uint32_t* bstat,
+                               uint32_t* bjob, int64_t n_max, const SegOut& out,
+                               uint32_t spin_limit, int* err, cudaStream_t stream);
+void warm_bucket_config();
 // Minimum-count filter (vg_filter.cu): its scratch follows the grouping method's layout.
 struct FilterLayout {
   size_t ticket, status, remap, zero_bytes, total;

@@ -105,7 +105,8 @@ __global__ __launch_bounds__(kStreamThreads) void origin_kernel(const float* __r
 
 // The streaming loop of the key kernel over this block's chunks.  kNarrow: 32-bit keys
 // (every key fits, checked from the extents) and packed corner offsets as payload;
-// otherwise 64-bit keys only.  Accumulates the digit-0 histogram, #valid and the largest
+// otherwise 64-bit keys only.  Accumulates the first sorted digit's histogram (digit 0,
+// or the digit at the bucket shift in the bucket tail), #valid and the largest
 // key.
 template <bool kPosed, bool kNarrow>
 __device__ __forceinline__ void key_loop(const float* __restrict__ xyz, const FramesArg& fr,
@@ -113,8 +114,8 @@ __device__ __forceinline__ void key_loop(const float* __restrict__ xyz, const Fr
                                          uint32_t key_shift, uint64_t* __restrict__ keys,
                                          uint32_t* __restrict__ keys32,
                                          uint64_t* __restrict__ payload, uint32_t* hist,
-                                         uint32_t& nvalid, unsigned long long& kmax_out,
-                                         bool& range_bad) {
+                                         uint32_t hshift, uint32_t& nvalid,
+                                         unsigned long long& kmax_out, bool& range_bad) {
   using KeyT = typename std::conditional<kNarrow, uint32_t, uint64_t>::type;
   const int F = fr.nframes;
   const bool xyz_vec = (reinterpret_cast<uintptr_t>(xyz) & 15) == 0;
@@ -181,7 +182,7 @@ __device__ __forceinline__ void key_loop(const float* __restrict__ xyz, const Fr
       if (ok) {
         ++nvalid;
         kmax = k[j] > kmax ? k[j] : kmax;
-        atomicAdd(&hist[uint32_t(k[j]) & (kRadix - 1)], 1u);
+        atomicAdd(&hist[uint32_t(k[j] >> hshift) & (kRadix - 1)], 1u);
         if (kNarrow) {
           int qq[3];
 #pragma unroll
@@ -220,7 +221,8 @@ __device__ __forceinline__ void key_loop(const float* __restrict__ xyz, const Fr
 }
 
 // a2: sort key per point (kKeySentinel for invalid or out-of-range rows), plus the
-// digit-0 histogram of the valid keys, the number of valid points and the largest key.
+// histogram of the first sorted digit of the valid keys, the number of valid points and
+// the largest key.
 // Block 0 also publishes every frame's origin and leaf (and the minimum to the caller
 // when the origin is computed) and the key shift.
 template <bool kPosed>
@@ -236,7 +238,9 @@ __global__ __launch_bounds__(kStreamThreads, kPosed ? 1 : VG_KEY_MINB) void key_
   for (int d = threadIdx.x; d < kRadix; d += kStreamThreads) hist[d] = 0;
   const uint32_t T = build_chunk_map(fr, sm.off, sm.cstart, sm.tmp, err);
   bool narrow = false;
-  const uint32_t key_shift = frame_prologue(fr, have_extent != 0, st, fs, T, sm, err, &narrow);
+  uint32_t bshift = 0;
+  const uint32_t key_shift =
+      frame_prologue(fr, have_extent != 0, st, fs, T, sm, err, &narrow, &bshift);
   narrow = narrow && keys32 && payload;
   uint32_t c0, c1;
   block_range(T, &c0, &c1);
@@ -244,11 +248,11 @@ __global__ __launch_bounds__(kStreamThreads, kPosed ? 1 : VG_KEY_MINB) void key_
   unsigned long long kmax = 0;
   bool range_bad = false;
   if (narrow)
-    key_loop<kPosed, true>(xyz, fr, sm, c0, c1, key_shift, keys, keys32, payload, hist, nvalid,
-                           kmax, range_bad);
+    key_loop<kPosed, true>(xyz, fr, sm, c0, c1, key_shift, keys, keys32, payload, hist, bshift,
+                           nvalid, kmax, range_bad);
   else
-    key_loop<kPosed, false>(xyz, fr, sm, c0, c1, key_shift, keys, keys32, payload, hist, nvalid,
-                            kmax, range_bad);
+    key_loop<kPosed, false>(xyz, fr, sm, c0, c1, key_shift, keys, keys32, payload, hist, 0u,
+                            nvalid, kmax, range_bad);
   if (__any_sync(kFullMask, range_bad) && lane == 0) set_error(err, kErrRange);
 #pragma unroll
   for (int off = 16; off; off >>= 1) {

@@ -66,7 +66,8 @@ __device__ __forceinline__ void block_range(uint32_t T, uint32_t* c0, uint32_t* 
 __device__ __forceinline__ uint32_t frame_prologue(const FramesArg& fr, bool have_extent,
                                                    State* st, FrameState* fs, uint32_t T,
                                                    ChunkSmem& sm, int* err,
-                                                   bool* narrow = nullptr) {
+                                                   bool* narrow = nullptr,
+                                                   uint32_t* bshift = nullptr) {
   const int F = fr.nframes;
   // per-frame origin and leaf; bits of the largest key of each frame
   uint32_t bits = 0;
@@ -141,11 +142,28 @@ __device__ __forceinline__ uint32_t frame_prologue(const FramesArg& fr, bool hav
                      : maxkey;
   const bool nar = fr.allow_narrow && have_extent && total_bits <= 32 && key_bound < 0xffffffffull;
   if (narrow) *narrow = nar;
+  // Bucket tail: the radix passes sort the top L bits of the key, L a whole number of
+  // digits aimed at kLocalTarget points per bucket, but at most kBucketMaxBits and enough
+  // that the low kb - L bits left to the on-chip sort are at most 16.
+  const bool bmode = nar && fr.bucket_tail;
+  uint32_t bs = 0;
+  if (bmode) {
+    const uint32_t kb = key_bound ? 64u - __clzll(static_cast<long long>(key_bound)) : 0u;
+    const int64_t q = (fr.n + kLocalTarget - 1) / kLocalTarget;
+    uint32_t lw = q > 1 ? 64u - __clzll(static_cast<long long>(q - 1)) : 0u;
+    lw = min((lw + kRadixBits - 1) / kRadixBits * kRadixBits, uint32_t(kBucketMaxBits));
+    const uint32_t lo = kb > 16u ? kb - 16u : 0u;
+    const uint32_t L = max(lo, min(kb, lw));
+    bs = kb - L;
+  }
+  if (bshift) *bshift = bs;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     st->key_shift = key_shift;
     st->nframes = F;
     st->nchunks = T;
     st->narrow = nar ? 1u : 0u;
+    st->bucket = bmode ? 1u : 0u;
+    st->bshift = bs;
   }
 
   __syncthreads();

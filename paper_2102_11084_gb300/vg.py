@@ -25,9 +25,14 @@ ORIGIN_FROM_MIN = 1
 METHOD_AUTO = 0
 METHOD_SORT = 16
 METHOD_HASH = 32
+SORT_BUCKETS = 2
 USE_GRAPH = 64
 GRID_SHIFT = 8
-_METHODS = {"auto": METHOD_AUTO, "sort": METHOD_SORT, "hash": METHOD_HASH}
+# "sort": radix sort of the points, every key digit in a global pass; "sort_bucket": the
+# narrow layout sorts only the top digits globally and every bucket of the rest in one
+# block's shared memory; "hash": hash-table accumulation.  All give identical rows.
+_METHODS = {"auto": METHOD_AUTO, "sort": METHOD_SORT,
+            "sort_bucket": METHOD_SORT | SORT_BUCKETS, "hash": METHOD_HASH}
 MAX_POINTS = (1 << 30) - 1
 MAX_FRAMES = 1024
 MAX_LEVELS = 8
@@ -674,10 +679,12 @@ class Plan:
 
 # ---- pyramid (step a6) -----------------------------------------------------------------
 def pyramid(xyz: torch.Tensor, leaf: float, levels: int, origin: Optional[torch.Tensor] = None,
-            *, point_to_voxel: bool = False, stream: Optional[torch.cuda.Stream] = None) -> list:
+            *, point_to_voxel: bool = False, method="sort",
+            stream: Optional[torch.cuda.Stream] = None) -> list:
     """vg_pyramid: level 0 = decimation at ``leaf``, level k+1 = merge of level k by key>>3.
 
-    Returns a list of ``levels`` Decimation tuples (point_to_voxel only on level 0).
+    ``method``: "sort" or "sort_bucket" (level 0's grouping).  Returns a list of ``levels``
+    Decimation tuples (point_to_voxel only on level 0).
     """
     xyz = _cuda_cloud(xyz)
     n = xyz.shape[0]
@@ -691,7 +698,9 @@ def pyramid(xyz: torch.Tensor, leaf: float, levels: int, origin: Optional[torch.
     loff = torch.zeros(levels + 1, dtype=torch.int64, device=dev)
     err = torch.zeros(1, dtype=torch.int32, device=dev)
     p2v = torch.empty(max(n, 1), dtype=torch.int32, device=dev) if point_to_voxel else None
-    flags = ORIGIN_FROM_MIN if origin is None else 0
+    if method_flag(method) & ~(METHOD_SORT | SORT_BUCKETS):
+        raise ValueError("vg_pyramid groups level 0 by sorting")
+    flags = (ORIGIN_FROM_MIN if origin is None else 0) | (method_flag(method) & SORT_BUCKETS)
     ws = torch.empty(max(int(lib().vg_pyramid_workspace_bytes(n, levels, flags)), 256),
                      dtype=torch.uint8, device=dev)
     st = lib().vg_pyramid(_ptr(xyz), n, _ptr(org), ctypes.c_float(leaf), int(levels), _ptr(keys),
