@@ -44,6 +44,9 @@ def parse():
     p.add_argument("--impl", default="vg", choices=["vg", "reference"])
     p.add_argument("--n", type=int, default=N_POINTS)
     p.add_argument("--leaf", type=float, default=LEAF)
+    p.add_argument("--method", default="sort", choices=["sort", "sort_bucket"],
+                   help="grouping of the timed step: the radix sort (default) or its opt-in "
+                        "bucket tail")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extra", action="store_true",
                    help="skip the other configurations (single frame, batch, pyramid, "
@@ -158,8 +161,8 @@ class ClockSampler:
 
 
 # the sources of the kernels the bench step launches (their traffic is profiled)
-STEP_KERNEL_SOURCES = ("vg_bucket.cu", "vg_device.cuh", "vg_internal.h", "vg_keys.cu",
-                       "vg_reduce.cu", "vg_sort.cu", "vg_stream.cuh")
+STEP_KERNEL_SOURCES = ("vg_device.cuh", "vg_internal.h", "vg_keys.cu", "vg_reduce.cu",
+                       "vg_sort.cu", "vg_stream.cuh")
 
 
 def kernel_source_hash():
@@ -448,7 +451,8 @@ def run_vg(args, rank, world, local):
     import ctypes
 
     def call():
-        vg.downsample_into(xyz, args.leaf, buf, origin_from_min=True, stream=stream)
+        vg.downsample_into(xyz, args.leaf, buf, origin_from_min=True, method=args.method,
+                           stream=stream)
 
     for _ in range(args.warmup):
         call()
@@ -603,14 +607,17 @@ def run_vg(args, rank, world, local):
         del buf
         torch.cuda.empty_cache()
         extra.update(extra_measurements(args, dev))
-    launches_per_step = 1 + 1 + 8 + 3  # extent, keys, 8 radix passes, count + scan + reduce
+    # extent, keys, 8 radix passes, count + scan + reduce (+ job scan, large-bucket pre-pass
+    # and bucket kernel with the bucket tail)
+    launches_per_step = 1 + 1 + 8 + 3 + (3 if args.method == "sort_bucket" else 0)
     out = {
         "metric": "points/s", "value": total_points / (ms / 1000), "unit": "points/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "points": n, "valid_points": nvalid, "voxels": V,
-                   "leaf_m": args.leaf, "method": "sort", "parallelism": f"replicas x{world}",
+                   "leaf_m": args.leaf, "method": args.method,
+                   "parallelism": f"replicas x{world}",
                    "l2": "inputs (600 MB) larger than L2 (129 MB); no flush"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,

@@ -1,22 +1,26 @@
-// Bucket tail of the narrow sort path: the radix passes (vg_sort.cu) order the points by
-// their bucket, the top L <= 16 bits of the sort key (key >> bshift), and count the
-// points of every bucket.  Here a one-block scan turns the counts into jobs (the
+// Bucket tail of the narrow sort path (opt-in): the radix passes (vg_sort.cu) order the
+// points by their bucket, the top L <= 16 bits of the sort key (key >> bshift), and count
+// the points of every bucket.  Here a one-block scan turns the counts into jobs (the
 // non-empty buckets, in key order), and a persistent kernel takes the jobs in ticket
-// order: it sorts each bucket by the low bshift <= 16 key bits in shared memory and
-// reduces the sorted runs into voxels, as the segmented reduction does.
+// order and reduces each bucket in shared memory without sorting it:
+//   * an occupancy bitmap over the bucket's low key bits (2^bshift <= 65536 bits, 8 KB);
+//   * a prefix popcount over the bitmap gives every occupied key its rank, i.e. its row
+//     within the bucket (the bucket's voxels in key order), and the bucket's voxel count;
+//   * every point adds its count and fixed-point offsets into its voxel's slot with
+//     shared-memory atomics (32-bit sums plus a carry count per axis, so the totals are
+//     exact integers: the rows are bit-identical to the sorted path's);
+//   * the slots are finalised into rows at the bucket's first row, which a chained scan
+//     over the jobs gives (each job publishes its voxel count as soon as its bitmap is
+//     counted, and waits for the rows before it only after it has accumulated).
+// Buckets of any size: points are streamed in chunks of kBmChunk, voxels in windows of
+// kBmWindow slots.
 //
 // arXiv 2102.11084 Sec. II-C / Algorithm 1 sorts the (cell, point) table with a radix
-// sort so that the points of each cell are contiguous and then reduces every cell.  A
-// radix sort may split its digits between passes over the whole table and passes inside
-// independent key ranges (an MSD step followed by per-range LSD passes gives the same
-// order), so this is still that sort: the ranges here are buckets small enough for one
-// block's shared memory, which saves the low digits' trips through HBM and the separate
-// reduction kernels.  Centroid sums are exact integers, so the order of equal keys does
-// not change any output bit.
-//
-// Jobs publish their voxel counts through a chained scan over the ticket order (bounded
-// waits, as everywhere else).  A bucket larger than one block's capacity (kLocalCap
-// points) is sorted through global scratch in chunks, with the same ranking code.
+// sort so that the points of each cell are contiguous, then reduces every cell.  Here the
+// radix sort orders the cells by their top key bits only; inside a bucket the order of
+// the cells is the order of the bits of the bitmap, and the points of a cell meet in its
+// slot instead of in a contiguous run: the same cells, in the same order, with the same
+// sums.
 #include "vg_device.cuh"
 #include "vg_internal.h"
 
@@ -24,129 +28,51 @@ namespace vg {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kLW = kLocalThreads / 32;
+// Geometry (build-time; the defaults are the measured best on the 50M map: 256 threads x 4
+// blocks with 1792 slots, 128 x 6 with 1024, and 256 x 2 with 3584 were all slower).
+#ifndef VG_BM_THREADS
+#define VG_BM_THREADS 512
+#endif
+#ifndef VG_BM_WINDOW
+#define VG_BM_WINDOW 4096
+#endif
+#ifndef VG_BM_MINB
+#define VG_BM_MINB 2
+#endif
+constexpr int kBmThreads = VG_BM_THREADS;
+constexpr int kBmWarps = kBmThreads / 32;
+constexpr int kBmItems = 16;                              // keys a thread holds per chunk
+constexpr int kBmChunk = kBmThreads * kBmItems;           // points per chunk
+constexpr int kBmWords = 1 << (kBucketMaxBits - 5);       // bitmap words (bshift <= 16)
+constexpr int kBmWindow = VG_BM_WINDOW;                   // voxel slots per window
+constexpr int kBmWordsPerThread = kBmWords / kBmThreads;
+constexpr uint32_t kCarryField = 10;                      // carry bits per axis
+constexpr uint32_t kExactLimit = 1u << 21;                // points of a slot the carries hold
 
-// Per-job words of the bjob array.
-constexpr int kJobStart = 0, kJobCount = 1, kJobLast = 2;
+// Job table (bjob, kBucketSlots entries per array): first point at [0, S), points at
+// [S, 2S), largest key at [2S, 3S), S = kBucketSlots.
 
-struct LocalSmem {
-  uint32_t words[kLocalCap];             // sort words (key16 << 16 | local index); scratch
-  unsigned long long pay[kLocalCap];     // payloads by local index
-  union {
-    uint16_t whist[kLW][kRadix];         // per-warp digit counts (sort passes)
-    uint16_t hpos[kLocalCap + 2];        // run heads (reduction)
-  } u;
-  uint16_t cnt[kRadix];                  // digit counts, then (in place) digit starts
-  uint32_t tmp[kLW];
+struct BmSmem {
+  uint32_t bits[kBmWords];            // occupancy of the low key bits
+  uint16_t rank[kBmWords];            // occupied keys before each word (exclusive)
+  uint32_t cnt[kBmWindow];            // points per slot
+  uint32_t lo[3][kBmWindow];          // per-axis sums of the biased offsets, mod 2^32
+  uint32_t hi[kBmWindow];             // per-axis wrap counts, kCarryField bits each
+  uint16_t vkey[kBmWindow];           // low key bits of every slot
+  uint32_t tmp[kBmWarps];
+  long long red[kBmWarps][4];
   int s_job, s_next;
-  uint32_t s_vbase, s_prev_last, s_v;
-  uint32_t s_a, s_m, s_bucket, s_na, s_nm, s_nbucket;  // current and next job descriptor
+  uint32_t s_a, s_m, s_bucket, s_na, s_nm, s_nbucket;
+  uint32_t s_v, s_vbase, s_prev_last, s_last16, s_prev16, s_big;
 };
-// Two blocks per SM: 2 x (this + 1 KB reserved) within the SM's 228 KB.
-static_assert(sizeof(LocalSmem) + 1024 <= 228 * 1024 / 2, "bucket block shared memory");
-
-__device__ __forceinline__ void cp_async8(void* smem, const void* g) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(smem)), "l"(g)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.wait_all;" ::: "memory");
-}
+// VG_BM_MINB blocks per SM: each takes this + 1 KB reserved of the SM's 228 KB.
+static_assert((sizeof(BmSmem) + 1024) * VG_BM_MINB <= 228 * 1024, "bucket block shared memory");
 
 // L2 prefetch of the 16-byte-aligned interior of [p, p + bytes).
 __device__ __forceinline__ void prefetch_range(const void* p, size_t bytes) {
   const uintptr_t a = (reinterpret_cast<uintptr_t>(p) + 15) & ~uintptr_t(15);
   const uintptr_t b = (reinterpret_cast<uintptr_t>(p) + bytes) & ~uintptr_t(15);
   if (b > a) prefetch_l2(reinterpret_cast<const void*>(a), static_cast<uint32_t>(b - a));
-}
-
-// Stable rank of the block's items by the 8-bit digit (x >> sh) & 255.  Items are
-// warp-striped (item j of lane l in warp w is element w*32*ipt + j*32 + l of the block's
-// sequence); bit j of `valid` says item j exists.  On return rank[j] = number of earlier
-// elements with the same digit, and cnt[d] (shared) = the block's count of digit d
-// (threads < 256 write it; at most kLocalCap).  Contains __syncthreads.
-__device__ __forceinline__ void rank_items(const uint32_t (&x)[kLocalItems], uint32_t sh,
-                                           uint32_t valid, int ipt, uint16_t (*whist)[kRadix],
-                                           uint32_t (&rank)[kLocalItems], uint16_t* cnt) {
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  for (int d = lane; d < kRadix; d += 32) whist[warp][d] = 0;
-  __syncwarp();
-  const uint32_t lt = (1u << lane) - 1u;
-#pragma unroll
-  for (int j = 0; j < kLocalItems; ++j) {
-    if (j < ipt) {
-      const bool ok = (valid >> j) & 1u;
-      const uint32_t d = (x[j] >> sh) & (kRadix - 1);
-      uint32_t peers = __ballot_sync(kFull, ok);
-#pragma unroll
-      for (int b = 0; b < kRadixBits; ++b) {
-        const bool bit = (d >> b) & 1u;
-        const uint32_t bal = __ballot_sync(kFull, bit);
-        peers &= bit ? bal : ~bal;
-      }
-      const uint32_t lower = peers & lt;
-      uint32_t old = 0;
-      if (ok) old = whist[warp][d];
-      __syncwarp();
-      if (ok && lower == 0) whist[warp][d] = static_cast<uint16_t>(old + __popc(peers));
-      __syncwarp();
-      rank[j] = old + __popc(lower);
-    }
-  }
-  __syncthreads();
-  if (t < kRadix) {
-    uint32_t run = 0;
-#pragma unroll
-    for (int w = 0; w < kLW; ++w) {
-      const uint32_t c = whist[w][t];
-      whist[w][t] = static_cast<uint16_t>(run);
-      run += c;
-    }
-    cnt[t] = static_cast<uint16_t>(run);
-  }
-  __syncthreads();
-#pragma unroll
-  for (int j = 0; j < kLocalItems; ++j)
-    if (j < ipt && ((valid >> j) & 1u)) rank[j] += whist[warp][(x[j] >> sh) & (kRadix - 1)];
-}
-
-// Exclusive scan of cnt[0..256) into dst (may be cnt itself), over the whole block.
-template <typename T>
-__device__ __forceinline__ void digit_starts(const T* cnt, T* dst, uint32_t* tmp) {
-  const int t = threadIdx.x;
-  uint32_t total;
-  const uint32_t e = block_excl_scan(t < kRadix ? uint32_t(cnt[t]) : 0u, &total, tmp);
-  if (t < kRadix) dst[t] = static_cast<T>(e);
-  __syncthreads();
-}
-
-// Sum of a block's Acc values (all threads receive it).  Contains __syncthreads.
-__device__ __forceinline__ Acc block_sum_acc(Acc a, long long (*red)[4]) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  long long v[4] = {a.s[0], a.s[1], a.s[2], static_cast<long long>(a.n)};
-#pragma unroll
-  for (int k = 0; k < 4; ++k)
-#pragma unroll
-    for (int off = 16; off; off >>= 1) v[k] += __shfl_xor_sync(kFull, v[k], off);
-  __syncthreads();
-  if (lane == 0)
-#pragma unroll
-    for (int k = 0; k < 4; ++k) red[warp][k] = v[k];
-  __syncthreads();
-  Acc r = acc_zero();
-  for (int w = 0; w < kLW; ++w) {
-    r.s[0] += red[w][0];
-    r.s[1] += red[w][1];
-    r.s[2] += red[w][2];
-    r.n += static_cast<uint32_t>(red[w][3]);
-  }
-  return r;
-}
-
-__device__ __forceinline__ void acc_add_payload(Acc& a, uint64_t w) {
-  a.s[0] += unpack_offset(w, 0);
-  a.s[1] += unpack_offset(w, 1);
-  a.s[2] += unpack_offset(w, 2);
 }
 
 // One output row: voxel `key` (the full sort key) at row `cur`, plus the frame marks.
@@ -235,42 +161,88 @@ __device__ __forceinline__ uint32_t warp_lookback(const uint32_t* status, int j,
   return excl;
 }
 
-// Warp 0: publishes `v` voxels for job j (its aggregate, unless a pre-pass already did,
-// after its largest key), waits for the rows before it, publishes its prefix.  Returns
-// the rows before it; *prev_last = the largest key of job j - 1.
-__device__ __forceinline__ uint32_t publish_job(uint32_t* bstat, uint32_t* bjob, int j, uint32_t v,
-                                                bool publish_aggregate, uint32_t last_key,
-                                                uint32_t spins, int* err, uint32_t* prev_last) {
-  const int lane = threadIdx.x & 31;
-  if (publish_aggregate && lane == 0) {
-    bjob[3 * size_t(j) + kJobLast] = last_key;
-    __threadfence();
-    st_relaxed(bstat + j, (j == 0 ? kFlagPrefix : kFlagAggregate) | v);
-  }
-  if (j == 0) {
-    if (lane == 0 && !publish_aggregate) st_relaxed(bstat, kFlagPrefix | v);
-    return 0;
-  }
+// Warp 0: publishes job j's aggregate (`v` voxels) after its largest key.
+__device__ __forceinline__ void publish_aggregate(uint32_t* bstat, uint32_t* bjob, int j,
+                                                  uint32_t v, uint32_t last_key) {
+  bjob[2 * size_t(kBucketSlots) + j] = last_key;
+  __threadfence();
+  st_relaxed(bstat + j, (j == 0 ? kFlagPrefix : kFlagAggregate) | v);
+}
+
+// Warp 0, after publish_aggregate: the rows before job j, then its prefix.  Returns the
+// rows before it (same in every lane); lane 0 sets *prev_last = job j - 1's largest key.
+__device__ __forceinline__ uint32_t resolve_job(uint32_t* bstat, const uint32_t* bjob, int j,
+                                                uint32_t v, uint32_t spins, int* err,
+                                                uint32_t* prev_last) {
+  if (j == 0) return 0;
   const uint32_t excl = warp_lookback(bstat, j, spins, err);
-  if (lane == 0) {
+  if ((threadIdx.x & 31) == 0) {
     st_relaxed(bstat + j, kFlagPrefix | ((excl + v) & kValueMask));
     __threadfence();
-    *prev_last = ld_relaxed(bjob + 3 * size_t(j - 1) + kJobLast);
+    *prev_last = ld_relaxed(bjob + 2 * size_t(kBucketSlots) + (j - 1));
   }
   return excl;
 }
 
-// Thread 0, once the current job's prefix is out: the next ticket and its descriptor,
-// whose rows start their way into L2 while this job reduces (taken any earlier, the
-// ticket would hold up every later job's look-back for a whole job).
-__device__ __forceinline__ void take_next(LocalSmem& sm, uint32_t* job_ctr, const uint32_t* K,
+// ---- the jobs -------------------------------------------------------------------------
+
+// One block: the non-empty buckets in key order become jobs (first point, points), in
+// rounds of 4096 buckets so that consecutive threads write consecutive jobs.
+__global__ __launch_bounds__(1024) void bucket_scan_kernel(State* st, const uint32_t* __restrict__ bcount,
+                                                           uint32_t* __restrict__ bjob) {
+  __shared__ uint32_t tmp[32];
+  __shared__ uint32_t smax[32];
+  if (!(st->narrow && st->bucket)) return;
+  const int t = threadIdx.x;
+  uint32_t* job_start = bjob;
+  uint32_t* job_count = bjob + kBucketSlots;
+  uint32_t base_e = 0, base_j = 0, mx = 0;
+  for (int r0 = 0; r0 < kBucketSlots; r0 += 4 * 1024) {
+    const uint4 v = reinterpret_cast<const uint4*>(bcount + r0)[t];
+    const uint32_t c[4] = {v.x, v.y, v.z, v.w};
+    const uint32_t sum = v.x + v.y + v.z + v.w;
+    const uint32_t nz = (v.x != 0) + (v.y != 0) + (v.z != 0) + (v.w != 0);
+    mx = max(max(mx, max(v.x, v.y)), max(v.z, v.w));
+    uint32_t tot_e, tot_j;
+    uint32_t run_e = base_e + block_excl_scan(sum, &tot_e, tmp);
+    __syncthreads();
+    uint32_t run_j = base_j + block_excl_scan(nz, &tot_j, tmp);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (c[q]) {
+        job_start[run_j] = run_e;
+        job_count[run_j] = c[q];
+        ++run_j;
+        run_e += c[q];
+      }
+    base_e += tot_e;
+    base_j += tot_j;
+    __syncthreads();
+  }
+#pragma unroll
+  for (int off = 16; off; off >>= 1) mx = max(mx, __shfl_xor_sync(kFull, mx, off));
+  if ((t & 31) == 0) smax[t >> 5] = mx;
+  __syncthreads();
+  if (t == 0) {
+    uint32_t m = 0;
+    for (int w = 0; w < 32; ++w) m = max(m, smax[w]);
+    // the counts cover exactly the valid points, unless the call already failed before
+    // the keys were written (bad frame offsets): then there is nothing to reduce
+    st->njobs = base_e == st->nitems ? base_j : 0u;
+    st->bmax = m;
+  }
+}
+
+// Thread 0: the next ticket and its descriptor; its rows start their way into L2 while
+// the current job runs.
+__device__ __forceinline__ void take_next(BmSmem& sm, uint32_t* job_ctr, const uint32_t* K,
                                           const uint64_t* P, const uint32_t* bjob, int njobs,
                                           uint32_t bshift) {
   const int nx = static_cast<int>(atomicAdd(job_ctr, 1u));
   sm.s_next = nx;
   if (nx < njobs) {
-    const uint32_t na = bjob[3 * size_t(nx) + kJobStart];
-    const uint32_t nm = bjob[3 * size_t(nx) + kJobCount];
+    const uint32_t na = bjob[nx];
+    const uint32_t nm = bjob[kBucketSlots + nx];
     prefetch_range(K + na, size_t(nm) * sizeof(uint32_t));
     prefetch_range(P + na, size_t(nm) * sizeof(uint64_t));
     sm.s_na = na;
@@ -279,339 +251,207 @@ __device__ __forceinline__ void take_next(LocalSmem& sm, uint32_t* job_ctr, cons
   }
 }
 
-// ---- the jobs -------------------------------------------------------------------------
-
-__global__ __launch_bounds__(1024) void bucket_scan_kernel(State* st, const uint32_t* __restrict__ bcount,
-                                                           uint32_t* __restrict__ bjob) {
-  __shared__ uint32_t tmp[32];
-  __shared__ uint32_t smax[32];
-  if (!(st->narrow && st->bucket)) return;
-  constexpr int kPer = kBucketSlots / 1024;
-  const int t = threadIdx.x;
-  const uint4* c4 = reinterpret_cast<const uint4*>(bcount + size_t(t) * kPer);
-  uint32_t sum = 0, nz = 0, mx = 0;
-#pragma unroll 4
-  for (int k = 0; k < kPer / 4; ++k) {
-    const uint4 v = c4[k];
-    sum += v.x + v.y + v.z + v.w;
-    nz += (v.x != 0) + (v.y != 0) + (v.z != 0) + (v.w != 0);
-    mx = max(max(mx, max(v.x, v.y)), max(v.z, v.w));
-  }
-  uint32_t nbig = 0;
-  for (int k = 0; k < kPer / 4; ++k) {
-    const uint4 v = c4[k];
-    nbig += (v.x > uint32_t(kLocalCap)) + (v.y > uint32_t(kLocalCap)) +
-            (v.z > uint32_t(kLocalCap)) + (v.w > uint32_t(kLocalCap));
-  }
-  uint32_t tot_e, tot_j, tot_b;
-  uint32_t run_e = block_excl_scan(sum, &tot_e, tmp);
-  __syncthreads();
-  uint32_t run_j = block_excl_scan(nz, &tot_j, tmp);
-  __syncthreads();
-  uint32_t run_b = block_excl_scan(nbig, &tot_b, tmp);
-  uint32_t* big = bjob + 3 * size_t(kBucketSlots);
-#pragma unroll
-  for (int off = 16; off; off >>= 1) mx = max(mx, __shfl_xor_sync(kFull, mx, off));
-  if ((t & 31) == 0) smax[t >> 5] = mx;
-  // The counts cover exactly the valid points, unless the call already failed before the
-  // keys were written (bad frame offsets): then there is nothing to reduce.
-  const bool consistent = tot_e == st->nitems;
-  for (int k = 0; consistent && k < kPer / 4; ++k) {
-    const uint4 v = c4[k];
-    const uint32_t c[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-      if (c[q]) {
-        bjob[3 * size_t(run_j) + kJobStart] = run_e;
-        bjob[3 * size_t(run_j) + kJobCount] = c[q];
-        if (c[q] > uint32_t(kLocalCap)) big[run_b++] = run_j;
-        ++run_j;
-        run_e += c[q];
-      }
-  }
-  __syncthreads();
-  if (t == 0) {
-    uint32_t m = 0;
-    for (int w = 0; w < 32; ++w) m = max(m, smax[w]);
-    st->njobs = consistent ? tot_j : 0u;
-    st->nbig = consistent ? tot_b : 0u;
-    st->bmax = m;
-  }
+// Rank of low key bits k16 among the bucket's occupied keys.
+__device__ __forceinline__ uint32_t key_rank(const BmSmem& sm, uint32_t k16) {
+  const uint32_t w = k16 >> 5;
+  return uint32_t(sm.rank[w]) + __popc(sm.bits[w] & ((1u << (k16 & 31u)) - 1u));
 }
 
-// Small job: the bucket's m <= kLocalCap points sorted and reduced in shared memory.
-__device__ __forceinline__ void small_job(LocalSmem& sm, const uint32_t* __restrict__ K,
-                                          const uint64_t* __restrict__ P, uint32_t a, uint32_t m,
-                                          uint32_t bucket, uint32_t bshift, int j, int njobs,
-                                          uint32_t* bstat, uint32_t* bjob, uint32_t* job_ctr,
-                                          const RowCtx& rc, const SegOut& out, uint32_t spins,
-                                          int* err) {
+// Exact biased sum of one axis of slot i: 32-bit sum plus the wrap count.
+__device__ __forceinline__ long long slot_sum(const BmSmem& sm, int axis, int i) {
+  const uint64_t carry = (sm.hi[i] >> (kCarryField * axis)) & ((1u << kCarryField) - 1u);
+  return static_cast<long long>((carry << 32) | sm.lo[axis][i]);
+}
+
+// One job: the bucket's m points at [a, a + m).
+__device__ __forceinline__ void bucket_job(BmSmem& sm, const uint32_t* __restrict__ K,
+                                           const uint64_t* __restrict__ P, uint32_t a, uint32_t m,
+                                           uint32_t bucket, uint32_t bshift, int j, int njobs,
+                                           uint32_t* bstat, uint32_t* bjob, uint32_t* job_ctr,
+                                           const RowCtx& rc, const SegOut& out, uint32_t spins,
+                                           int* err) {
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  const int ipt = static_cast<int>((m + kLocalThreads - 1) / kLocalThreads);
-  const uint32_t smask = bshift >= 32 ? kFull : ((1u << bshift) - 1u);
-  uint32_t w[kLocalItems];
-  uint32_t valid = 0;
-  const uint32_t ebase = uint32_t(warp) * 32u * uint32_t(ipt) + uint32_t(lane);
-#pragma unroll
-  for (int j2 = 0; j2 < kLocalItems; ++j2) {
-    w[j2] = 0;
-    if (j2 < ipt) {
-      const uint32_t e = ebase + uint32_t(j2) * 32u;
-      if (e < m) {
-        cp_async8(&sm.pay[e], P + a + e);
-        w[j2] = ((__ldcs(K + a + e) & smask) << 16) | e;
-        valid |= 1u << j2;
-      }
-    }
-  }
-  const int npl = bshift == 0 ? 0 : (bshift <= 8 ? 1 : 2);
-  for (int q = 0; q < npl; ++q) {
-    const uint32_t sh = 16u + 8u * uint32_t(q);
-    uint32_t rank[kLocalItems];
-    rank_items(w, sh, valid, ipt, sm.u.whist, rank, sm.cnt);
-    digit_starts(sm.cnt, sm.cnt, sm.tmp);
-#pragma unroll
-    for (int j2 = 0; j2 < kLocalItems; ++j2)
-      if (j2 < ipt && ((valid >> j2) & 1u))
-        sm.words[sm.cnt[(w[j2] >> sh) & (kRadix - 1)] + rank[j2]] = w[j2];
-    __syncthreads();
-    if (q + 1 < npl) {
-#pragma unroll
-      for (int j2 = 0; j2 < kLocalItems; ++j2)
-        if (j2 < ipt && ((valid >> j2) & 1u)) w[j2] = sm.words[ebase + uint32_t(j2) * 32u];
-    }
-  }
-  if (npl == 0) {
-#pragma unroll
-    for (int j2 = 0; j2 < kLocalItems; ++j2)
-      if (j2 < ipt && ((valid >> j2) & 1u)) sm.words[ebase + uint32_t(j2) * 32u] = w[j2];
-  }
-  cp_async_wait_all();
+  const uint32_t smask = (1u << bshift) - 1u;  // bshift <= 16
+  const int nw = bshift >= 5 ? 1 << (bshift - 5) : 1;
+  const bool resident = m <= uint32_t(kBmChunk);  // keys stay in registers
+  for (int w = t; w < nw; w += kBmThreads) sm.bits[w] = 0;
   __syncthreads();
 
-  // run heads over blocked positions [t*ipt, t*ipt + ipt)
-  const uint32_t p0 = uint32_t(t) * uint32_t(ipt);
-  uint32_t hmask = 0, hc = 0;
+  // 1. occupancy bitmap
+  uint32_t k16[kBmItems];
+  for (uint32_t c0 = 0; c0 < m; c0 += kBmChunk) {
 #pragma unroll
-  for (int j2 = 0; j2 < kLocalItems; ++j2) {
-    const uint32_t p = p0 + uint32_t(j2);
-    if (j2 < ipt && p < m) {
-      const bool head = p == 0 || (sm.words[p] >> 16) != (sm.words[p - 1] >> 16);
-      hmask |= uint32_t(head) << j2;
-      hc += head;
+    for (int i = 0; i < kBmItems; ++i) {
+      const uint32_t e = c0 + uint32_t(i) * kBmThreads + uint32_t(t);
+      k16[i] = e < m ? (__ldcs(K + a + e) & smask) : kFull;
+      if (k16[i] != kFull) atomicOr(&sm.bits[k16[i] >> 5], 1u << (k16[i] & 31u));
     }
+  }
+  __syncthreads();
+
+  // 2. ranks: exclusive popcounts of the words, the voxel count, the largest key
+  uint32_t pc[kBmWordsPerThread], mine = 0;
+#pragma unroll
+  for (int q = 0; q < kBmWordsPerThread; ++q) {
+    const int w = kBmWordsPerThread * t + q;
+    pc[q] = w < nw ? __popc(sm.bits[w]) : 0u;
+    mine += pc[q];
   }
   uint32_t V;
-  uint32_t r = block_excl_scan(hc, &V, sm.tmp);
+  uint32_t run = block_excl_scan(mine, &V, sm.tmp);
 #pragma unroll
-  for (int j2 = 0; j2 < kLocalItems; ++j2)
-    if ((hmask >> j2) & 1u) sm.u.hpos[r++] = static_cast<uint16_t>(p0 + uint32_t(j2));
-  if (warp == 0) {
-    const uint32_t last_key = (bucket << bshift) | (sm.words[m - 1] >> 16);
-    uint32_t prev_last = 0;
-    const uint32_t vb = publish_job(bstat, bjob, j, V, true, last_key, spins, err, &prev_last);
-    if (lane == 0) {
-      sm.u.hpos[V] = static_cast<uint16_t>(m);
-      sm.s_vbase = vb;
-      sm.s_prev_last = prev_last;
-      take_next(sm, job_ctr, K, P, bjob, njobs, bshift);
+  for (int q = 0; q < kBmWordsPerThread; ++q) {
+    const int w = kBmWordsPerThread * t + q;
+    if (w < nw) {
+      sm.rank[w] = static_cast<uint16_t>(run);
+      if (pc[q] && run + pc[q] == V)  // the last occupied word
+        sm.s_last16 = uint32_t(w) * 32u + 31u - __clz(static_cast<int>(sm.bits[w]));
+      run += pc[q];
     }
   }
   __syncthreads();
-  const uint32_t vbase = sm.s_vbase;
+  const uint32_t last_key = (bucket << bshift) | sm.s_last16;
+  if (t == 0) publish_aggregate(bstat, bjob, j, V, last_key);
   const bool last_job = j + 1 == njobs;
-  for (uint32_t v = t; v < V; v += kLocalThreads) {
-    const uint32_t e0 = sm.u.hpos[v], e1 = sm.u.hpos[v + 1];
-    const uint32_t key = (bucket << bshift) | (sm.words[e0] >> 16);
-    Acc run = acc_zero();
-    run.n = e1 - e0;
-    for (uint32_t e = e0; e < e1; ++e) acc_add_payload(run, sm.pay[sm.words[e] & 0xffffu]);
-    const uint32_t cur = vbase + v;
-    const uint32_t prev_key = v > 0 ? ((bucket << bshift) | (sm.words[e0 - 1] >> 16)) : sm.s_prev_last;
-    write_row(rc, out, cur, key, prev_key, cur > 0, last_job && v + 1 == V, run, err);
-  }
-  __syncthreads();
-}
 
-// Rows of a large job after large_sort: sorted keys and payloads, and the run heads.
-struct LargeRows {
-  uint32_t* keys;
-  uint64_t* pay;
-  uint32_t* heads;
-};
-__device__ __forceinline__ LargeRows large_rows(uint32_t* K, uint64_t* P, uint32_t* K2,
-                                                uint64_t* P2, uint32_t bshift) {
-  // one on-chip digit pass leaves the rows in the other buffer; zero or two in this one
-  const bool moved = bshift != 0 && bshift <= 8;
-  return moved ? LargeRows{K2, P2, K} : LargeRows{K, P, K2};
-}
-
-// Large job, pre-pass: m > kLocalCap points, sorted through the other ping-pong buffer in
-// chunks of kLocalCap (stable LSD passes on the low digits, the same ranking as on chip);
-// the run heads go to the free key buffer and the voxel count is published as the job's
-// chained-scan aggregate before the main kernel starts, so no later job ever waits for a
-// large one's sort.
-__device__ void large_sort(LocalSmem& sm, uint32_t* K, uint64_t* P, uint32_t* K2, uint64_t* P2,
-                           uint32_t a, uint32_t m, uint32_t bucket, uint32_t bshift, int j,
-                           uint32_t* bstat, uint32_t* bjob) {
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  const uint32_t smask = bshift >= 32 ? kFull : ((1u << bshift) - 1u);
-  const int npl = bshift == 0 ? 0 : (bshift <= 8 ? 1 : 2);
-  uint32_t* hist = sm.words;              // [2][256]
-  uint32_t* base = sm.words + 2 * kRadix;  // [2][256]
-  uint32_t* runc = sm.words + 4 * kRadix;  // [256]
-  uint16_t* cnt = sm.cnt;
-  for (int d = t; d < 2 * kRadix; d += kLocalThreads) hist[d] = 0;
-  __syncthreads();
-  for (uint32_t e = t; e < m; e += kLocalThreads) {
-    const uint32_t k16 = K[a + e] & smask;
-    atomicAdd(&hist[k16 & (kRadix - 1)], 1u);
-    if (npl == 2) atomicAdd(&hist[kRadix + (k16 >> 8)], 1u);
-  }
-  __syncthreads();
-  digit_starts(hist, base, sm.tmp);
-  digit_starts(hist + kRadix, base + kRadix, sm.tmp);
-  uint32_t* sk = K;
-  uint64_t* sp = P;
-  uint32_t* dk = K2;
-  uint64_t* dp = P2;
-  for (int q = 0; q < npl; ++q) {
-    if (t < kRadix) runc[t] = 0;
+  // 3. windows of kBmWindow voxel slots: accumulate, then finalise into rows
+  for (uint32_t w0 = 0; w0 < V; w0 += kBmWindow) {
+    const uint32_t wn = V - w0 < uint32_t(kBmWindow) ? V - w0 : uint32_t(kBmWindow);
+    for (uint32_t i = t; i < wn; i += kBmThreads) {
+      sm.cnt[i] = 0;
+      sm.lo[0][i] = 0;
+      sm.lo[1][i] = 0;
+      sm.lo[2][i] = 0;
+      sm.hi[i] = 0;
+    }
+    // the keys of the window's slots, from the bitmap
+    for (int w = t; w < nw; w += kBmThreads) {
+      uint32_t b = sm.bits[w];
+      uint32_t r = sm.rank[w];
+      while (b) {
+        const uint32_t bit = __ffs(static_cast<int>(b)) - 1;
+        if (r >= w0 && r < w0 + wn) sm.vkey[r - w0] = static_cast<uint16_t>(uint32_t(w) * 32u + bit);
+        b &= b - 1;
+        ++r;
+      }
+    }
     __syncthreads();
-    for (uint32_t c0 = 0; c0 < m; c0 += kLocalCap) {
-      const uint32_t mc = m - c0 < uint32_t(kLocalCap) ? m - c0 : uint32_t(kLocalCap);
-      const int ipt = static_cast<int>((mc + kLocalThreads - 1) / kLocalThreads);
-      const uint32_t ebase = uint32_t(warp) * 32u * uint32_t(ipt) + uint32_t(lane);
-      uint32_t key[kLocalItems], rank[kLocalItems];
-      uint32_t valid = 0;
+    for (uint32_t c0 = 0; c0 < m; c0 += kBmChunk) {
 #pragma unroll
-      for (int j2 = 0; j2 < kLocalItems; ++j2) {
-        key[j2] = 0;
-        if (j2 < ipt) {
-          const uint32_t e = ebase + uint32_t(j2) * 32u;
-          if (e < mc) {
-            cp_async8(&sm.pay[e], sp + a + c0 + e);
-            key[j2] = sk[a + c0 + e] & smask;  // the bits above are the job's bucket
-            valid |= 1u << j2;
+      for (int i = 0; i < kBmItems; ++i) {
+        const uint32_t e = c0 + uint32_t(i) * kBmThreads + uint32_t(t);
+        if (e >= m) continue;
+        const uint32_t k = resident ? k16[i] : (__ldcs(K + a + e) & smask);
+        const uint32_t s = key_rank(sm, k) - w0;
+        if (s >= wn) continue;
+        const uint64_t p = __ldcs(P + a + e);
+        atomicAdd(&sm.cnt[s], 1u);
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+          const uint32_t v = static_cast<uint32_t>(p >> (21 * ax)) & 0x1fffffu;
+          const uint32_t old = atomicAdd(&sm.lo[ax][s], v);
+          if (old + v < old) atomicAdd(&sm.hi[s], 1u << (kCarryField * ax));
+        }
+      }
+    }
+    // the rows before this job (first window: by now the predecessors have published)
+    if (w0 == 0 && warp == 0) {
+      uint32_t prev_last = 0;
+      const uint32_t vb = resolve_job(bstat, bjob, j, V, spins, err, &prev_last);
+      if (lane == 0) {
+        sm.s_vbase = vb;
+        sm.s_prev_last = prev_last;
+        // the next ticket only now: taken any earlier, a job waits to start behind this
+        // one while later jobs' look-backs wait for it (measured slower)
+        take_next(sm, job_ctr, K, P, bjob, njobs, bshift);
+      }
+    }
+    __syncthreads();
+    // slots with kExactLimit points or more may have overflowed their carry fields: those
+    // (only in clouds with millions of points in one voxel) are summed again exactly
+    if (t == 0) sm.s_big = 0;
+    __syncthreads();
+    for (uint32_t i = t; i < wn; i += kBmThreads)
+      if (sm.cnt[i] >= kExactLimit) atomicOr(&sm.s_big, 1u);
+    __syncthreads();
+    const bool exact_pass = sm.s_big != 0;
+    const uint32_t vbase = sm.s_vbase;
+    for (uint32_t i = t; i < wn; i += kBmThreads) {
+      const uint32_t n = sm.cnt[i];
+      if (exact_pass && n >= kExactLimit) continue;  // written below
+      Acc acc;
+      acc.n = n;
+      const long long bias = static_cast<long long>(n) * kQMin;
+      acc.s[0] = slot_sum(sm, 0, int(i)) + bias;
+      acc.s[1] = slot_sum(sm, 1, int(i)) + bias;
+      acc.s[2] = slot_sum(sm, 2, int(i)) + bias;
+      const uint32_t r = w0 + i;
+      const uint32_t key = (bucket << bshift) | sm.vkey[i];
+      const uint32_t prev_key =
+          i > 0 ? ((bucket << bshift) | sm.vkey[i - 1])
+                : (r > 0 ? ((bucket << bshift) | sm.s_prev16) : sm.s_prev_last);
+      write_row(rc, out, vbase + r, key, prev_key, vbase + r > 0, last_job && r + 1 == V, acc,
+                err);
+    }
+    if (exact_pass) {
+      for (uint32_t i = 0; i < wn; ++i) {
+        if (sm.cnt[i] < kExactLimit) continue;  // (uniform: every thread reads the same slot)
+        const uint32_t kk = sm.vkey[i];
+        Acc part = acc_zero();
+        for (uint32_t e = t; e < m; e += kBmThreads)
+          if ((__ldcs(K + a + e) & smask) == kk) {
+            const uint64_t p = __ldcs(P + a + e);
+            part.s[0] += unpack_offset(p, 0);
+            part.s[1] += unpack_offset(p, 1);
+            part.s[2] += unpack_offset(p, 2);
           }
+        // block sum of the three axes
+        long long v3[3] = {part.s[0], part.s[1], part.s[2]};
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax)
+#pragma unroll
+          for (int off = 16; off; off >>= 1) v3[ax] += __shfl_xor_sync(kFull, v3[ax], off);
+        __syncthreads();
+        if (lane == 0)
+#pragma unroll
+          for (int ax = 0; ax < 3; ++ax) sm.red[warp][ax] = v3[ax];
+        __syncthreads();
+        if (t == 0) {
+          Acc acc = acc_zero();
+          acc.n = sm.cnt[i];
+          for (int w = 0; w < kBmWarps; ++w) {
+            acc.s[0] += sm.red[w][0];
+            acc.s[1] += sm.red[w][1];
+            acc.s[2] += sm.red[w][2];
+          }
+          const uint32_t r = w0 + i;
+          const uint32_t key = (bucket << bshift) | kk;
+          const uint32_t prev_key =
+              i > 0 ? ((bucket << bshift) | sm.vkey[i - 1])
+                    : (r > 0 ? ((bucket << bshift) | sm.s_prev16) : sm.s_prev_last);
+          write_row(rc, out, vbase + r, key, prev_key, vbase + r > 0, last_job && r + 1 == V,
+                    acc, err);
         }
       }
-      const uint32_t sh = 8u * uint32_t(q);
-      rank_items(key, sh, valid, ipt, sm.u.whist, rank, cnt);
-      cp_async_wait_all();
-      __syncthreads();
-#pragma unroll
-      for (int j2 = 0; j2 < kLocalItems; ++j2)
-        if (j2 < ipt && ((valid >> j2) & 1u)) {
-          const uint32_t d = (key[j2] >> sh) & (kRadix - 1);
-          const uint32_t g = base[q * kRadix + d] + runc[d] + rank[j2];
-          dk[a + g] = (bucket << bshift) | key[j2];
-          dp[a + g] = sm.pay[ebase + uint32_t(j2) * 32u];
-        }
-      __syncthreads();
-      if (t < kRadix) runc[t] += cnt[t];
-      __syncthreads();
     }
-    uint32_t* xk = sk;
-    uint64_t* xp = sp;
-    sk = dk;
-    sp = dp;
-    dk = xk;
-    dp = xp;
-  }
-  // sorted rows in (sk, sp); dk is free scratch for the run heads
-  uint32_t V = 0;
-  for (uint32_t c0 = 0; c0 < m; c0 += kLocalCap) {
-    const uint32_t mc = m - c0 < uint32_t(kLocalCap) ? m - c0 : uint32_t(kLocalCap);
-    const int ipt = static_cast<int>((mc + kLocalThreads - 1) / kLocalThreads);
-    const uint32_t p0 = c0 + uint32_t(t) * uint32_t(ipt);
-    uint32_t hmask = 0, hc = 0;
-#pragma unroll
-    for (int j2 = 0; j2 < kLocalItems; ++j2) {
-      const uint32_t p = p0 + uint32_t(j2);
-      if (j2 < ipt && p < c0 + mc) {
-        const bool head = p == 0 || sk[a + p] != sk[a + p - 1];
-        hmask |= uint32_t(head) << j2;
-        hc += head;
-      }
-    }
-    uint32_t tot;
-    uint32_t r = V + block_excl_scan(hc, &tot, sm.tmp);
-#pragma unroll
-    for (int j2 = 0; j2 < kLocalItems; ++j2)
-      if ((hmask >> j2) & 1u) dk[a + r++] = p0 + uint32_t(j2);
-    V += tot;
+    __syncthreads();
+    if (t == 0) sm.s_prev16 = sm.vkey[wn - 1];
     __syncthreads();
   }
-  if (t == 0) {
-    bjob[3 * size_t(j) + kJobLast] = sk[a + m - 1];
-    st_relaxed(bstat + j, kFlagAggregate | (V & kValueMask));
-  }
-  __syncthreads();
 }
 
-// Large job, main kernel: the rows before it from the chained scan, then its voxels from
-// the sorted rows in global memory (one voxel per thread; a single voxel block-wide).
-__device__ __noinline__ void large_reduce(LocalSmem& sm, uint32_t* K, uint64_t* P, uint32_t* K2,
-                                          uint64_t* P2, uint32_t a, uint32_t m, uint32_t bshift,
-                                          int j, int njobs, uint32_t* bstat, uint32_t* bjob,
-                                          uint32_t* job_ctr, const RowCtx& rc, const SegOut& out,
-                                          uint32_t spins, int* err) {
-  const int t = threadIdx.x;
-  const LargeRows R = large_rows(K, P, K2, P2, bshift);
-  const uint32_t* sk = R.keys;
-  const uint64_t* sp = R.pay;
-  const uint32_t* dk = R.heads;
-  if (t < 32) {
-    const uint32_t V = ld_relaxed(bstat + j) & kValueMask;  // the pre-pass's aggregate
-    uint32_t prev_last = 0;
-    const uint32_t vb = publish_job(bstat, bjob, j, V, false, 0u, spins, err, &prev_last);
-    if (t == 0) {
-      sm.s_vbase = vb;
-      sm.s_prev_last = prev_last;
-      sm.s_v = V;
-      take_next(sm, job_ctr, K, P, bjob, njobs, bshift);
-    }
-  }
-  __syncthreads();
-  const uint32_t vbase = sm.s_vbase, V = sm.s_v;
-  const bool last_job = j + 1 == njobs;
-  if (V == 1) {  // one voxel: a block-wide sum
-    Acc part = acc_zero();
-    for (uint32_t e = t; e < m; e += kLocalThreads) acc_add_payload(part, sp[a + e]);
-    part.n = 0;
-    Acc run = block_sum_acc(part, reinterpret_cast<long long (*)[4]>(&sm.u));
-    run.n = m;
-    if (t == 0) write_row(rc, out, vbase, sk[a], sm.s_prev_last, vbase > 0, last_job, run, err);
-  } else {
-    for (uint32_t v = t; v < V; v += kLocalThreads) {
-      const uint32_t e0 = dk[a + v], e1 = v + 1 < V ? dk[a + v + 1] : m;
-      Acc run = acc_zero();
-      run.n = e1 - e0;
-      for (uint32_t e = e0; e < e1; ++e) acc_add_payload(run, sp[a + e]);
-      const uint32_t cur = vbase + v;
-      const uint32_t prev_key = v > 0 ? sk[a + e0 - 1] : sm.s_prev_last;
-      write_row(rc, out, cur, sk[a + e0], prev_key, cur > 0, last_job && v + 1 == V, run, err);
-    }
-  }
-  __syncthreads();
-}
-
-
-__global__ __launch_bounds__(kLocalThreads, 2) void bucket_local_kernel(
+__global__ __launch_bounds__(kBmThreads, VG_BM_MINB) void bucket_local_kernel(
     State* st, const FrameState* __restrict__ fs, int nframes, uint32_t* k0, uint64_t* p0,
     uint32_t* k1, uint64_t* p1, uint32_t* bstat, uint32_t* bjob, SegOut out, uint32_t spins,
     int* err) {
-  extern __shared__ __align__(128) unsigned char local_smem[];
-  LocalSmem& sm = *reinterpret_cast<LocalSmem*>(local_smem);
+  extern __shared__ __align__(128) unsigned char bm_smem[];
+  BmSmem& sm = *reinterpret_cast<BmSmem*>(bm_smem);
   if (!(st->narrow && st->bucket)) return;
   const int njobs = static_cast<int>(st->njobs);
   if (njobs == 0) return;
   const bool odd = pass_count(st) & 1;
-  uint32_t* K = odd ? k1 : k0;
-  uint64_t* P = odd ? p1 : p0;
-  uint32_t* K2 = odd ? k0 : k1;
-  uint64_t* P2 = odd ? p0 : p1;
+  const uint32_t* K = odd ? k1 : k0;
+  const uint64_t* P = odd ? p1 : p0;
   const uint32_t bshift = st->bshift;
   RowCtx rc{fs, st->key_shift, nframes, {fs[0].origin[0], fs[0].origin[1], fs[0].origin[2]},
             fs[0].leaf};
@@ -626,55 +466,18 @@ __global__ __launch_bounds__(kLocalThreads, 2) void bucket_local_kernel(
     if (j >= njobs) break;
     const uint32_t a = sm.s_na, m = sm.s_nm, bucket = sm.s_nbucket;
     __syncthreads();  // (the descriptor slots are refilled by this job's take_next)
-    if (m <= uint32_t(kLocalCap))
-      small_job(sm, K, P, a, m, bucket, bshift, j, njobs, bstat, bjob, &st->job_ctr, rc, out,
-                spins, err);
-    else
-      large_reduce(sm, K, P, K2, P2, a, m, bshift, j, njobs, bstat, bjob, &st->job_ctr, rc, out,
-                   spins, err);
+    bucket_job(sm, K, P, a, m, bucket, bshift, j, njobs, bstat, bjob, &st->job_ctr, rc, out,
+               spins, err);
     if (t == 0) sm.s_job = sm.s_next;
     __syncthreads();
-  }
-}
-
-// Pre-pass over the large jobs (in any order: each publishes only its own aggregate).
-__global__ __launch_bounds__(kLocalThreads, 2) void bucket_large_kernel(State* st, uint32_t* k0,
-                                                                        uint64_t* p0, uint32_t* k1,
-                                                                        uint64_t* p1,
-                                                                        uint32_t* bstat,
-                                                                        uint32_t* bjob) {
-  extern __shared__ __align__(128) unsigned char local_smem[];
-  LocalSmem& sm = *reinterpret_cast<LocalSmem*>(local_smem);
-  if (!(st->narrow && st->bucket)) return;
-  const int nbig = static_cast<int>(st->nbig);
-  if (nbig == 0) return;
-  const bool odd = pass_count(st) & 1;
-  uint32_t* K = odd ? k1 : k0;
-  uint64_t* P = odd ? p1 : p0;
-  uint32_t* K2 = odd ? k0 : k1;
-  uint64_t* P2 = odd ? p0 : p1;
-  const uint32_t bshift = st->bshift;
-  const uint32_t* big = bjob + 3 * size_t(kBucketSlots);
-  for (;;) {
-    if (threadIdx.x == 0) sm.s_job = static_cast<int>(atomicAdd(&st->big_ctr, 1u));
-    __syncthreads();
-    const int b = sm.s_job;
-    __syncthreads();
-    if (b >= nbig) break;
-    const int j = static_cast<int>(big[b]);
-    const uint32_t a = bjob[3 * size_t(j) + kJobStart];
-    const uint32_t m = bjob[3 * size_t(j) + kJobCount];
-    large_sort(sm, K, P, K2, P2, a, m, K[a] >> bshift, bshift, j, bstat, bjob);
   }
 }
 
 }  // namespace
 
 void warm_bucket_config() {
-  persistent_grid(reinterpret_cast<const void*>(bucket_local_kernel), kLocalThreads,
-                  sizeof(LocalSmem), 1);
-  persistent_grid(reinterpret_cast<const void*>(bucket_large_kernel), kLocalThreads,
-                  sizeof(LocalSmem), 1);
+  persistent_grid(reinterpret_cast<const void*>(bucket_local_kernel), kBmThreads, sizeof(BmSmem),
+                  1);
 }
 
 cudaError_t launch_bucket_tail(State* st, const FrameState* fs, int nframes,
@@ -683,13 +486,9 @@ cudaError_t launch_bucket_tail(State* st, const FrameState* fs, int nframes,
                                uint32_t spin_limit, int* err, cudaStream_t stream) {
   if (n_max == 0) return cudaSuccess;
   bucket_scan_kernel<<<1, 1024, 0, stream>>>(st, bcount, bjob);
-  const int lgrid = persistent_grid(reinterpret_cast<const void*>(bucket_large_kernel),
-                                    kLocalThreads, sizeof(LocalSmem), kBucketSlots);
-  bucket_large_kernel<<<lgrid, kLocalThreads, sizeof(LocalSmem), stream>>>(
-      st, nb.k0, nb.p0, nb.k1, nb.p1, bstat, bjob);
   const int grid = persistent_grid(reinterpret_cast<const void*>(bucket_local_kernel),
-                                   kLocalThreads, sizeof(LocalSmem), kBucketSlots);
-  bucket_local_kernel<<<grid, kLocalThreads, sizeof(LocalSmem), stream>>>(
+                                   kBmThreads, sizeof(BmSmem), kBucketSlots);
+  bucket_local_kernel<<<grid, kBmThreads, sizeof(BmSmem), stream>>>(
       st, fs, nframes, nb.k0, nb.p0, nb.k1, nb.p1, bstat, bjob, out, spin_limit, err);
   return cudaGetLastError();
 }

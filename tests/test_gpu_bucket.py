@@ -1,9 +1,10 @@
 """The bucket tail of the narrow sort path (method "sort_bucket": the radix passes sort
-the top key digits, every bucket of the low ones is sorted and reduced in one block's
-shared memory): the same rows as the oracle and, bit for bit, as the all-global radix
-sort (method "sort"),
-for 0, 1 and 2 on-chip passes, buckets larger than one block (sorted through global
-scratch in chunks), a bucket that is one voxel, skewed clouds and batched frames."""
+the top key digits, every bucket is reduced in one block's shared memory through an
+occupancy bitmap of its low key bits): the same rows as the oracle and, bit for bit, as
+the all-global radix sort (method "sort"), for bucket shifts of 0, at most 8 and above 8
+bits, buckets of more points than a block holds in registers and of more voxels than one
+window of slots, buckets that are one voxel, a voxel of more points than the 32-bit slot
+sums and their carry counts hold, skewed clouds, batched frames and the pyramid."""
 import numpy as np
 import pytest
 import torch
@@ -40,22 +41,23 @@ def rng(seed):
 
 
 @pytest.mark.parametrize("n", [1, 2, 511, 512, 513, 8191, 8192, 8193, 100_000])
-def test_sizes_around_block_capacity(n):
+def test_sizes_around_a_register_chunk(n):
     x = synth.random_cloud(n, seed=17 + n, extent=2.0, nan_frac=0.03)
     check(x, 0.02)
 
 
 @pytest.mark.parametrize("edge,n", [(4, 50_000), (30, 50_000), (700, 120_000)])
-def test_zero_one_two_onchip_passes(edge, n):
-    # key widths of 6, 15 and 30 bits: the bucket shift is 0 (no on-chip pass),
-    # at most 8 (one) and above 8 (two)
+def test_bucket_shifts(edge, n):
+    # key widths of 6, 15 and 30 bits: bucket shifts of 0 (one key per bucket), at most 8
+    # and above 8 bits (bitmaps of one word up to 2048 words)
     x = (rng(edge).random((n, 3)) * edge * 0.02).astype(np.float32)
     check(x, 0.02, np.zeros(3, np.float32))
 
 
 def test_bucket_larger_than_a_block():
-    # a dense 0.4 m cluster holds ~150k points in one bucket (far more than one block
-    # sorts on chip); a handful of far points widen the key to 30 bits
+    # a dense 0.4 m cluster puts ~150k points and ~8000 voxels in one bucket (more points
+    # than a block holds in registers, more voxels than one window of slots); a handful of
+    # far points widen the key to 30 bits
     r = rng(5)
     cluster = (r.random((150_000, 3)) * 0.4).astype(np.float32)
     far = (r.random((50, 3)) * 20.0).astype(np.float32)
@@ -65,9 +67,17 @@ def test_bucket_larger_than_a_block():
 
 
 def test_one_voxel_buckets_of_many_points():
-    # 8 voxels of ~12k points each: every bucket is one voxel, too large for one block
+    # 8 voxels of ~12k points each: every bucket is one voxel
     x = (rng(6).random((100_000, 3)) * 2.0).astype(np.float32)
     check(x, 1.0, np.zeros(3, np.float32))
+
+
+def test_voxel_beyond_the_slot_carry_limit():
+    # 2.2M points in one voxel: more than the slot's 32-bit sums with 10-bit carry counts
+    # hold, so the voxel is summed again exactly
+    x = (0.2 + rng(11).random((2_200_000, 3)) * 0.6).astype(np.float32)
+    got = check(x, 1.0, np.zeros(3, np.float32))
+    assert int(gpu_counts(got.counts)[0]) == 2_200_000
 
 
 def test_all_points_in_one_voxel():
