@@ -575,7 +575,7 @@ def run_vg(args, rank, world, local):
     # copy in and decimation run while step k's rows are copied back
     del keys_h, cent_h, cnt_h
     from paper_2102_11084_gb300 import serve
-    pipe = serve.CloudPipeline(n, args.leaf, depth=3, device=dev)
+    pipe = serve.CloudPipeline(n, args.leaf, depth=3, method=args.method, device=dev)
     for _ in pipe.run([xyz_host] * 3):  # untimed: first touch of the slots' buffers
         pass
     torch.cuda.synchronize()

@@ -61,9 +61,10 @@ struct BmSmem {
   uint16_t vkey[kBmWindow];           // low key bits of every slot
   uint32_t tmp[kBmWarps];
   long long red[kBmWarps][4];
-  int s_job, s_next;
-  uint32_t s_a, s_m, s_bucket, s_na, s_nm, s_nbucket;
-  uint32_t s_v, s_vbase, s_prev_last, s_last16, s_prev16, s_big;
+  int s_job, s_next;                    // current and next ticket
+  uint32_t s_na, s_nm, s_nbucket;       // next job: first point, points, bucket
+  uint32_t s_vbase, s_prev_last;        // rows before this job; job j - 1's largest key
+  uint32_t s_last16, s_prev16, s_big;   // largest key bits; last slot key of the window
 };
 // VG_BM_MINB blocks per SM: each takes this + 1 KB reserved of the SM's 228 KB.
 static_assert((sizeof(BmSmem) + 1024) * VG_BM_MINB <= 228 * 1024, "bucket block shared memory");
