@@ -29,7 +29,8 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 // Geometry (build-time; the defaults are the measured best on the 50M map: 256 threads x 4
-// blocks with 1792 slots, 128 x 6 with 1024, and 256 x 2 with 3584 were all slower).
+// blocks with 1792 slots, 128 x 6 with 1024 and 256 x 2 with 3584 were slower, and with
+// the chained-scan wait taken out 256 x 4 was still slower than 512 x 2).
 #ifndef VG_BM_THREADS
 #define VG_BM_THREADS 512
 #endif
