@@ -15,7 +15,7 @@
 //     parent of a Morton-coded voxel is key >> 3 (the "iterative reduction with an
 //     ordered subdivision of space" of the abstract is read as this pyramid).
 //
-// Readings where the paper is silent (all listed in the design doc):
+// Readings where the paper is silent:
 //   R1  a point is valid iff x, y and z are all finite (NaN marks a missing depth);
 //   R2  per axis, in IEEE binary32 with round-to-nearest and no contraction:
 //         t = fl(p - o), q = fl(t / leaf), i = floor(q);  a point on a face goes up;
