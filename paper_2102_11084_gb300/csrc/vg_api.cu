@@ -174,6 +174,8 @@ vg_status run_frames(const float* xyz, const FramesArg& fr, bool from_min, const
     int* err = out_error ? reinterpret_cast<int*>(out_error) : &st->error;
 
     cudaError_t e = cudaMemsetAsync(ws, 0, L.zero_bytes, stream);
+    if (e == cudaSuccess && btail)  // bucket counts and job status, adjacent
+      e = cudaMemsetAsync(ws + L.bcount, 0, L.bjob - L.bcount, stream);
     if (e == cudaSuccess && out_error) e = cudaMemsetAsync(out_error, 0, sizeof(int32_t), stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(out.num_voxels, 0, sizeof(int64_t), stream);
     if (e == cudaSuccess && out.frame_offsets)

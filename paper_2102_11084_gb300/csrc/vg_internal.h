@@ -179,13 +179,13 @@ constexpr SortLayout sort_layout(int64_t n, int frames = 1) {
   off = align_up(off + size_t(L.sort_tiles) * kRadix * sizeof(uint32_t), 256);
   L.seg_lb = off;  // per-tile records, then the tiles' head counts as a compact array
   off = align_up(off + size_t(L.seg_tiles) * (sizeof(TileRec) + sizeof(uint32_t)), 256);
-  L.bcount = off;  // points per bucket (bucket tail)
+  L.zero_bytes = off;  // state, frames, pass-0 status rows and segment status
+  L.bcount = off;  // points per bucket, then the chained-scan status per bucket job (the
+  off = align_up(off + size_t(kBucketSlots) * sizeof(uint32_t), 256);  // bucket tail
+  L.bstat = off;   // zeroes both only when it runs)
   off = align_up(off + size_t(kBucketSlots) * sizeof(uint32_t), 256);
-  L.bstat = off;  // chained-scan status per bucket job
-  off = align_up(off + size_t(kBucketSlots) * sizeof(uint32_t), 256);
-  L.zero_bytes = off;  // state, frames, pass-0 status rows, segment and bucket counters
-  L.bjob = off;  // per job: first point, points, largest key (3 x u32), then the list
-  off = align_up(off + size_t(kBucketSlots) * 4 * sizeof(uint32_t), 256);  // of large jobs
+  L.bjob = off;  // job table: first point, points, largest key (kBucketSlots each)
+  off = align_up(off + size_t(kBucketSlots) * 3 * sizeof(uint32_t), 256);
   L.lb_b = off;
   off = align_up(off + size_t(L.sort_tiles) * kRadix * sizeof(uint32_t), 256);
   L.keys0 = off;  // also the two 32-bit key arrays of the narrow layout, 16-byte aligned
