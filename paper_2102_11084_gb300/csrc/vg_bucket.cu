@@ -1,19 +1,19 @@
 // Bucket tail of the narrow sort path (opt-in): the radix passes (vg_sort.cu) order the
 // points by their bucket, the top L <= 16 bits of the sort key (key >> bshift), and count
 // the points of every bucket.  Here a one-block scan turns the counts into jobs (the
-// non-empty buckets, in key order), and a persistent kernel takes the jobs in ticket
-// order and reduces each bucket in shared memory without sorting it:
-//   * an occupancy bitmap over the bucket's low key bits (2^bshift <= 65536 bits, 8 KB);
+// non-empty buckets, in key order); a counting kernel finds every job's voxel count (the
+// population of an occupancy bitmap over the bucket's low key bits) and largest key; a
+// one-block scan turns the counts into each job's first row; and a persistent kernel
+// reduces the buckets in shared memory without sorting them:
+//   * the occupancy bitmap again (2^bshift <= 65536 bits, 8 KB);
 //   * a prefix popcount over the bitmap gives every occupied key its rank, i.e. its row
-//     within the bucket (the bucket's voxels in key order), and the bucket's voxel count;
+//     within the bucket (the bucket's voxels in key order);
 //   * every point adds its count and fixed-point offsets into its voxel's slot with
 //     shared-memory atomics (32-bit sums plus a carry count per axis, so the totals are
 //     exact integers: the rows are bit-identical to the sorted path's);
-//   * the slots are finalised into rows at the bucket's first row, which a chained scan
-//     over the jobs gives (each job publishes its voxel count as soon as its bitmap is
-//     counted, and waits for the rows before it only after it has accumulated).
-// Buckets of any size: points are streamed in chunks of kBmChunk, voxels in windows of
-// kBmWindow slots.
+//   * the slots are finalised into rows from the job's first row on.
+// No job waits for another.  Buckets of any size: points are streamed in chunks of
+// kBmChunk, voxels in windows of kBmWindow slots.
 //
 // arXiv 2102.11084 Sec. II-C / Algorithm 1 sorts the (cell, point) table with a radix
 // sort so that the points of each cell are contiguous, then reduces every cell.  Here the
@@ -53,6 +53,12 @@ constexpr uint32_t kExactLimit = 1u << 21;                // points of a slot th
 // Job table (bjob, kBucketSlots entries per array): first point at [0, S), points at
 // [S, 2S), largest key at [2S, 3S), S = kBucketSlots.
 
+// A job's descriptor: first point, points, bucket, first row, and the largest key of the
+// job before it (frame marks).  Independent loads (the bucket comes from the job's own
+// largest key).
+struct JobDesc {
+  uint32_t a, m, bucket, vbase, prev;
+};
 struct BmSmem {
   uint32_t bits[kBmWords];            // occupancy of the low key bits
   uint16_t rank[kBmWords];            // occupied keys before each word (exclusive)
@@ -62,10 +68,8 @@ struct BmSmem {
   uint16_t vkey[kBmWindow];           // low key bits of every slot
   uint32_t tmp[kBmWarps];
   long long red[kBmWarps][4];
-  int s_job, s_next;                    // current and next ticket
-  uint32_t s_na, s_nm, s_nbucket;       // next job: first point, points, bucket
-  uint32_t s_vbase, s_prev_last;        // rows before this job; job j - 1's largest key
-  uint32_t s_last16, s_prev16, s_big;   // largest key bits; last slot key of the window
+  JobDesc s_desc;                       // the job about to run
+  uint32_t s_prev16, s_big;             // last slot key of the window; big-slot flag
 };
 // VG_BM_MINB blocks per SM: each takes this + 1 KB reserved of the SM's 228 KB.
 static_assert((sizeof(BmSmem) + 1024) * VG_BM_MINB <= 228 * 1024, "bucket block shared memory");
@@ -127,90 +131,45 @@ __device__ __forceinline__ void write_row(const RowCtx& rc, const SegOut& out, u
   if (last) *out.num_voxels = int64_t(cur) + 1;
 }
 
-// Warp-wide chained-scan wait over the jobs before j: every round trip loads 32
-// predecessors' status words (a wave of jobs publishes its aggregates at about the same
-// time, so a one-word walk would pay one L2 round trip per job).  Returns the exclusive
-// prefix of job j (the same in every lane).  Bounded like every other wait.
-__device__ __forceinline__ uint32_t warp_lookback(const uint32_t* status, int j,
-                                                  uint32_t spin_limit, int* err) {
-  const int lane = threadIdx.x & 31;
-  uint32_t excl = 0, spins = 0;
-  int base = j - 1;
-  while (base >= 0) {
-    const int idx = base - lane;
-    const uint32_t w = idx >= 0 ? ld_relaxed(status + idx) : kFlagPrefix;  // before job 0: 0
-    const uint32_t f = w & ~kValueMask;
-    const uint32_t notready = __ballot_sync(kFull, f == 0);
-    const uint32_t prefix = __ballot_sync(kFull, f == kFlagPrefix);
-    const int first_nr = notready ? __ffs(static_cast<int>(notready)) - 1 : 32;
-    const int first_p = prefix ? __ffs(static_cast<int>(prefix)) - 1 : 32;
-    const bool done = first_p < first_nr;
-    const int take = done ? first_p + 1 : first_nr;
-    uint32_t v = lane < take ? (w & kValueMask) : 0u;
-#pragma unroll
-    for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
-    excl += v;
-    if (done) break;
-    base -= take;
-    if (take == 0) {
-      if (++spins > spin_limit) {
-        if (lane == 0) set_error(err, kErrTimeout);
-        break;
-      }
-      if (spins > 64) __nanosleep(64);
-    }
-  }
-  return excl;
-}
-
-// Warp 0: publishes job j's aggregate (`v` voxels) after its largest key.
-__device__ __forceinline__ void publish_aggregate(uint32_t* bstat, uint32_t* bjob, int j,
-                                                  uint32_t v, uint32_t last_key) {
-  bjob[2 * size_t(kBucketSlots) + j] = last_key;
-  __threadfence();
-  st_relaxed(bstat + j, (j == 0 ? kFlagPrefix : kFlagAggregate) | v);
-}
-
-// Warp 0, after publish_aggregate: the rows before job j, then its prefix.  Returns the
-// rows before it (same in every lane); lane 0 sets *prev_last = job j - 1's largest key.
-__device__ __forceinline__ uint32_t resolve_job(uint32_t* bstat, const uint32_t* bjob, int j,
-                                                uint32_t v, uint32_t spins, int* err,
-                                                uint32_t* prev_last) {
-  if (j == 0) return 0;
-  const uint32_t excl = warp_lookback(bstat, j, spins, err);
-  if ((threadIdx.x & 31) == 0) {
-    st_relaxed(bstat + j, kFlagPrefix | ((excl + v) & kValueMask));
-    __threadfence();
-    *prev_last = ld_relaxed(bjob + 2 * size_t(kBucketSlots) + (j - 1));
-  }
-  return excl;
-}
-
 // ---- the jobs -------------------------------------------------------------------------
 
 // One block: the non-empty buckets in key order become jobs (first point, points), in
-// rounds of 4096 buckets so that consecutive threads write consecutive jobs.
+// rounds of 16 consecutive buckets per thread (four 16-byte loads in flight), so that a
+// thread writes consecutive jobs.
 __global__ __launch_bounds__(1024) void bucket_scan_kernel(State* st, const uint32_t* __restrict__ bcount,
                                                            uint32_t* __restrict__ bjob) {
   __shared__ uint32_t tmp[32];
   __shared__ uint32_t smax[32];
   if (!(st->narrow && st->bucket)) return;
+  constexpr int kPer = 16;
   const int t = threadIdx.x;
   uint32_t* job_start = bjob;
   uint32_t* job_count = bjob + kBucketSlots;
   uint32_t base_e = 0, base_j = 0, mx = 0;
-  for (int r0 = 0; r0 < kBucketSlots; r0 += 4 * 1024) {
-    const uint4 v = reinterpret_cast<const uint4*>(bcount + r0)[t];
-    const uint32_t c[4] = {v.x, v.y, v.z, v.w};
-    const uint32_t sum = v.x + v.y + v.z + v.w;
-    const uint32_t nz = (v.x != 0) + (v.y != 0) + (v.z != 0) + (v.w != 0);
-    mx = max(max(mx, max(v.x, v.y)), max(v.z, v.w));
+  for (int r0 = 0; r0 < kBucketSlots; r0 += kPer * 1024) {
+    const uint4* c4 = reinterpret_cast<const uint4*>(bcount + r0 + kPer * t);
+    uint32_t c[kPer];
+#pragma unroll
+    for (int q = 0; q < kPer / 4; ++q) {
+      const uint4 v = c4[q];
+      c[4 * q] = v.x;
+      c[4 * q + 1] = v.y;
+      c[4 * q + 2] = v.z;
+      c[4 * q + 3] = v.w;
+    }
+    uint32_t sum = 0, nz = 0;
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      sum += c[q];
+      nz += c[q] != 0;
+      mx = max(mx, c[q]);
+    }
     uint32_t tot_e, tot_j;
     uint32_t run_e = base_e + block_excl_scan(sum, &tot_e, tmp);
     __syncthreads();
     uint32_t run_j = base_j + block_excl_scan(nz, &tot_j, tmp);
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
+    for (int q = 0; q < kPer; ++q)
       if (c[q]) {
         job_start[run_j] = run_e;
         job_count[run_j] = c[q];
@@ -235,22 +194,15 @@ __global__ __launch_bounds__(1024) void bucket_scan_kernel(State* st, const uint
   }
 }
 
-// Thread 0: the next ticket and its descriptor; its rows start their way into L2 while
-// the current job runs.
-__device__ __forceinline__ void take_next(BmSmem& sm, uint32_t* job_ctr, const uint32_t* K,
-                                          const uint64_t* P, const uint32_t* bjob, int njobs,
-                                          uint32_t bshift) {
-  const int nx = static_cast<int>(atomicAdd(job_ctr, 1u));
-  sm.s_next = nx;
-  if (nx < njobs) {
-    const uint32_t na = bjob[nx];
-    const uint32_t nm = bjob[kBucketSlots + nx];
-    prefetch_range(K + na, size_t(nm) * sizeof(uint32_t));
-    prefetch_range(P + na, size_t(nm) * sizeof(uint64_t));
-    sm.s_na = na;
-    sm.s_nm = nm;
-    sm.s_nbucket = K[na] >> bshift;
-  }
+__device__ __forceinline__ JobDesc load_desc(const uint32_t* bjob, const uint32_t* vbase, int j,
+                                             uint32_t bshift) {
+  JobDesc d;
+  d.a = bjob[j];
+  d.m = bjob[kBucketSlots + j];
+  d.bucket = bjob[2 * size_t(kBucketSlots) + j] >> bshift;
+  d.vbase = vbase[j];
+  d.prev = j > 0 ? bjob[2 * size_t(kBucketSlots) + j - 1] : 0u;
+  return d;
 }
 
 // Rank of low key bits k16 among the bucket's occupied keys.
@@ -265,13 +217,13 @@ __device__ __forceinline__ long long slot_sum(const BmSmem& sm, int axis, int i)
   return static_cast<long long>((carry << 32) | sm.lo[axis][i]);
 }
 
-// One job: the bucket's m points at [a, a + m).
+// One job: the bucket's m points at [a, a + m), its rows from row vbase on; prev_last is
+// the largest key of the job before it (frame marks).
 __device__ __forceinline__ void bucket_job(BmSmem& sm, const uint32_t* __restrict__ K,
                                            const uint64_t* __restrict__ P, uint32_t a, uint32_t m,
-                                           uint32_t bucket, uint32_t bshift, int j, int njobs,
-                                           uint32_t* bstat, uint32_t* bjob, uint32_t* job_ctr,
-                                           const RowCtx& rc, const SegOut& out, uint32_t spins,
-                                           int* err) {
+                                           uint32_t bucket, uint32_t bshift, uint32_t vbase,
+                                           uint32_t prev_last, bool last_job, const RowCtx& rc,
+                                           const SegOut& out, int* err) {
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const uint32_t smask = (1u << bshift) - 1u;  // bshift <= 16
   const int nw = bshift >= 5 ? 1 << (bshift - 5) : 1;
@@ -282,12 +234,15 @@ __device__ __forceinline__ void bucket_job(BmSmem& sm, const uint32_t* __restric
   // 1. occupancy bitmap
   uint32_t k16[kBmItems];
   for (uint32_t c0 = 0; c0 < m; c0 += kBmChunk) {
+    // all loads first, then the atomics (so the loads overlap)
 #pragma unroll
     for (int i = 0; i < kBmItems; ++i) {
       const uint32_t e = c0 + uint32_t(i) * kBmThreads + uint32_t(t);
       k16[i] = e < m ? (__ldcs(K + a + e) & smask) : kFull;
-      if (k16[i] != kFull) atomicOr(&sm.bits[k16[i] >> 5], 1u << (k16[i] & 31u));
     }
+#pragma unroll
+    for (int i = 0; i < kBmItems; ++i)
+      if (k16[i] != kFull) atomicOr(&sm.bits[k16[i] >> 5], 1u << (k16[i] & 31u));
   }
   __syncthreads();
 
@@ -306,19 +261,15 @@ __device__ __forceinline__ void bucket_job(BmSmem& sm, const uint32_t* __restric
     const int w = kBmWordsPerThread * t + q;
     if (w < nw) {
       sm.rank[w] = static_cast<uint16_t>(run);
-      if (pc[q] && run + pc[q] == V)  // the last occupied word
-        sm.s_last16 = uint32_t(w) * 32u + 31u - __clz(static_cast<int>(sm.bits[w]));
       run += pc[q];
     }
   }
   __syncthreads();
-  const uint32_t last_key = (bucket << bshift) | sm.s_last16;
-  if (t == 0) publish_aggregate(bstat, bjob, j, V, last_key);
-  const bool last_job = j + 1 == njobs;
 
   // 3. windows of kBmWindow voxel slots: accumulate, then finalise into rows
   for (uint32_t w0 = 0; w0 < V; w0 += kBmWindow) {
     const uint32_t wn = V - w0 < uint32_t(kBmWindow) ? V - w0 : uint32_t(kBmWindow);
+    if (t == 0) sm.s_big = 0;
     for (uint32_t i = t; i < wn; i += kBmThreads) {
       sm.cnt[i] = 0;
       sm.lo[0][i] = 0;
@@ -339,45 +290,44 @@ __device__ __forceinline__ void bucket_job(BmSmem& sm, const uint32_t* __restric
     }
     __syncthreads();
     for (uint32_t c0 = 0; c0 < m; c0 += kBmChunk) {
+      // in halves: the half's payload loads first, then its atomics
 #pragma unroll
-      for (int i = 0; i < kBmItems; ++i) {
-        const uint32_t e = c0 + uint32_t(i) * kBmThreads + uint32_t(t);
-        if (e >= m) continue;
-        const uint32_t k = resident ? k16[i] : (__ldcs(K + a + e) & smask);
-        const uint32_t s = key_rank(sm, k) - w0;
-        if (s >= wn) continue;
-        const uint64_t p = __ldcs(P + a + e);
-        atomicAdd(&sm.cnt[s], 1u);
+      for (int h = 0; h < kBmItems; h += kBmItems / 2) {
+        uint64_t pl[kBmItems / 2];
+        uint32_t sl[kBmItems / 2];
 #pragma unroll
-        for (int ax = 0; ax < 3; ++ax) {
-          const uint32_t v = static_cast<uint32_t>(p >> (21 * ax)) & 0x1fffffu;
-          const uint32_t old = atomicAdd(&sm.lo[ax][s], v);
-          if (old + v < old) atomicAdd(&sm.hi[s], 1u << (kCarryField * ax));
+        for (int i = 0; i < kBmItems / 2; ++i) {
+          const uint32_t e = c0 + uint32_t(h + i) * kBmThreads + uint32_t(t);
+          sl[i] = kFull;
+          pl[i] = 0;
+          if (e < m) {
+            const uint32_t k = resident ? k16[h + i] : (__ldcs(K + a + e) & smask);
+            const uint32_t s = key_rank(sm, k) - w0;
+            if (s < wn) {
+              sl[i] = s;
+              pl[i] = __ldcs(P + a + e);
+            }
+          }
         }
-      }
-    }
-    // the rows before this job (first window: by now the predecessors have published)
-    if (w0 == 0 && warp == 0) {
-      uint32_t prev_last = 0;
-      const uint32_t vb = resolve_job(bstat, bjob, j, V, spins, err, &prev_last);
-      if (lane == 0) {
-        sm.s_vbase = vb;
-        sm.s_prev_last = prev_last;
-        // the next ticket only now: taken any earlier, a job waits to start behind this
-        // one while later jobs' look-backs wait for it (measured slower)
-        take_next(sm, job_ctr, K, P, bjob, njobs, bshift);
+#pragma unroll
+        for (int i = 0; i < kBmItems / 2; ++i) {
+          if (sl[i] == kFull) continue;
+          const uint32_t s = sl[i];
+          // the point that fills a slot to kExactLimit flags the window for the exact pass
+          if (atomicAdd(&sm.cnt[s], 1u) + 1u == kExactLimit) sm.s_big = 1u;
+#pragma unroll
+          for (int ax = 0; ax < 3; ++ax) {
+            const uint32_t v = static_cast<uint32_t>(pl[i] >> (21 * ax)) & 0x1fffffu;
+            const uint32_t old = atomicAdd(&sm.lo[ax][s], v);
+            if (old + v < old) atomicAdd(&sm.hi[s], 1u << (kCarryField * ax));
+          }
+        }
       }
     }
     __syncthreads();
     // slots with kExactLimit points or more may have overflowed their carry fields: those
     // (only in clouds with millions of points in one voxel) are summed again exactly
-    if (t == 0) sm.s_big = 0;
-    __syncthreads();
-    for (uint32_t i = t; i < wn; i += kBmThreads)
-      if (sm.cnt[i] >= kExactLimit) atomicOr(&sm.s_big, 1u);
-    __syncthreads();
     const bool exact_pass = sm.s_big != 0;
-    const uint32_t vbase = sm.s_vbase;
     for (uint32_t i = t; i < wn; i += kBmThreads) {
       const uint32_t n = sm.cnt[i];
       if (exact_pass && n >= kExactLimit) continue;  // written below
@@ -391,7 +341,7 @@ __device__ __forceinline__ void bucket_job(BmSmem& sm, const uint32_t* __restric
       const uint32_t key = (bucket << bshift) | sm.vkey[i];
       const uint32_t prev_key =
           i > 0 ? ((bucket << bshift) | sm.vkey[i - 1])
-                : (r > 0 ? ((bucket << bshift) | sm.s_prev16) : sm.s_prev_last);
+                : (r > 0 ? ((bucket << bshift) | sm.s_prev16) : prev_last);
       write_row(rc, out, vbase + r, key, prev_key, vbase + r > 0, last_job && r + 1 == V, acc,
                 err);
     }
@@ -430,7 +380,7 @@ __device__ __forceinline__ void bucket_job(BmSmem& sm, const uint32_t* __restric
           const uint32_t key = (bucket << bshift) | kk;
           const uint32_t prev_key =
               i > 0 ? ((bucket << bshift) | sm.vkey[i - 1])
-                    : (r > 0 ? ((bucket << bshift) | sm.s_prev16) : sm.s_prev_last);
+                    : (r > 0 ? ((bucket << bshift) | sm.s_prev16) : prev_last);
           write_row(rc, out, vbase + r, key, prev_key, vbase + r > 0, last_job && r + 1 == V,
                     acc, err);
         }
@@ -442,15 +392,113 @@ __device__ __forceinline__ void bucket_job(BmSmem& sm, const uint32_t* __restric
   }
 }
 
+// Voxels of every job: its bitmap's population (no accumulation), then the job's largest
+// key.  Small blocks, many per SM: a job here is one pass over its keys.
+constexpr int kCountThreads = 256;
+__global__ __launch_bounds__(kCountThreads) void bucket_count_kernel(State* st, const uint32_t* k0,
+                                                                     const uint32_t* k1,
+                                                                     uint32_t* __restrict__ vox,
+                                                                     uint32_t* __restrict__ bjob) {
+  __shared__ uint32_t bits[kBmWords];
+  __shared__ uint32_t s_sum[kCountThreads / 32];
+  __shared__ int s_max[kCountThreads / 32];
+  if (!(st->narrow && st->bucket)) return;
+  const int njobs = static_cast<int>(st->njobs);
+  const uint32_t* K = (pass_count(st) & 1) ? k1 : k0;
+  const uint32_t bshift = st->bshift;
+  const uint32_t smask = (1u << bshift) - 1u;
+  const int nw = bshift >= 5 ? 1 << (bshift - 5) : 1;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  for (int j = blockIdx.x; j < njobs; j += gridDim.x) {
+    const uint32_t a = bjob[j], m = bjob[kBucketSlots + j];
+    for (int w = t; w < nw; w += kCountThreads) bits[w] = 0;
+    __syncthreads();
+    for (uint32_t e0 = t; e0 < m; e0 += 4 * kCountThreads) {
+      uint32_t k16[4];  // four loads in flight, then their atomics
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const uint32_t e = e0 + uint32_t(q) * kCountThreads;
+        k16[q] = e < m ? (__ldcs(K + a + e) & smask) : kFull;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (k16[q] != kFull) atomicOr(&bits[k16[q] >> 5], 1u << (k16[q] & 31u));
+    }
+    __syncthreads();
+    uint32_t c = 0;
+    int last = -1;  // largest occupied low key
+    for (int w = t; w < nw; w += kCountThreads) {
+      const uint32_t b = bits[w];
+      c += __popc(b);
+      if (b) last = w * 32 + 31 - __clz(static_cast<int>(b));
+    }
+#pragma unroll
+    for (int off = 16; off; off >>= 1) {
+      c += __shfl_xor_sync(kFull, c, off);
+      last = max(last, __shfl_xor_sync(kFull, last, off));
+    }
+    if (lane == 0) {
+      s_sum[warp] = c;
+      s_max[warp] = last;
+    }
+    __syncthreads();
+    if (t == 0) {
+      uint32_t v = 0;
+      int l = -1;
+      for (int w = 0; w < kCountThreads / 32; ++w) {
+        v += s_sum[w];
+        l = max(l, s_max[w]);
+      }
+      vox[j] = v;
+      bjob[2 * size_t(kBucketSlots) + j] = ((K[a] >> bshift) << bshift) | uint32_t(l);
+    }
+    __syncthreads();
+  }
+}
+
+// One block: the jobs' voxel counts become their first rows (exclusive scan in place),
+// 16 consecutive counts per thread per round.
+__global__ __launch_bounds__(1024) void bucket_vscan_kernel(const State* st, uint32_t* vox) {
+  __shared__ uint32_t tmp[32];
+  if (!(st->narrow && st->bucket)) return;
+  constexpr int kPer = 16;
+  const int njobs = static_cast<int>(st->njobs);
+  uint32_t carry = 0;
+  for (int base = 0; base < njobs; base += kPer * 1024) {
+    const int i0 = base + kPer * int(threadIdx.x);
+    uint32_t c[kPer], sum = 0;
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      c[q] = i0 + q < njobs ? vox[i0 + q] : 0u;
+      sum += c[q];
+    }
+    uint32_t total;
+    uint32_t run = carry + block_excl_scan(sum, &total, tmp);
+#pragma unroll
+    for (int q = 0; q < kPer; ++q)
+      if (i0 + q < njobs) {
+        vox[i0 + q] = run;
+        run += c[q];
+      }
+    carry += total;
+    __syncthreads();
+  }
+}
+
+// Jobs j = blockIdx.x + k * gridDim.x (no job waits for another: every job's first row is
+// known).  Thread 0 keeps the next two descriptors in flight: the one after next is loaded
+// while a job runs, the next one's rows start their way into L2 as that job starts.
 __global__ __launch_bounds__(kBmThreads, VG_BM_MINB) void bucket_local_kernel(
     State* st, const FrameState* __restrict__ fs, int nframes, uint32_t* k0, uint64_t* p0,
-    uint32_t* k1, uint64_t* p1, uint32_t* bstat, uint32_t* bjob, SegOut out, uint32_t spins,
+    uint32_t* k1, uint64_t* p1, const uint32_t* __restrict__ vbase, uint32_t* bjob, SegOut out,
     int* err) {
   extern __shared__ __align__(128) unsigned char bm_smem[];
   BmSmem& sm = *reinterpret_cast<BmSmem*>(bm_smem);
   if (!(st->narrow && st->bucket)) return;
   const int njobs = static_cast<int>(st->njobs);
-  if (njobs == 0) return;
+  const int G = static_cast<int>(gridDim.x);
+  const int j0 = static_cast<int>(blockIdx.x);
+  if (j0 >= njobs) return;
   const bool odd = pass_count(st) & 1;
   const uint32_t* K = odd ? k1 : k0;
   const uint64_t* P = odd ? p1 : p0;
@@ -458,19 +506,28 @@ __global__ __launch_bounds__(kBmThreads, VG_BM_MINB) void bucket_local_kernel(
   RowCtx rc{fs, st->key_shift, nframes, {fs[0].origin[0], fs[0].origin[1], fs[0].origin[2]},
             fs[0].leaf};
   const int t = threadIdx.x;
+  JobDesc d1{}, d2{};  // thread 0: the next job's descriptor, and the one after
   if (t == 0) {
-    take_next(sm, &st->job_ctr, K, P, bjob, njobs, bshift);
-    sm.s_job = sm.s_next;
+    sm.s_desc = load_desc(bjob, vbase, j0, bshift);
+    if (j0 + G < njobs) d1 = load_desc(bjob, vbase, j0 + G, bshift);
   }
   __syncthreads();
-  for (;;) {
-    const int j = sm.s_job;
-    if (j >= njobs) break;
-    const uint32_t a = sm.s_na, m = sm.s_nm, bucket = sm.s_nbucket;
-    __syncthreads();  // (the descriptor slots are refilled by this job's take_next)
-    bucket_job(sm, K, P, a, m, bucket, bshift, j, njobs, bstat, bjob, &st->job_ctr, rc, out,
-               spins, err);
-    if (t == 0) sm.s_job = sm.s_next;
+  for (int j = j0; j < njobs; j += G) {
+    const JobDesc d = sm.s_desc;
+    __syncthreads();  // (the slot is refilled at the end of this job)
+    if (t == 0) {
+      if (j + G < njobs) {
+        prefetch_range(K + d1.a, size_t(d1.m) * sizeof(uint32_t));
+        prefetch_range(P + d1.a, size_t(d1.m) * sizeof(uint64_t));
+      }
+      if (j + 2 * G < njobs) d2 = load_desc(bjob, vbase, j + 2 * G, bshift);
+    }
+    bucket_job(sm, K, P, d.a, d.m, d.bucket, bshift, d.vbase, d.prev, j + 1 == njobs, rc, out,
+               err);
+    if (t == 0) {
+      sm.s_desc = d1;
+      d1 = d2;
+    }
     __syncthreads();
   }
 }
@@ -480,18 +537,25 @@ __global__ __launch_bounds__(kBmThreads, VG_BM_MINB) void bucket_local_kernel(
 void warm_bucket_config() {
   persistent_grid(reinterpret_cast<const void*>(bucket_local_kernel), kBmThreads, sizeof(BmSmem),
                   1);
+  persistent_grid(reinterpret_cast<const void*>(bucket_count_kernel), kCountThreads, 0, 1);
 }
 
 cudaError_t launch_bucket_tail(State* st, const FrameState* fs, int nframes,
                                const NarrowBuffers& nb, const uint32_t* bcount, uint32_t* bstat,
                                uint32_t* bjob, int64_t n_max, const SegOut& out,
                                uint32_t spin_limit, int* err, cudaStream_t stream) {
+  (void)spin_limit;  // no job of the bucket tail waits for another
   if (n_max == 0) return cudaSuccess;
   bucket_scan_kernel<<<1, 1024, 0, stream>>>(st, bcount, bjob);
+  // bstat holds the jobs' voxel counts, then (scanned in place) their first rows
+  const int cgrid = persistent_grid(reinterpret_cast<const void*>(bucket_count_kernel),
+                                    kCountThreads, 0, kBucketSlots);
+  bucket_count_kernel<<<cgrid, kCountThreads, 0, stream>>>(st, nb.k0, nb.k1, bstat, bjob);
+  bucket_vscan_kernel<<<1, 1024, 0, stream>>>(st, bstat);
   const int grid = persistent_grid(reinterpret_cast<const void*>(bucket_local_kernel),
                                    kBmThreads, sizeof(BmSmem), kBucketSlots);
   bucket_local_kernel<<<grid, kBmThreads, sizeof(BmSmem), stream>>>(
-      st, fs, nframes, nb.k0, nb.p0, nb.k1, nb.p1, bstat, bjob, out, spin_limit, err);
+      st, fs, nframes, nb.k0, nb.p0, nb.k1, nb.p1, bstat, bjob, out, err);
   return cudaGetLastError();
 }
 
