@@ -73,9 +73,9 @@ typedef enum {
 #define VG_METHOD_HASH 32    /* hash-table accumulation + radix sort of the voxels     */
 #define VG_METHOD_MASK 48
 #define VG_SORT_BUCKETS 2    /* SORT, narrow layout: only the top key digits in global
-                                radix passes, every bucket of the rest sorted and reduced
-                                in one block's shared memory (same rows; by default every
-                                digit takes a global pass)                               */
+                                radix passes, every bucket of the rest reduced in one
+                                block's shared memory through a bitmap of its keys (same
+                                rows; by default every digit takes a global pass)        */
 #define VG_USE_GRAPH 64      /* vg_downsample_batch: capture / replay a CUDA graph      */
 #define VG_GRID_SHIFT 8      /* vg_downsample_frames: blocks per SM of the streaming    */
 #define VG_GRID_MASK (0xff << VG_GRID_SHIFT) /* kernels (0 = default 8)                */

@@ -143,13 +143,12 @@ __device__ __forceinline__ void write_row(const RowCtx& rc, const SegOut& out, u
 __global__ __launch_bounds__(1024) void bucket_scan_kernel(State* st, const uint32_t* __restrict__ bcount,
                                                            uint32_t* __restrict__ bjob) {
   __shared__ uint32_t tmp[32];
-  __shared__ uint32_t smax[32];
   if (!(st->narrow && st->bucket)) return;
   constexpr int kPer = 16;
   const int t = threadIdx.x;
   uint32_t* job_start = bjob;
   uint32_t* job_count = bjob + kBucketSlots;
-  uint32_t base_e = 0, base_j = 0, mx = 0;
+  uint32_t base_e = 0, base_j = 0;
   for (int r0 = 0; r0 < kBucketSlots; r0 += kPer * 1024) {
     const uint4* c4 = reinterpret_cast<const uint4*>(bcount + r0 + kPer * t);
     uint32_t c[kPer];
@@ -166,7 +165,6 @@ __global__ __launch_bounds__(1024) void bucket_scan_kernel(State* st, const uint
     for (int q = 0; q < kPer; ++q) {
       sum += c[q];
       nz += c[q] != 0;
-      mx = max(mx, c[q]);
     }
     uint32_t tot_e, tot_j;
     uint32_t run_e = base_e + block_excl_scan(sum, &tot_e, tmp);
@@ -184,18 +182,9 @@ __global__ __launch_bounds__(1024) void bucket_scan_kernel(State* st, const uint
     base_j += tot_j;
     __syncthreads();
   }
-#pragma unroll
-  for (int off = 16; off; off >>= 1) mx = max(mx, __shfl_xor_sync(kFull, mx, off));
-  if ((t & 31) == 0) smax[t >> 5] = mx;
-  __syncthreads();
-  if (t == 0) {
-    uint32_t m = 0;
-    for (int w = 0; w < 32; ++w) m = max(m, smax[w]);
-    // the counts cover exactly the valid points, unless the call already failed before
-    // the keys were written (bad frame offsets): then there is nothing to reduce
-    st->njobs = base_e == st->nitems ? base_j : 0u;
-    st->bmax = m;
-  }
+  // the counts cover exactly the valid points, unless the call already failed before the
+  // keys were written (bad frame offsets): then there is nothing to reduce
+  if (t == 0) st->njobs = base_e == st->nitems ? base_j : 0u;
 }
 
 __device__ __forceinline__ JobDesc load_desc(const uint32_t* bjob, const uint32_t* vbase, int j,

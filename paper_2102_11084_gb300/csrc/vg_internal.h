@@ -35,16 +35,12 @@ constexpr int kSortItems = VG_SORT_ITEMS;
 constexpr int kSortTile = kSortThreads * kSortItems;
 constexpr int kSortMinBlocks = VG_SORT_MINB;
 
-// Bucket tail of the narrow layout: the radix passes sort only the top L <= 16 key bits
-// (the bucket, key >> bshift); one block then sorts each bucket by its low bshift <= 16
-// bits in shared memory and reduces it.  512 threads x 16 items: buckets of up to 8192
-// points stay on chip, larger ones take a chunked path through global scratch.
+// Bucket tail of the narrow layout (opt-in): the radix passes sort only the top L <= 16
+// key bits (the bucket, key >> bshift); every bucket is then reduced in one block's
+// shared memory through an occupancy bitmap of its low bshift <= 16 bits (vg_bucket.cu).
 constexpr int kBucketMaxBits = 16;
 constexpr int kBucketSlots = 1 << kBucketMaxBits;
-constexpr int kLocalThreads = 512;
-constexpr int kLocalItems = 16;
-constexpr int kLocalCap = kLocalThreads * kLocalItems;
-constexpr int kLocalTarget = 4096;  // average points per bucket the bucket width aims at
+constexpr int kBucketTarget = 4096;  // average points per bucket the bucket width aims at
 
 // Segmented reduction geometry (256 threads x 4 sorted entries per tile).
 constexpr int kRedThreads = 256;
@@ -103,12 +99,8 @@ struct alignas(256) State {
   uint32_t narrow;            // 1: 32-bit sort keys + packed-offset payload (no gather)
   int32_t error;              // internal error word when the caller passes none
   uint32_t bucket;            // 1: narrow layout with the bucket tail (top passes only)
-  uint32_t bshift;            // bucket = key >> bshift (bits sorted on chip)
+  uint32_t bshift;            // bucket = key >> bshift (bits reduced on chip)
   uint32_t njobs;             // non-empty buckets (bucket tail)
-  uint32_t job_ctr;           // ticket counter of the bucket tail
-  uint32_t bmax;              // largest bucket (points)
-  uint32_t nbig;              // buckets larger than one block (sorted by a pre-pass)
-  uint32_t big_ctr;           // ticket counter of that pre-pass
   uint32_t tile_ctr[kMaxPasses + 8];
   uint32_t hist[kMaxPasses][kRadix];
 };

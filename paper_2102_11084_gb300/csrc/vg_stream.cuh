@@ -143,13 +143,13 @@ __device__ __forceinline__ uint32_t frame_prologue(const FramesArg& fr, bool hav
   const bool nar = fr.allow_narrow && have_extent && total_bits <= 32 && key_bound < 0xffffffffull;
   if (narrow) *narrow = nar;
   // Bucket tail: the radix passes sort the top L bits of the key, L a whole number of
-  // digits aimed at kLocalTarget points per bucket, but at most kBucketMaxBits and enough
-  // that the low kb - L bits left to the on-chip sort are at most 16.
+  // digits aimed at kBucketTarget points per bucket, but at most kBucketMaxBits and enough
+  // that the low kb - L bits left to the on-chip reduction are at most 16.
   const bool bmode = nar && fr.bucket_tail;
   uint32_t bs = 0;
   if (bmode) {
     const uint32_t kb = key_bound ? 64u - __clzll(static_cast<long long>(key_bound)) : 0u;
-    const int64_t q = (fr.n + kLocalTarget - 1) / kLocalTarget;
+    const int64_t q = (fr.n + kBucketTarget - 1) / kBucketTarget;
     uint32_t lw = q > 1 ? 64u - __clzll(static_cast<long long>(q - 1)) : 0u;
     lw = min((lw + kRadixBits - 1) / kRadixBits * kRadixBits, uint32_t(kBucketMaxBits));
     const uint32_t lo = kb > 16u ? kb - 16u : 0u;

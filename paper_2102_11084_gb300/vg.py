@@ -29,8 +29,8 @@ SORT_BUCKETS = 2
 USE_GRAPH = 64
 GRID_SHIFT = 8
 # "sort": radix sort of the points, every key digit in a global pass; "sort_bucket": the
-# narrow layout sorts only the top digits globally and every bucket of the rest in one
-# block's shared memory; "hash": hash-table accumulation.  All give identical rows.
+# narrow layout sorts only the top digits globally and reduces every bucket of the rest in
+# one block's shared memory; "hash": hash-table accumulation.  All give identical rows.
 _METHODS = {"auto": METHOD_AUTO, "sort": METHOD_SORT,
             "sort_bucket": METHOD_SORT | SORT_BUCKETS, "hash": METHOD_HASH}
 MAX_POINTS = (1 << 30) - 1
