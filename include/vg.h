@@ -34,6 +34,11 @@
  *     on the device (index out of range, output capacity, chained-scan timeout) are
  *     written to *out_error (device int32, first error wins, 0 = none) and are visible
  *     once the stream has completed; the outputs are then unspecified.
+ *   * The radix passes and reductions are persistent kernels sized to fill the GPU, and a
+ *     tile may wait (bounded) on tiles other blocks of its grid hold.  Two large calls
+ *     running at the same time on different streams share the SMs and slow each other
+ *     down several times over: order such calls (an event between them); their copies
+ *     may still overlap.
  *   * No C++ exception crosses this interface.
  */
 #ifndef VG_H_
