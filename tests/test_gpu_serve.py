@@ -65,11 +65,11 @@ def test_failed_batch_fails_its_requests_and_server_keeps_serving(monkeypatch):
     real_launch = serve._Slot.launch
     state = {"failed": False}
 
-    def flaky_launch(self, batch):
+    def flaky_launch(self, batch, *args, **kwargs):
         if not state["failed"]:
             state["failed"] = True
             raise vg.VGError(vg.Status.CUDA, "injected launch failure")
-        return real_launch(self, batch)
+        return real_launch(self, batch, *args, **kwargs)
 
     monkeypatch.setattr(serve._Slot, "launch", flaky_launch)
     frame = synth.rgbd_frame(160, 120, seed=31)
