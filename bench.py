@@ -32,7 +32,6 @@ if ROOT not in sys.path:
 N_POINTS = 50_000_000
 LEAF = 0.02
 WORKLOAD = "fused map cloud, 50M xyz f32 points, 40x40x10 m, leaf 0.02 m, origin = cloud min"
-ORACLE_SAMPLE = 1_000_000     # cpu_baseline: first 1M points of the same cloud
 REFERENCE_SAMPLE = 250_000    # --impl reference: points per step
 
 
@@ -44,9 +43,9 @@ def parse():
     p.add_argument("--impl", default="vg", choices=["vg", "reference"])
     p.add_argument("--n", type=int, default=N_POINTS)
     p.add_argument("--leaf", type=float, default=LEAF)
-    p.add_argument("--method", default="sort", choices=["sort", "sort_bucket"],
-                   help="grouping of the timed step: the radix sort (default) or its opt-in "
-                        "bucket tail")
+    p.add_argument("--method", default="sort", choices=["sort", "sort_lsd", "hash"],
+                   help="grouping of the timed step: the default sort (bucket grouping for "
+                        "32-bit keys), the global LSD radix sort, or the hash path")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extra", action="store_true",
                    help="skip the other configurations (single frame, batch, pyramid, "
@@ -161,8 +160,8 @@ class ClockSampler:
 
 
 # the sources of the kernels the bench step launches (their traffic is profiled)
-STEP_KERNEL_SOURCES = ("vg_device.cuh", "vg_internal.h", "vg_keys.cu", "vg_reduce.cu",
-                       "vg_sort.cu", "vg_stream.cuh")
+STEP_KERNEL_SOURCES = ("vg_device.cuh", "vg_internal.h", "vg_keys.cu", "vg_msd.cu",
+                       "vg_reduce.cu", "vg_sort.cu", "vg_stream.cuh")
 
 
 def kernel_source_hash():
@@ -174,8 +173,9 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kernel: str, units: float):
-    """DRAM bytes per launch from the committed ncu summary, if it matches the source."""
+def profiled_traffic(units: dict):
+    """DRAM bytes of one step from the committed ncu summary (per kernel: bytes per unit x
+    the units of this run), if it was taken on the current sources; else None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
@@ -184,10 +184,10 @@ def profiled_traffic(kernel: str, units: float):
         return None
     if d.get("source_hash") != kernel_source_hash():
         return None
-    k = d.get("kernels", {}).get(kernel)
-    if not k:
-        return None
-    return float(k["bytes_per_unit"]) * units
+    total = 0.0
+    for name, k in d.get("kernels", {}).items():
+        total += float(k["bytes_per_unit"]) * float(units[k["unit"]]) * float(k.get("launches", 1))
+    return total
 
 
 # --------------------------------------------------------------------------------------
@@ -207,7 +207,7 @@ def _time_ms(fn, reps, warmup=3, stream=None):
     return a.elapsed_time(b) / reps
 
 
-def extra_measurements(args, dev):
+def extra_measurements(args, dev, peak):
     """The other configurations of the workload set, each timed on the device."""
     import torch
     from paper_2102_11084_gb300 import serve, synth, vg
@@ -219,11 +219,13 @@ def extra_measurements(args, dev):
     x = torch.from_numpy(frame).to(dev)
     n = x.shape[0]
     r = {}
-    for m in ("sort", "hash"):
+    for m in ("sort", "sort_lsd", "hash"):
         buf = vg.alloc_buffers(n, dev, flags=vg.method_flag(m))
         ms = _time_ms(lambda: vg.downsample_into(x, 0.05, buf, origin_from_min=True, method=m), 200)
-        r[m] = {"ms": ms, "points_per_s": n / (ms / 1e3)}
-    r["voxels"] = int(buf.num_voxels.item())
+        v = int(buf.num_voxels.item())
+        r[m] = {"ms": ms, "points_per_s": n / (ms / 1e3),
+                "roofline_frac": (12.0 * n + 16.0 * v) / (ms / 1e3) / 1e9 / peak}
+    r["voxels"] = v
     out["rgbd_640x480_leaf0.05"] = r
 
     # 64 frames of uneven size: 64 plain calls vs one batched call (plan, tuned, graph)
@@ -416,16 +418,69 @@ def run_reference(args, rank, world):
     }), flush=True)
 
 
-def cpu_baseline(xyz, leaf):
+ORACLE_CLOUD_SNIPPET = (
+    "import sys, time, numpy as np\n"
+    "sys.path.insert(0, sys.argv[1])\n"
+    "import oracle\n"
+    "x = np.load(sys.argv[2], mmap_mode='r')\n"
+    "x = np.ascontiguousarray(x)\n"
+    "t0 = time.perf_counter()\n"
+    "oracle.downsample(x, float(sys.argv[3]))\n"
+    "print(time.perf_counter() - t0)\n")
+
+
+class OracleTimer:
+    """The single-threaded oracle timed on the whole workload cloud, once, in a separate
+    process (fork + exec, started before this process's timed GPU work and collected at
+    the end), so the CPU run overlaps the GPU measurements."""
+
+    def __init__(self, xyz, leaf):
+        import tempfile
+        self.tmp = tempfile.NamedTemporaryFile(suffix=".npy", delete=False)
+        self.tmp.close()
+        np.save(self.tmp.name, xyz)
+        self.n = xyz.shape[0]
+        self.proc = subprocess.Popen([sys.executable, "-c", ORACLE_CLOUD_SNIPPET, ROOT,
+                                      self.tmp.name, repr(float(leaf))],
+                                     stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True)
+
+    def result(self):
+        try:
+            out, errs = self.proc.communicate(timeout=1800)
+            dt = float(out.strip().splitlines()[-1])
+        except (subprocess.TimeoutExpired, ValueError, IndexError):
+            self.proc.kill()
+            return None
+        finally:
+            os.unlink(self.tmp.name)
+        return dt
+
+
+def cpu_baseline(oracle_timer, frame_xyz):
+    """cpu_baseline: the oracle (std::map, FP64, one thread) on the whole workload cloud,
+    once, plus the 640x480 frame at leaf 0.05 m with 10 repetitions."""
     import oracle
-    sample = np.ascontiguousarray(xyz[:ORACLE_SAMPLE])
+    dt = oracle_timer.result() if oracle_timer else None
+    reps = 10
+    oracle.downsample(frame_xyz, 0.05)
     t0 = time.perf_counter()
-    oracle.downsample(sample, leaf)
-    dt = time.perf_counter() - t0
-    return {"value": ORACLE_SAMPLE / dt, "unit": "points/s", "cores": 1, "kind": "oracle",
-            "sample": f"first {ORACLE_SAMPLE} points of the workload cloud (same leaf, origin = "
-                      f"sample min), single-threaded std::map FP64 oracle, {dt:.1f} s",
-            "host_cores_available": os.cpu_count()}
+    for _ in range(reps):
+        oracle.downsample(frame_xyz, 0.05)
+    dt_frame = (time.perf_counter() - t0) / reps
+    out = {"unit": "points/s", "cores": 1, "kind": "oracle",
+           "host_cores_available": os.cpu_count(),
+           "rgbd_640x480_leaf0.05": {"ms": dt_frame * 1e3,
+                                     "points_per_s": frame_xyz.shape[0] / dt_frame,
+                                     "reps": reps}}
+    if dt is not None:
+        out["value"] = oracle_timer.n / dt
+        out["sample"] = (f"the whole workload cloud ({oracle_timer.n} points, same leaf, "
+                         f"origin = cloud min), once: {dt:.1f} s on one core; single-threaded "
+                         f"std::map FP64 oracle")
+    else:
+        out["value"] = None
+        out["sample"] = "the whole-cloud oracle run did not finish"
+    return out
 
 
 def run_vg(args, rank, world, local):
@@ -444,10 +499,15 @@ def run_vg(args, rank, world, local):
     buf = vg.alloc_buffers(n, dev)
     stream = torch.cuda.current_stream(dev)
 
-    # stage events (profiling hook of the C ABI): one set per timed step
-    # sort path: extent/origin, keys, 8 radix passes (the needed ones do work), the bucket
-    # tail (only with method "sort_bucket"; an empty stage here) and the segmented reduction
-    n_stages = 12
+    # the single-threaded oracle on the whole cloud, in another process while the GPU works
+    oracle_timer = (OracleTimer(xyz_np, args.leaf)
+                    if rank == 0 and not args.no_cpu_baseline else None)
+
+    # stage events (profiling hook of the C ABI): one set per timed step.  Sort path:
+    # extent/origin, keys, the bucket grouping's first partition pass, second partition
+    # pass and bucket kernel, 8 radix passes (the needed ones do work; none with the bucket
+    # grouping), the segmented reduction (returns at once with the bucket grouping)
+    n_stages = 14
     import ctypes
 
     def call():
@@ -493,43 +553,45 @@ def run_vg(args, rank, world, local):
     nvalid = int(np.isfinite(xyz_np).all(axis=1).sum())
 
     # per-stage device times (ms, mean over steps)
-    stage_names = (["origin", "keys"] + [f"sort_pass{p}" for p in range(8)] +
-                   ["bucket_tail", "segreduce"])
+    stage_names = (["origin", "keys", "partition1", "partition2", "bucket"] +
+                   [f"sort_pass{p}" for p in range(8)] + ["segreduce"])
     stage_ms = np.zeros(n_stages)
     for s in ev_sets:
         for i in range(n_stages):
             stage_ms[i] += s[i].elapsed_time(s[i + 1])
     stage_ms /= args.steps
-    # passes that did work (the others return at once, in a few microseconds)
-    passes = max(1, int((stage_ms[2:10] > 0.02).sum()))
+    st_ms = dict(zip(stage_names, (float(v) for v in stage_ms)))
+    bucketed = st_ms["bucket"] > 0.02  # the bucket grouping ran (else the global radix sort)
+    passes = int((stage_ms[5:13] > 0.02).sum())
     narrow = int(buf.keys[V - 1].item()).bit_length() <= 32 if V else True
-    bucket = stage_ms[10] > stage_ms[11]  # the narrow layout's bucket tail ran
-    # algorithmic bytes per launch of each kernel (narrow: 4 B key + 8 B packed offsets;
-    # every output row: 8 B key + 12 B centroid + 4 B count)
+    # algorithmic bytes of each kernel group per launch: narrow entries are a 4 B key and an
+    # 8 B packed offset; every output row is an 8 B key, a 12 B centroid and a 4 B count
     algo = {
         "origin": 12.0 * n,
         "keys": 12.0 * n + 12.0 * n,
+        "partition1": 4.0 * n + 8.0 * nvalid + 12.0 * nvalid,
+        "partition2": 4.0 * nvalid + 24.0 * nvalid,
+        "bucket": 12.0 * nvalid + 24.0 * V,
         "sort_pass": 24.0 * nvalid,
-        "bucket_tail": 12.0 * nvalid + 24.0 * V,
         "segreduce": ((4.0 + 12.0) if narrow else (8.0 + 24.0)) * nvalid + 24.0 * V,
     }
-    sort_ms = stage_ms[2:2 + passes]
-    tail = "bucket_tail" if bucket else "segreduce"
-    kern = {
-        "origin": (stage_ms[0], algo["origin"], 1),
-        "keys": (stage_ms[1], algo["keys"], 1),
-        "sort_pass": (float(sort_ms.mean()), algo["sort_pass"], passes),
-        tail: (float(stage_ms[10] if bucket else stage_ms[11]), algo[tail], 1),
-    }
-    dom = max(kern, key=lambda k: kern[k][0] * kern[k][2])
+    kern = {"origin": (st_ms["origin"], 1), "keys": (st_ms["keys"], 1)}
+    if bucketed:
+        kern.update({"partition1": (st_ms["partition1"], 1),
+                     "partition2": (st_ms["partition2"], 1), "bucket": (st_ms["bucket"], 1)})
+    else:
+        kern.update({"sort_pass": (float(stage_ms[5:5 + max(passes, 1)].mean()), max(passes, 1)),
+                     "segreduce": (st_ms["segreduce"], 1)})
+    dom = max(kern, key=lambda k: kern[k][0] * kern[k][1])
     peaks, peak_src = measured_peaks()
     peak = float(peaks["hbm_gbs"])
-    d_ms, d_bytes, _ = kern[dom]
-    achieved = d_bytes / (d_ms / 1000) / 1e9
-    traffic = profiled_traffic(dom, {"origin": n, "keys": n, "sort_pass": nvalid,
-                                     "bucket_tail": nvalid, "segreduce": nvalid}[dom])
+    d_ms = kern[dom][0]
+    d_gbs = algo[dom] / (d_ms / 1000) / 1e9
+    # the headline roofline: the whole step against the scope's algorithmic bytes, 12 B per
+    # input point (xyz read once) + 16 B per output voxel (centroid + count written)
     path_bytes = 12.0 * n + 16.0 * V
     path_gbs = path_bytes / (ms / 1000) / 1e9
+    traffic = profiled_traffic({"point": n, "valid_point": nvalid, "voxel": V})
 
     # end to end: pinned host cloud in, key/centroid/count rows out, through the C ABI
     keys_h = torch.empty(n, dtype=torch.int64).pin_memory()
@@ -592,24 +654,29 @@ def run_vg(args, rank, world, local):
         if world > 1:
             dist.destroy_process_group()
         return
-    cpu = None if args.no_cpu_baseline else cpu_baseline(xyz_np, args.leaf)
     extra = {}
     if not args.no_extra:
         # the same cloud at leaf 0.1 m
         ms01 = _time_ms(lambda: vg.downsample_into(xyz, 0.1, buf, origin_from_min=True), 10)
-        extra["fused_map_50M_leaf0.1"] = {"ms": ms01, "points_per_s": n / (ms01 / 1e3),
-                                          "voxels": int(buf.num_voxels.item())}
-        # the opt-in bucket tail on the same cloud (top digits global, buckets on chip)
-        msb = _time_ms(lambda: vg.downsample_into(xyz, args.leaf, buf, origin_from_min=True,
-                                                  method="sort_bucket"), 10)
-        extra["fused_map_50M_sort_bucket"] = {"ms": msb, "points_per_s": n / (msb / 1e3),
-                                              "voxels": int(buf.num_voxels.item())}
+        v01 = int(buf.num_voxels.item())
+        extra["fused_map_50M_leaf0.1"] = {
+            "ms": ms01, "points_per_s": n / (ms01 / 1e3), "voxels": v01,
+            "roofline_frac": (12.0 * n + 16.0 * v01) / (ms01 / 1e3) / 1e9 / peak}
+        # the same cloud through the global LSD radix sort and segmented reduction
+        msl = _time_ms(lambda: vg.downsample_into(xyz, args.leaf, buf, origin_from_min=True,
+                                                  method="sort_lsd"), 10)
+        extra["fused_map_50M_sort_lsd"] = {"ms": msl, "points_per_s": n / (msl / 1e3),
+                                           "voxels": int(buf.num_voxels.item())}
         del buf
         torch.cuda.empty_cache()
-        extra.update(extra_measurements(args, dev))
-    # extent, keys, 8 radix passes, count + scan + reduce (+ job scan, large-bucket pre-pass
-    # and bucket kernel with the bucket tail)
-    launches_per_step = 1 + 1 + 8 + 3 + (3 if args.method == "sort_bucket" else 0)
+        extra.update(extra_measurements(args, dev, peak))
+    from paper_2102_11084_gb300 import synth as _synth
+    cpu = (None if args.no_cpu_baseline else
+           cpu_baseline(oracle_timer, _synth.rgbd_frame(640, 480, seed=0)))
+    # our kernels per step: extent, keys, first-digit scan, partition, second-digit
+    # histogram, bucket scan, partition, bucket kernel, 8 radix passes, count + scan + reduce
+    # (the kernels of the grouping not chosen return at once)
+    launches_per_step = 1 + 1 + 6 + 8 + 3
     out = {
         "metric": "points/s", "value": total_points / (ms / 1000), "unit": "points/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -619,18 +686,21 @@ def run_vg(args, rank, world, local):
                    "leaf_m": args.leaf, "method": args.method,
                    "parallelism": f"replicas x{world}",
                    "l2": "inputs (600 MB) larger than L2 (129 MB); no flush"},
-        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
-                     "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+        "roofline": {"bound": "hbm", "kernel": "whole step (all kernels of one call)",
+                     "achieved": path_gbs, "peak": peak, "unit": "GB/s",
+                     "frac": path_gbs / peak, "traffic": traffic,
                      "peak_source": f"hbm_gbs of MEASURED_PEAKS.json ({peak_src})",
-                     "algorithmic_bytes_per_launch": d_bytes, "ms_per_launch": d_ms},
-        "roofline_path": {"bytes_per_step": path_bytes, "achieved": path_gbs, "peak": peak,
-                          "unit": "GB/s", "frac": path_gbs / peak,
-                          "definition": "12 B per input point + 16 B per output voxel"},
-        "stages_ms": {nm: float(v) for nm, v in zip(stage_names, stage_ms)},
+                     "algorithmic_bytes_per_launch": path_bytes, "ms_per_launch": ms,
+                     "definition": "12 B per input point (xyz read once) + 16 B per output "
+                                   "voxel (centroid + count written)"},
+        "roofline_kernel": {"kernel": dom, "achieved": d_gbs, "peak": peak, "unit": "GB/s",
+                            "frac": d_gbs / peak, "algorithmic_bytes_per_launch": algo[dom],
+                            "ms_per_launch": d_ms, "launches_per_step": kern[dom][1]},
+        "stages_ms": st_ms,
         "sort_passes": passes,
         "layout": "narrow (32-bit keys, packed offsets)" if narrow else "wide (64-bit keys, index)",
-        "grouping": ("top key digits in global radix passes, every bucket of the low digits "
-                     "sorted and reduced in one block's shared memory") if bucket else
+        "grouping": ("partition passes over the top key bits, every bucket of the low bits "
+                     "reduced in one block's shared memory") if bucketed else
                     "every key digit in global radix passes, segmented reduction",
         "cpu_baseline": cpu,
         "e2e": {"value": total_points / e2e_s, "unit": "points/s", "h2d_bytes_per_step": 12 * n,

@@ -74,13 +74,20 @@ typedef enum {
 #define VG_ORIGIN_FROM_MIN 1 /* compute origin = per-axis min of the valid points and
                                 write it to `origin` (else `origin` is read)            */
 #define VG_METHOD_AUTO 0     /* the library's default grouping method (currently SORT)  */
-#define VG_METHOD_SORT 16    /* radix sort of every point + segmented reduction        */
+#define VG_METHOD_SORT 16    /* sort the points by key and reduce each run of equal keys.
+                                32-bit keys (no point_to_voxel, no attributes, extents
+                                bound the keys): the top <= 16 key bits are split by one
+                                or two most-significant-digit partition passes and every
+                                bucket of the low bits is reduced in one block's shared
+                                memory; otherwise a global LSD radix sort of every digit
+                                and a segmented reduction                                 */
 #define VG_METHOD_HASH 32    /* hash-table accumulation + radix sort of the voxels     */
 #define VG_METHOD_MASK 48
-#define VG_SORT_BUCKETS 2    /* SORT, narrow layout: only the top key digits in global
-                                radix passes, every bucket of the rest reduced in one
-                                block's shared memory through a bitmap of its keys (same
-                                rows; by default every digit takes a global pass)        */
+#define VG_SORT_BUCKETS 2    /* accepted for compatibility; changes nothing (32-bit keys
+                                are grouped by buckets by default)                       */
+#define VG_SORT_LSD 4        /* SORT with 32-bit keys: every key digit in a global LSD
+                                radix pass, then the segmented reduction, instead of the
+                                bucket grouping (same rows; for comparison)              */
 #define VG_USE_GRAPH 64      /* vg_downsample_batch: capture / replay a CUDA graph      */
 #define VG_GRID_SHIFT 8      /* vg_downsample_frames: blocks per SM of the streaming    */
 #define VG_GRID_MASK (0xff << VG_GRID_SHIFT) /* kernels (0 = default 8)                */
@@ -377,6 +384,11 @@ VG_API vg_status vg_downsample_backward(const float* grad_centroids, const uint3
  * VG_NOALLOC_MAX_POINTS points) that every GPU loading the library keeps until the
  * process exits.  The call allocates nothing.
  *   * n > VG_NOALLOC_MAX_POINTS is rejected with VG_ERR_INVALID_ARG before any launch.
+ *   * Only the sort method runs here (VG_METHOD_AUTO, VG_METHOD_SORT, with or without
+ *     VG_SORT_BUCKETS): the array holds the sort path's workspace, so VG_METHOD_HASH is
+ *     rejected with VG_ERR_INVALID_ARG before any launch.
+ *   * The device address of the array is cached per device; cudaDeviceReset invalidates
+ *     it, so do not call this entry point after resetting the device.
  *   * The first call on a device looks up the array's device address (once per device,
  *     with that device current); make that first call before any stream capture.
  *   * All calls on a device share the one array; it keeps the last call's contents and
@@ -396,9 +408,13 @@ VG_API size_t vg_downsample_noalloc_scratch_bytes(void);
  * events[0] on its stream before its first kernel and events[k] after stage k, for
  * k = 1 .. min(max_events - 1, number of stages); NULL turns it off.  The events are
  * cudaEvent_t handles owned by the caller.  Stages of the sort path, in order: extent /
- * origin (recorded even when skipped), keys, 8 radix passes (those beyond the key's
- * significant digits return at once), segmented reduction (count, scan, reduce); of the
- * hash path: origin, insert, compaction, 8 radix passes, finalize, point-to-voxel.
+ * origin (recorded even when skipped), keys, then the bucket grouping's first partition
+ * pass (with the scan of its digit counts), second partition pass (with its digit
+ * histogram and bucket scan) and bucket kernel (all three return at once, or are not
+ * launched, when the call takes the global radix sort), then 8 radix passes (those
+ * beyond the key's significant digits, and all of them with the bucket grouping, return
+ * at once) and the segmented reduction (count, scan, reduce); of the hash path: origin,
+ * insert, compaction, 8 radix passes, finalize, point-to-voxel.
  * Returns the largest number of events a call records (20). */
 VG_API int vg_set_stage_events(void** events, int max_events);
 

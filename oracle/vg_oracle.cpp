@@ -245,10 +245,6 @@ void oracle_backward(const double* grad_centroids, const uint64_t* counts,
   }
 }
 
-// The loss whose gradient oracle_backward propagates, as a function of FP64 point
-// coordinates with the voxel membership held fixed (point_to_voxel from an
-// oracle_downsample of the FP32 cloud):  L = (1/(3V)) sum_v |c_v - t_v|^2 where
-// c_v is the mean of the member points.  Used for central finite differences.
 // R13: mean attributes of voxels 0..V-1 from each point's voxel row (p2v, -1 = none).
 void oracle_voxel_attrs(const int32_t* p2v, int64_t n, const uint8_t* attrs, int channels,
                         int64_t num_voxels, float* out) {
@@ -368,6 +364,10 @@ void oracle_pose(const float* xyz, int64_t n, const float* pose, const float* zl
   }
 }
 
+// The loss whose gradient oracle_backward propagates, as a function of FP64 point
+// coordinates with the voxel membership held fixed (point_to_voxel from an
+// oracle_downsample of the FP32 cloud):  L = (1/(3V)) sum_v |c_v - t_v|^2 where
+// c_v is the mean of the member points.  Used for central finite differences.
 double oracle_centroid_loss(const double* xyz, int64_t n, const int32_t* point_to_voxel,
                             int64_t v, const double* targets) {
   std::vector<double> sums(3 * v, 0.0);

@@ -58,7 +58,7 @@ void warm_launch_config() {
   warm_sort_config();
   warm_reduce_config();
   warm_filter_config();
-  warm_bucket_config();
+  warm_msd_config();
 }
 
 int persistent_grid(const void* kernel, int threads, size_t dyn_smem, int64_t work_tiles) {
@@ -147,11 +147,12 @@ vg_status run_frames(const float* xyz, const FramesArg& fr, bool from_min, const
   int stage = 0;
 
   if (method == VG_METHOD_SORT) {
-    // The narrow layout (no gather) needs the extents up front and no point_to_voxel.
+    // The narrow layout (no gather) needs the extents up front and no point_to_voxel; it
+    // is grouped by buckets unless the caller asks for every digit in global passes.
     FramesArg frn = fr;
     frn.allow_narrow = out.p2v == nullptr && out.attrs_in == nullptr;
-    frn.bucket_tail = (flags & VG_SORT_BUCKETS) != 0;
-    const bool btail = frn.allow_narrow && frn.bucket_tail;
+    frn.lsd_narrow = (flags & VG_SORT_LSD) != 0;
+    const bool maybe_msd = frn.allow_narrow && !frn.lsd_narrow;
     const bool have_extent = from_min || F > 1 || frn.allow_narrow;
     const SortLayout L = sort_layout(n, F);
     State* st = reinterpret_cast<State*>(ws + L.state);
@@ -163,9 +164,6 @@ vg_status run_frames(const float* xyz, const FramesArg& fr, bool from_min, const
     uint32_t* lb_a = reinterpret_cast<uint32_t*>(ws + L.lb_a);
     uint32_t* lb_b = reinterpret_cast<uint32_t*>(ws + L.lb_b);
     TileRec* recs = reinterpret_cast<TileRec*>(ws + L.seg_lb);
-    uint32_t* bcount = reinterpret_cast<uint32_t*>(ws + L.bcount);
-    uint32_t* bstat = reinterpret_cast<uint32_t*>(ws + L.bstat);
-    uint32_t* bjob = reinterpret_cast<uint32_t*>(ws + L.bjob);
     const int64_t nn = n < 1 ? 1 : n;
     uint32_t* k32_0 = reinterpret_cast<uint32_t*>(ws + L.keys0);
     uint32_t* k32_1 = k32_0 + align_up(size_t(nn), 4);  // 16-byte aligned, like k32_0
@@ -174,8 +172,8 @@ vg_status run_frames(const float* xyz, const FramesArg& fr, bool from_min, const
     int* err = out_error ? reinterpret_cast<int*>(out_error) : &st->error;
 
     cudaError_t e = cudaMemsetAsync(ws, 0, L.zero_bytes, stream);
-    if (e == cudaSuccess && btail)  // bucket counts and job status, adjacent
-      e = cudaMemsetAsync(ws + L.bcount, 0, L.bjob - L.bcount, stream);
+    if (e == cudaSuccess && maybe_msd)  // points per bucket
+      e = cudaMemsetAsync(ws + L.mhist, 0, L.mvcnt - L.mhist, stream);
     if (e == cudaSuccess && out_error) e = cudaMemsetAsync(out_error, 0, sizeof(int32_t), stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(out.num_voxels, 0, sizeof(int64_t), stream);
     if (e == cudaSuccess && out.frame_offsets)
@@ -188,19 +186,21 @@ vg_status run_frames(const float* xyz, const FramesArg& fr, bool from_min, const
     if (e == cudaSuccess)
       e = launch_keys_any(xyz, frn, have_extent, st, fs, keys0, k32_0, pay_0, err, stream);
     mark(stage++, stream);
-    // The layout is chosen on the device (it depends on the largest key); every kernel
-    // below reads it and runs that layout's code.
+    // The layout and the grouping are chosen on the device (they depend on the largest
+    // key); the kernels of the ones not chosen return at once.
     const NarrowBuffers nb{k32_0, pay_0, k32_1, pay_1};
+    if (maybe_msd) {
+      if (e == cudaSuccess)
+        e = launch_msd(st, fs, F, nb, ws, L, n, out, spins, err, stream, stage, mark);
+    } else {
+      for (int k = 0; k < 3; ++k) mark(stage + k, stream);
+    }
+    stage += 3;
     for (int p = 0; p < kMaxPasses && e == cudaSuccess; ++p) {
       e = launch_sort_pass(st, keys0, idx0, keys1, idx1, lb_a, lb_b, n, p, false, spins, err,
-                           stream, &nb, btail ? bcount : nullptr);
+                           stream, &nb);
       mark(stage++, stream);
     }
-    // a narrow layout with the bucket tail reduces here; the segmented reduction below then
-    // returns at once (and the other way round)
-    if (e == cudaSuccess && btail)
-      e = launch_bucket_tail(st, fs, F, nb, bcount, bstat, bjob, n, out, spins, err, stream);
-    mark(stage++, stream);
     if (e == cudaSuccess)
       e = launch_segreduce(st, fs, F, keys0, idx0, keys1, idx1, xyz, recs, n, out, err, stream,
                            &nb, frn.poses);
@@ -336,7 +336,7 @@ vg_status vg_downsample(const float* xyz, int64_t n, float* origin, float leaf,
                         int32_t* out_error, void* workspace, size_t workspace_bytes, int flags,
                         vg_stream_t stream) {
   if (!(leaf > 0.0f) || !std::isfinite(leaf)) return VG_ERR_INVALID_ARG;
-  if ((flags & ~(VG_ORIGIN_FROM_MIN | VG_METHOD_MASK | VG_SORT_BUCKETS)) != 0)
+  if ((flags & ~(VG_ORIGIN_FROM_MIN | VG_METHOD_MASK | VG_SORT_BUCKETS | VG_SORT_LSD)) != 0)
     return VG_ERR_INVALID_ARG;
   if ((flags & VG_METHOD_MASK) == VG_METHOD_MASK) return VG_ERR_INVALID_ARG;
   if (!origin || !out_num_voxels) return VG_ERR_INVALID_ARG;
@@ -404,7 +404,8 @@ vg_status vg_downsample_frames_ex(const float* xyz, int64_t n_total,
     if (!aligned(extras->out_attrs, 4)) return VG_ERR_ALIGN;
   }
   const bool filtered = extras && extras->min_count > 1;
-  if ((flags & ~(VG_ORIGIN_FROM_MIN | VG_METHOD_MASK | VG_GRID_MASK | VG_SORT_BUCKETS)) != 0)
+  if ((flags & ~(VG_ORIGIN_FROM_MIN | VG_METHOD_MASK | VG_GRID_MASK | VG_SORT_BUCKETS |
+                 VG_SORT_LSD)) != 0)
     return VG_ERR_INVALID_ARG;
   if ((flags & VG_METHOD_MASK) == VG_METHOD_MASK) return VG_ERR_INVALID_ARG;
   if (!frame_offsets || !origins || !leaves || !out_frame_offsets) return VG_ERR_INVALID_ARG;
@@ -450,7 +451,8 @@ vg_status vg_pyramid(const float* xyz, int64_t n, float* origin, float leaf, int
   cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
   if (!(leaf > 0.0f) || !std::isfinite(leaf)) return VG_ERR_INVALID_ARG;
   if (levels < 1 || levels > kMaxLevels) return VG_ERR_INVALID_ARG;
-  if ((flags & ~(VG_ORIGIN_FROM_MIN | VG_SORT_BUCKETS)) != 0) return VG_ERR_INVALID_ARG;
+  if ((flags & ~(VG_ORIGIN_FROM_MIN | VG_SORT_BUCKETS | VG_SORT_LSD)) != 0)
+    return VG_ERR_INVALID_ARG;
   if (!origin || !out_level_offsets) return VG_ERR_INVALID_ARG;
   if (!std::isfinite(leaf * float(1u << (levels - 1)))) return VG_ERR_INVALID_ARG;
   vg_status s = check_outputs(n, xyz, out_keys, out_centroids, out_counts, cap_total,
@@ -478,7 +480,7 @@ vg_status vg_pyramid(const float* xyz, int64_t n, float* origin, float leaf, int
   SegOut out{out_keys, out_centroids, out_counts, sums[0], cap_total, out_level_offsets + 1,
              nullptr, out_point_to_voxel};
   s = run_frames(xyz, fr, from_min, out, out_error, workspace, L.total,
-                 VG_METHOD_SORT | (flags & VG_SORT_BUCKETS), stream);
+                 VG_METHOD_SORT | (flags & (VG_SORT_BUCKETS | VG_SORT_LSD)), stream);
   if (s != VG_OK) return s;
   const uint32_t spins = spin_limit();
   for (int k = 1; k < levels && e == cudaSuccess; ++k)

@@ -246,7 +246,13 @@ __device__ __forceinline__ Acc point_acc(uint64_t local, float x, float y, float
 // voxel.  (unit_leaf = leaf except in the pyramid, whose sums keep the level-0 unit.)
 __device__ __forceinline__ void acc_centroid(uint64_t local, const Acc& a, const float o[3],
                                              float leaf, float unit_leaf, float out[3]) {
-  const float scale = __fdiv_rn(unit_leaf, __fmul_rn(__uint2float_rn(a.n), kQuantScale));
+  // For n = 2^k the divisor n * 2^20 = 2^(20+k) is exact and so is the quotient (a normal
+  // number when unit_leaf >= 2^-76 and k <= 30): the same bits as the division, cheaper.
+  float scale;
+  if ((a.n & (a.n - 1u)) == 0u && a.n != 0u && unit_leaf >= 1.3234889800848443e-23f)
+    scale = __fmul_rn(unit_leaf, __int_as_float((127 - 20 - (__ffs(int(a.n)) - 1)) << 23));
+  else
+    scale = __fdiv_rn(unit_leaf, __fmul_rn(__uint2float_rn(a.n), kQuantScale));
 #pragma unroll
   for (int ax = 0; ax < 3; ++ax) {
     const float c = voxel_corner(key_axis(local, ax), o[ax], leaf);
@@ -298,15 +304,9 @@ __device__ __forceinline__ int sort_passes(unsigned long long maxkey) {
 }
 
 // Radix passes a call runs: every significant digit of the largest key (at least one,
-// which also drops the invalid rows), or in the bucket tail only the digits above the
-// bucket shift.
+// which also drops the invalid rows); none when the narrow layout is grouped by buckets.
 __device__ __forceinline__ int pass_count(const State* st) {
-  if (st->narrow && st->bucket) {
-    const uint32_t mk = static_cast<uint32_t>(st->maxkey);
-    const int bits = mk ? 32 - __clz(static_cast<int>(mk)) : 0;
-    const int top = bits > int(st->bshift) ? bits - int(st->bshift) : 0;
-    return max(1, (top + kRadixBits - 1) / kRadixBits);
-  }
+  if (st->narrow && st->msd) return 0;
   return max(1, sort_passes(st->maxkey));
 }
 
@@ -411,7 +411,8 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t pari
 
 // ---- block-wide helpers (256 threads) -------------------------------------------------
 // Exclusive scan of one u32 per thread; *total receives the block sum.  `tmp` holds
-// blockDim/32 words of shared memory.  Contains __syncthreads.
+// blockDim/32 words of shared memory (blockDim <= 1024).  The warp totals are scanned by
+// every warp with shuffles.  Contains __syncthreads.
 __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* total,
                                                     uint32_t* tmp) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -421,17 +422,18 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* total,
     const uint32_t y = __shfl_up_sync(kFullMask, inc, off);
     if (lane >= off) inc += y;
   }
-  __syncthreads();
+  __syncthreads();  // earlier readers of tmp are done
   if (lane == 31) tmp[warp] = inc;
   __syncthreads();
-  uint32_t before = 0, all = 0;
-  for (int w = 0; w < nw; ++w) {
-    const uint32_t x = tmp[w];
-    if (w < warp) before += x;
-    all += x;
+  const uint32_t wt = lane < nw ? tmp[lane] : 0u;
+  uint32_t ws = wt;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const uint32_t y = __shfl_up_sync(kFullMask, ws, off);
+    if (lane >= off) ws += y;
   }
-  *total = all;
-  return before + inc - v;
+  *total = __shfl_sync(kFullMask, ws, 31);
+  return __shfl_sync(kFullMask, ws - wt, warp) + inc - v;
 }
 
 // ---- frame decomposition (chunks of kChunk points inside one frame) -----------------------

@@ -35,12 +35,24 @@ constexpr int kSortItems = VG_SORT_ITEMS;
 constexpr int kSortTile = kSortThreads * kSortItems;
 constexpr int kSortMinBlocks = VG_SORT_MINB;
 
-// Bucket tail of the narrow layout (opt-in): the radix passes sort only the top L <= 16
-// key bits (the bucket, key >> bshift); every bucket is then reduced in one block's
-// shared memory through an occupancy bitmap of its low bshift <= 16 bits (vg_bucket.cu).
-constexpr int kBucketMaxBits = 16;
-constexpr int kBucketSlots = 1 << kBucketMaxBits;
-constexpr int kBucketTarget = 4096;  // average points per bucket the bucket width aims at
+// Bucket grouping of the narrow layout (the default for 32-bit keys, vg_msd.cu): the top
+// key bits (the bucket, key >> lowbits) are split in one or two most-significant-digit
+// partition passes of at most 8 bits each; every bucket's low lowbits <= 16 bits are then
+// reduced on chip.
+constexpr int kMsdMaxLow = 16;                 // largest bucket-local key width
+constexpr int kMsdMaxTop = 16;                 // largest bucket id width (two 8-bit levels)
+constexpr int kMsdBuckets = 1 << kMsdMaxTop;   // bucket ids
+constexpr int kMsdTarget = 2048;               // average points per bucket the split aims at
+constexpr int kPartThreads = 256;              // partition pass: 256 threads x 16 records
+constexpr int kPartItems = 16;
+constexpr int kPartTile = kPartThreads * kPartItems;
+// Entries the bucket kernel stages per job (build-time); larger buckets are cut into
+// windows of at most this many entries by key range.
+#ifndef VG_BK_STAGE
+#define VG_BK_STAGE 3072
+#endif
+constexpr int kBkStage = VG_BK_STAGE;
+constexpr int kJobWords = 8;                   // 32-bit words of one bucket-kernel job
 
 // Segmented reduction geometry (256 threads x 4 sorted entries per tile).
 constexpr int kRedThreads = 256;
@@ -98,9 +110,19 @@ struct alignas(256) State {
   uint32_t nchunks;           // chunks of the frame decomposition
   uint32_t narrow;            // 1: 32-bit sort keys + packed-offset payload (no gather)
   int32_t error;              // internal error word when the caller passes none
-  uint32_t bucket;            // 1: narrow layout with the bucket tail (top passes only)
-  uint32_t bshift;            // bucket = key >> bshift (bits reduced on chip)
-  uint32_t njobs;             // non-empty buckets (bucket tail)
+  uint32_t msd;               // 1: narrow layout grouped by buckets (vg_msd.cu)
+  uint32_t lowbits;           // bucket = key >> lowbits; the low bits are reduced on chip
+  uint32_t levels;            // partition passes over the bucket bits (1 or 2)
+  uint32_t b1, b2;            // digit widths of the two passes (b2 = 0 with one pass)
+  uint32_t njobs2;            // second-pass jobs (chunks of the first pass's digit runs)
+  uint32_t nbjobs;            // non-empty buckets (in key order)
+  uint32_t nmjobs;            // bucket-kernel jobs of whole buckets (runs of small ones)
+  uint32_t nwjobs;            // bucket-kernel jobs of windows of large buckets
+  uint32_t nbig;              // buckets of more than kBkStage entries
+  uint32_t njobs3;            // chunks of large buckets the third partition pass splits
+  uint32_t ctot[64];          // entries of every 1024 consecutive buckets
+  uint32_t nztot[64];         // non-empty buckets of every 1024 consecutive buckets
+  uint32_t vtot[64];          // cells of every 1024 consecutive non-empty buckets
   uint32_t tile_ctr[kMaxPasses + 8];
   uint32_t hist[kMaxPasses][kRadix];
 };
@@ -130,7 +152,8 @@ struct FramesArg {
   const float* poses;      // device [F,12] row-major [R|t] sensor poses, or nullptr
   const float* zlims;      // device [F,2] [z_min, z_max] after the pose, or nullptr
   int merge_frames;        // 1: every frame keys into one voxel space (no frame id)
-  int bucket_tail;         // 1: a narrow layout takes the bucket tail (see kBucketMaxBits)
+  int lsd_narrow;          // 1: a narrow layout sorts every key digit in global radix passes
+                           //    (the segmented reduction follows) instead of by buckets
 };
 
 // A posed call maps every point into the common frame, p' = R p + t, before anything
@@ -150,11 +173,22 @@ constexpr int64_t max_chunks(int64_t n, int frames) { return ceil_div(n, kChunk)
 // (32-bit keys, 64-bit packed offsets) aliases the same bytes: keys32 ping-pong in keys0,
 // payload ping-pong in keys1 and in idx0..idx1.
 struct SortLayout {
-  size_t state, frames, keys0, keys1, idx0, idx1, lb_a, lb_b, seg_lb, bcount, bstat, bjob,
-      total;
+  size_t state, frames, keys0, keys1, idx0, idx1, lb_a, lb_b, seg_lb, mhist, mvcnt, mcur,
+      mjob, mjob2, mjobm, mjobw, mcur3, mjob3, total;
   size_t zero_bytes;  // bytes from `state` that must be zero at call start
-  int64_t sort_tiles, seg_tiles;
+  int64_t sort_tiles, seg_tiles, jobs2, jobsw, big, jobs3;
 };
+
+// Second-pass jobs of the bucket grouping: the first pass's digit runs cut into pieces of
+// at most kPartTile entries.
+constexpr int64_t max_jobs2(int64_t n) { return ceil_div(n, kPartTile) + 256; }
+// Window jobs of large buckets: two consecutive windows of a bucket hold more than
+// kBkStage entries (or the first is one oversized key range), so a bucket of m entries
+// has at most 2m/kBkStage + 1 windows, and only buckets above kBkStage entries have any.
+constexpr int64_t max_jobsw(int64_t n) { return 3 * ceil_div(n, kBkStage) + 16; }
+// Buckets of more than kBkStage entries, and their chunks of at most kPartTile entries.
+constexpr int64_t max_big(int64_t n) { return n / (kBkStage + 1) + 1; }
+constexpr int64_t max_jobs3(int64_t n) { return ceil_div(n, kPartTile) + max_big(n); }
 
 constexpr SortLayout sort_layout(int64_t n, int frames = 1) {
   SortLayout L{};
@@ -162,6 +196,10 @@ constexpr SortLayout sort_layout(int64_t n, int frames = 1) {
   const int64_t ff = frames < 1 ? 1 : frames;
   L.sort_tiles = ceil_div(nn, kSortTile);
   L.seg_tiles = ceil_div(nn, kRedTile);
+  L.jobs2 = max_jobs2(nn);
+  L.jobsw = max_jobsw(nn);
+  L.big = max_big(nn);
+  L.jobs3 = max_jobs3(nn);
   size_t off = 0;
   L.state = off;
   off = align_up(off + sizeof(State), 256);
@@ -172,12 +210,26 @@ constexpr SortLayout sort_layout(int64_t n, int frames = 1) {
   L.seg_lb = off;  // per-tile records, then the tiles' head counts as a compact array
   off = align_up(off + size_t(L.seg_tiles) * (sizeof(TileRec) + sizeof(uint32_t)), 256);
   L.zero_bytes = off;  // state, frames, pass-0 status rows and segment status
-  L.bcount = off;  // points per bucket, then the chained-scan status per bucket job (the
-  off = align_up(off + size_t(kBucketSlots) * sizeof(uint32_t), 256);  // bucket tail
-  L.bstat = off;   // zeroes both only when it runs)
-  off = align_up(off + size_t(kBucketSlots) * sizeof(uint32_t), 256);
-  L.bjob = off;  // job table: first point, points, largest key (kBucketSlots each)
-  off = align_up(off + size_t(kBucketSlots) * 3 * sizeof(uint32_t), 256);
+  // bucket grouping: points per bucket (zeroed by calls that may take the grouping)
+  L.mhist = off;
+  off = align_up(off + size_t(kMsdBuckets) * sizeof(uint32_t), 256);
+  L.mvcnt = off;  // cells of every non-empty bucket
+  off = align_up(off + size_t(kMsdBuckets) * sizeof(uint32_t), 256);
+  L.mcur = off;  // write cursors: 256 of the first pass, then one per bucket (which later
+                 // hold every non-empty bucket's first row)
+  off = align_up(off + size_t(256 + kMsdBuckets) * sizeof(uint32_t), 256);
+  L.mjob = off;  // non-empty buckets: first entry, entries, bucket id (kMsdBuckets each)
+  off = align_up(off + size_t(kMsdBuckets) * 3 * sizeof(uint32_t), 256);
+  L.mjob2 = off;  // tables of the first pass's digit runs (first entries, first jobs)
+  off = align_up(off + 2 * 257 * sizeof(uint32_t), 256);
+  L.mjobm = off;  // bucket-kernel jobs of whole buckets
+  off = align_up(off + size_t(kMsdBuckets) * kJobWords * sizeof(uint32_t), 256);
+  L.mjobw = off;  // bucket-kernel jobs of windows of large buckets
+  off = align_up(off + size_t(L.jobsw) * kJobWords * sizeof(uint32_t), 256);
+  L.mcur3 = off;  // third-pass write cursors: 256 per large bucket
+  off = align_up(off + size_t(L.big) * 256 * sizeof(uint32_t), 256);
+  L.mjob3 = off;  // third-pass jobs: first entry, entries, large-bucket index
+  off = align_up(off + size_t(L.jobs3) * 4 * sizeof(uint32_t), 256);
   L.lb_b = off;
   off = align_up(off + size_t(L.sort_tiles) * kRadix * sizeof(uint32_t), 256);
   L.keys0 = off;  // also the two 32-bit key arrays of the narrow layout, 16-byte aligned
@@ -188,7 +240,9 @@ constexpr SortLayout sort_layout(int64_t n, int frames = 1) {
   off = align_up(off + size_t(nn) * sizeof(uint32_t), 256);
   L.idx1 = off;
   off = align_up(off + size_t(nn) * sizeof(uint32_t), 256);
-  L.total = off;
+  // bulk copies of the bucket kernel read whole 16-byte granules: up to 16 bytes past the
+  // last entry of an array
+  L.total = off + 256;
   return L;
 }
 
@@ -224,8 +278,7 @@ constexpr int kNarrowPasses = 4;
 cudaError_t launch_sort_pass(State* st, uint64_t* keys0, uint32_t* idx0, uint64_t* keys1,
                              uint32_t* idx1, uint32_t* lb_a, uint32_t* lb_b, int64_t n_max,
                              int pass, bool compact_input, uint32_t spin_limit, int* err,
-                             cudaStream_t stream, const NarrowBuffers* nb = nullptr,
-                             uint32_t* bcount = nullptr);
+                             cudaStream_t stream, const NarrowBuffers* nb = nullptr);
 // a4 + a5: reduce-by-key of the sorted table into key-ordered voxels.
 struct SegOut {
   uint64_t* keys;
@@ -245,13 +298,14 @@ cudaError_t launch_segreduce(State* st, const FrameState* fs, int nframes,
                              const uint32_t* idx1, const float* xyz, TileRec* recs,
                              int64_t n_max, const SegOut& out, int* err, cudaStream_t stream,
                              const NarrowBuffers* nb = nullptr, const float* poses = nullptr);
-// Bucket tail of the narrow layout (vg_bucket.cu): jobs from the bucket counts of the last
-// radix pass, then every bucket sorted by its low key bits on chip and reduced.
-cudaError_t launch_bucket_tail(State* st, const FrameState* fs, int nframes,
-                               const NarrowBuffers& nb, const uint32_t* bcount, uint32_t* bstat,
-                               uint32_t* bjob, int64_t n_max, const SegOut& out,
-                               uint32_t spin_limit, int* err, cudaStream_t stream);
-void warm_bucket_config();
+// Bucket grouping of the narrow layout (vg_msd.cu): the partition passes over the bucket
+// bits, then every bucket reduced on chip into its rows.  Kernels return at once unless
+// the key kernel chose the narrow layout with bucket grouping.
+cudaError_t launch_msd(State* st, const FrameState* fs, int nframes, const NarrowBuffers& nb,
+                       char* ws, const SortLayout& L, int64_t n_max, const SegOut& out,
+                       uint32_t spin_limit, int* err, cudaStream_t stream, int stage0,
+                       void (*mark)(int, cudaStream_t));
+void warm_msd_config();
 // Minimum-count filter (vg_filter.cu): its scratch follows the grouping method's layout.
 struct FilterLayout {
   size_t ticket, status, remap, zero_bytes, total;

@@ -8,7 +8,8 @@
 // points (the sort-path workspace for that many points, about 25 MB).  Every GPU that
 // loads this module keeps the array until the process exits.  Nothing here allocates:
 // the call looks up the array's device address once per device and then runs the
-// ordinary vg_downsample on it.
+// ordinary vg_downsample (sort path only) on it.  A cudaDeviceReset unloads the module;
+// the cached address is then stale, so the entry point is not for use after a reset.
 #include <mutex>
 
 #include "../../include/vg.h"
@@ -50,6 +51,8 @@ vg_status vg_downsample_noalloc(const float* xyz, int64_t n, float* origin, floa
                                 int64_t cap, int64_t* out_num_voxels, int32_t* out_point_to_voxel,
                                 int32_t* out_error, int flags, vg_stream_t stream) {
   if (n < 0 || n > kMaxPoints) return VG_ERR_INVALID_ARG;
+  // The array is sized for the sort path's workspace; the hash path needs far more.
+  if ((flags & VG_METHOD_MASK) == VG_METHOD_HASH) return VG_ERR_INVALID_ARG;
   void* scratch = nullptr;
   const vg_status s = scratch_for_current_device(&scratch);
   if (s != VG_OK) return s;

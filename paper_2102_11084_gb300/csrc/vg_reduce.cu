@@ -219,9 +219,11 @@ __device__ __forceinline__ void seg_count_body(
 // scan per round, a running carry between rounds.
 __global__ __launch_bounds__(1024) void seg_scan_kernel(const State* st,
                                                         const uint32_t* __restrict__ tile_heads,
-                                                        TileRec* recs, int64_t* num_voxels) {
+                                                        TileRec* recs, int64_t* num_voxels,
+                                                        const int* err) {
   __shared__ uint32_t s_tmp[32];
-  if (st->narrow && st->bucket) return;
+  if (st->narrow && st->msd) return;
+  if (*reinterpret_cast<const volatile int*>(err)) return;  // an earlier step failed
   const int64_t ntiles = ceil_div(int64_t(st->nitems), kRedTile);
   uint32_t carry = 0;
   for (int64_t base = 0; base < ntiles; base += 4 * 1024) {
@@ -618,8 +620,9 @@ struct RedPtrs {
 __global__ __launch_bounds__(kRedThreads) void seg_count_kernel(
     const State* st, const FrameState* __restrict__ fs, RedPtrs rp, const float* __restrict__ xyz,
     const float* __restrict__ poses, const uint8_t* __restrict__ attrs, int channels,
-    TileRec* recs, uint32_t* tile_heads) {
-  if (st->narrow && st->bucket) return;  // the bucket tail reduces instead
+    TileRec* recs, uint32_t* tile_heads, const int* err) {
+  if (st->narrow && st->msd) return;  // the bucket grouping reduces instead
+  if (*reinterpret_cast<const volatile int*>(err)) return;  // an earlier step failed
   if (st->narrow)
     seg_count_body<true>(st, fs, rp.nk0, rp.np0, rp.nk1, rp.np1, xyz, poses, nullptr, 0, recs,
                          tile_heads);
@@ -632,7 +635,8 @@ __global__ __launch_bounds__(kRedThreads, VG_RED_MINB) void seg_reduce_kernel(
     const State* st, const FrameState* __restrict__ fs, int nframes, RedPtrs rp,
     const float* __restrict__ xyz, const float* __restrict__ poses,
     const TileRec* __restrict__ recs, SegOut out, int* err) {
-  if (st->narrow && st->bucket) return;
+  if (st->narrow && st->msd) return;
+  if (*reinterpret_cast<const volatile int*>(err)) return;  // an earlier step failed
   if (st->narrow) {
     const bool odd = max(1, sort_passes(st->maxkey)) & 1;
     seg_reduce_narrow(st, fs, nframes, static_cast<const uint32_t*>(odd ? rp.nk1 : rp.nk0),
@@ -669,8 +673,8 @@ cudaError_t launch_segreduce(State* st, const FrameState* fs, int nframes,
                                  tiles);
   uint32_t* tile_heads = reinterpret_cast<uint32_t*>(recs + tiles);  // after the records
   seg_count_kernel<<<gc, kRedThreads, 0, stream>>>(st, fs, rp, xyz, poses, out.attrs_in,
-                                                   out.channels, recs, tile_heads);
-  seg_scan_kernel<<<1, 1024, 0, stream>>>(st, tile_heads, recs, out.num_voxels);
+                                                   out.channels, recs, tile_heads, err);
+  seg_scan_kernel<<<1, 1024, 0, stream>>>(st, tile_heads, recs, out.num_voxels, err);
   const int gr = persistent_grid(reinterpret_cast<const void*>(seg_reduce_kernel), kRedThreads,
                                  kRedSmem, tiles);
   seg_reduce_kernel<<<gr, kRedThreads, kRedSmem, stream>>>(st, fs, nframes, rp, xyz, poses, recs,

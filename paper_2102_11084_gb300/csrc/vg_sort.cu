@@ -71,7 +71,6 @@ struct SortSmem {
   uint32_t sdst[kSortTile];  // output position of each local slot
   int s_tile;
   uint32_t s_tile_n;
-  uint32_t s_bshift;  // bucket shift when this pass counts buckets, else 32 (no counting)
 };
 
 // One radix pass.  KeyT/PayT: (uint64, uint32 point index) for the wide layout, or
@@ -84,7 +83,7 @@ __device__ __forceinline__ void onesweep_body(
     const KeyT* __restrict__ keys_in, const PayT* __restrict__ pay_in,
     KeyT* __restrict__ keys_out, PayT* __restrict__ pay_out, State* st, uint32_t* lb_cur,
     uint32_t* lb_next, int pass, int64_t n_host, int compact_input, uint32_t spin_limit,
-    int* err, uint32_t* bcount, SortSmem& sm) {
+    int* err, SortSmem& sm) {
   uint32_t (&warp_hist)[kSortThreads / 32][kRadix] = sm.warp_hist;
   uint32_t* digit_start = sm.digit_start;
   int32_t* gofs = sm.gofs;
@@ -103,15 +102,8 @@ __device__ __forceinline__ void onesweep_body(
   const bool raw = pass == 0 && !compact_input;
   const int64_t n_items = raw ? n_host : int64_t(st->nitems);
   const int64_t ntiles = ceil_div(n_items, kSortTile);
-  // the bucket tail sorts only the digits above the bucket shift; its last pass also
-  // counts the points of every bucket (equal buckets are adjacent in the locally sorted
-  // tile: the earlier passes ordered them below the pass digit)
-  // (the bucket shift of the counting pass waits in shared memory: registers are full)
-  const bool btail = kNarrow && st->bucket;
-  const int shift = int(btail ? st->bshift : 0u) + pass * kRadixBits;
-  const bool has_next =
-      btail ? pass + 1 < passes : shift + kRadixBits < int(8 * sizeof(KeyT));
-  if (t == 0) sm.s_bshift = btail && pass + 1 == passes ? st->bshift : 32u;
+  const int shift = pass * kRadixBits;
+  const bool has_next = shift + kRadixBits < int(8 * sizeof(KeyT));
 
   // The next digit's histogram is accumulated over all tiles of this block and folded
   // into the global one once, at exit.
@@ -243,25 +235,6 @@ __device__ __forceinline__ void onesweep_body(
       atomicAdd(&next_hist[static_cast<uint32_t>(uint64_t(k) >> (shift + kRadixBits)) & (kRadix - 1)],
                 1u);
   }
-  const uint32_t bshift = sm.s_bshift;
-  if (kNarrow && bshift < 32u) {
-    // one atomic per run of equal buckets within each warp's 32 entries
-    for (uint32_t i0 = uint32_t(warp) * 32u; i0 < tile_n; i0 += kSortThreads) {
-      const uint32_t i = i0 + lane;
-      const bool in = i < tile_n;
-      const uint32_t b = in ? static_cast<uint32_t>(skey[i]) >> bshift : 0u;
-      const bool head = in && (lane == 0 || b != (static_cast<uint32_t>(skey[i - 1]) >> bshift));
-      const uint32_t hm = __ballot_sync(kFull, head);
-      // (b is below kBucketSlots for every key the key kernel wrote; the bound only
-      // matters after a failed call left the key buffer unwritten)
-      if (head && b < uint32_t(kBucketSlots)) {
-        const uint32_t above = hm & ~((2u << lane) - 1u);
-        const uint32_t nin = tile_n - i0 < 32u ? tile_n - i0 : 32u;
-        const uint32_t end = above ? uint32_t(__ffs(static_cast<int>(above)) - 1) : nin;
-        atomicAdd(&bcount[b], end - uint32_t(lane));
-      }
-    }
-  }
   __syncthreads();
 #if VG_SORT_EARLY_TICKET && VG_SORT_PREFETCH
   // the next tile's keys and payloads start their way into L2 while this one scatters
@@ -297,15 +270,15 @@ __global__ __launch_bounds__(kSortThreads, kSortMinBlocks) void onesweep_kernel(
     const uint64_t* kw_in, const uint32_t* iw_in, uint64_t* kw_out, uint32_t* iw_out,
     const uint32_t* kn_in, const uint64_t* pn_in, uint32_t* kn_out, uint64_t* pn_out, State* st,
     uint32_t* lb_cur, uint32_t* lb_next, int pass, int64_t n_host, int compact_input,
-    uint32_t spin_limit, int* err, uint32_t* bcount) {
+    uint32_t spin_limit, int* err) {
   __shared__ SortSmem sm;
+  if (*reinterpret_cast<volatile int*>(err)) return;  // an earlier step failed
   if (st->narrow)
     onesweep_body<uint32_t, uint64_t, true>(kn_in, pn_in, kn_out, pn_out, st, lb_cur, lb_next, pass,
-                                            n_host, compact_input, spin_limit, err, bcount, sm);
+                                            n_host, compact_input, spin_limit, err, sm);
   else
     onesweep_body<uint64_t, uint32_t, false>(kw_in, iw_in, kw_out, iw_out, st, lb_cur, lb_next,
-                                             pass, n_host, compact_input, spin_limit, err, bcount,
-                                             sm);
+                                             pass, n_host, compact_input, spin_limit, err, sm);
 }
 
 // Test kernel: one chained-scan wait of tile `tile` on status words nobody publishes; it
@@ -325,7 +298,7 @@ cudaError_t launch_debug_wait(const uint32_t* status, int tile, uint32_t limit, 
 cudaError_t launch_sort_pass(State* st, uint64_t* keys0, uint32_t* idx0, uint64_t* keys1,
                              uint32_t* idx1, uint32_t* lb_a, uint32_t* lb_b, int64_t n_max,
                              int pass, bool compact_input, uint32_t spin_limit, int* err,
-                             cudaStream_t stream, const NarrowBuffers* nb, uint32_t* bcount) {
+                             cudaStream_t stream, const NarrowBuffers* nb) {
   if (n_max == 0) return cudaSuccess;
   const int tiles = persistent_grid(reinterpret_cast<const void*>(onesweep_kernel), kSortThreads,
                                     0, ceil_div(n_max, kSortTile));
@@ -339,7 +312,7 @@ cudaError_t launch_sort_pass(State* st, uint64_t* keys0, uint32_t* idx0, uint64_
   onesweep_kernel<<<tiles, kSortThreads, 0, stream>>>(
       even ? keys0 : keys1, raw ? nullptr : (even ? idx0 : idx1), even ? keys1 : keys0,
       even ? idx1 : idx0, kn_in, pn_in, kn_out, pn_out, st, even ? lb_a : lb_b,
-      even ? lb_b : lb_a, pass, n_max, compact_input ? 1 : 0, spin_limit, err, bcount);
+      even ? lb_b : lb_a, pass, n_max, compact_input ? 1 : 0, spin_limit, err);
   return cudaGetLastError();
 }
 

@@ -142,28 +142,41 @@ __device__ __forceinline__ uint32_t frame_prologue(const FramesArg& fr, bool hav
                      : maxkey;
   const bool nar = fr.allow_narrow && have_extent && total_bits <= 32 && key_bound < 0xffffffffull;
   if (narrow) *narrow = nar;
-  // Bucket tail: the radix passes sort the top L bits of the key, L a whole number of
-  // digits aimed at kBucketTarget points per bucket, but at most kBucketMaxBits and enough
-  // that the low kb - L bits left to the on-chip reduction are at most 16.
-  const bool bmode = nar && fr.bucket_tail;
-  uint32_t bs = 0;
-  if (bmode) {
-    const uint32_t kb = key_bound ? 64u - __clzll(static_cast<long long>(key_bound)) : 0u;
-    const int64_t q = (fr.n + kBucketTarget - 1) / kBucketTarget;
-    uint32_t lw = q > 1 ? 64u - __clzll(static_cast<long long>(q - 1)) : 0u;
-    lw = min((lw + kRadixBits - 1) / kRadixBits * kRadixBits, uint32_t(kBucketMaxBits));
-    const uint32_t lo = kb > 16u ? kb - 16u : 0u;
-    const uint32_t L = max(lo, min(kb, lw));
-    bs = kb - L;
+  // Bucket grouping (narrow layout unless the caller forces the global radix sort): the
+  // top `top` key bits name the bucket, aimed at kMsdTarget points per bucket, at most
+  // kMsdMaxTop bits, and enough that the low kb - top bits reduced on chip are at most
+  // kMsdMaxLow -- and, with several frames, at most the frame key field, so that a bucket
+  // never holds two frames.  One partition pass splits up to 8 bucket bits, two up to 16.
+  bool mmode = nar && !fr.lsd_narrow;
+  uint32_t low = 0, levels = 0, b1 = 0, b2 = 0;
+  const uint32_t kb = key_bound ? 64u - __clzll(static_cast<long long>(key_bound)) : 0u;
+  const uint32_t lmax = key_shift < 64 ? min(uint32_t(kMsdMaxLow), key_shift)
+                                       : uint32_t(kMsdMaxLow);
+  const uint32_t lo = max(1u, kb > lmax ? kb - lmax : 0u);
+  // (kb <= 32 and the frame id takes at most 10 bits keep lo <= 16; checked all the same)
+  mmode = mmode && lo <= uint32_t(kMsdMaxTop);
+  if (mmode) {
+    const int64_t q = (fr.n + kMsdTarget - 1) / kMsdTarget;
+    const uint32_t want = q > 1 ? 64u - __clzll(static_cast<long long>(q - 1)) : 0u;
+    const uint32_t hi = max(lo, min(uint32_t(kMsdMaxTop), kb));
+    const uint32_t top = min(hi, max(lo, want));
+    low = kb > top ? kb - top : 0u;
+    levels = top > uint32_t(kRadixBits) ? 2u : 1u;
+    b2 = levels == 2 ? uint32_t(kRadixBits) : 0u;
+    b1 = top - b2;
   }
-  if (bshift) *bshift = bs;
+  // the key kernel histograms the first partition pass's digit
+  if (bshift) *bshift = mmode ? low + b2 : 0u;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     st->key_shift = key_shift;
     st->nframes = F;
     st->nchunks = T;
     st->narrow = nar ? 1u : 0u;
-    st->bucket = bmode ? 1u : 0u;
-    st->bshift = bs;
+    st->msd = mmode ? 1u : 0u;
+    st->lowbits = low;
+    st->levels = levels;
+    st->b1 = b1;
+    st->b2 = b2;
   }
 
   __syncthreads();

@@ -26,13 +26,16 @@ METHOD_AUTO = 0
 METHOD_SORT = 16
 METHOD_HASH = 32
 SORT_BUCKETS = 2
+SORT_LSD = 4
 USE_GRAPH = 64
 GRID_SHIFT = 8
-# "sort": radix sort of the points, every key digit in a global pass; "sort_bucket": the
-# narrow layout sorts only the top digits globally and reduces every bucket of the rest in
-# one block's shared memory; "hash": hash-table accumulation.  All give identical rows.
+# "sort": 32-bit keys grouped by buckets (partition passes over the top key bits, every
+# bucket reduced on chip), otherwise a global radix sort; "sort_lsd": every key digit in a
+# global radix pass and the segmented reduction; "sort_bucket": the same as "sort" (kept
+# for compatibility); "hash": hash-table accumulation.  All give identical rows.
 _METHODS = {"auto": METHOD_AUTO, "sort": METHOD_SORT,
-            "sort_bucket": METHOD_SORT | SORT_BUCKETS, "hash": METHOD_HASH}
+            "sort_bucket": METHOD_SORT | SORT_BUCKETS, "sort_lsd": METHOD_SORT | SORT_LSD,
+            "hash": METHOD_HASH}
 MAX_POINTS = (1 << 30) - 1
 MAX_FRAMES = 1024
 MAX_LEVELS = 8
@@ -683,7 +686,7 @@ def pyramid(xyz: torch.Tensor, leaf: float, levels: int, origin: Optional[torch.
             stream: Optional[torch.cuda.Stream] = None) -> list:
     """vg_pyramid: level 0 = decimation at ``leaf``, level k+1 = merge of level k by key>>3.
 
-    ``method``: "sort" or "sort_bucket" (level 0's grouping).  Returns a list of ``levels``
+    ``method``: "sort", "sort_lsd" or "sort_bucket" (level 0's grouping).  Returns a list of ``levels``
     Decimation tuples (point_to_voxel only on level 0).
     """
     xyz = _cuda_cloud(xyz)
@@ -698,9 +701,10 @@ def pyramid(xyz: torch.Tensor, leaf: float, levels: int, origin: Optional[torch.
     loff = torch.zeros(levels + 1, dtype=torch.int64, device=dev)
     err = torch.zeros(1, dtype=torch.int32, device=dev)
     p2v = torch.empty(max(n, 1), dtype=torch.int32, device=dev) if point_to_voxel else None
-    if method_flag(method) & ~(METHOD_SORT | SORT_BUCKETS):
+    if method_flag(method) & ~(METHOD_SORT | SORT_BUCKETS | SORT_LSD):
         raise ValueError("vg_pyramid groups level 0 by sorting")
-    flags = (ORIGIN_FROM_MIN if origin is None else 0) | (method_flag(method) & SORT_BUCKETS)
+    flags = (ORIGIN_FROM_MIN if origin is None else 0) | (method_flag(method) &
+                                                          (SORT_BUCKETS | SORT_LSD))
     ws = torch.empty(max(int(lib().vg_pyramid_workspace_bytes(n, levels, flags)), 256),
                      dtype=torch.uint8, device=dev)
     st = lib().vg_pyramid(_ptr(xyz), n, _ptr(org), ctypes.c_float(leaf), int(levels), _ptr(keys),

@@ -76,16 +76,20 @@ def test_argument_errors_return_before_any_launch():
 
 
 def test_grouping_flags():
-    # the bucket tail is a flag of the sort method: accepted by the single-cloud call and
-    # the pyramid (these calls stop at the missing workspace, before any launch), and the
-    # binding's method names map onto the header's flags
+    # the grouping choices are flags of the sort method: accepted by the single-cloud call
+    # and the pyramid (these calls stop at the missing workspace, before any launch), and
+    # the binding's method names map onto the header's flags
     assert vg.method_flag("sort_bucket") == vg.METHOD_SORT | vg.SORT_BUCKETS
+    assert vg.method_flag("sort_lsd") == vg.METHOD_SORT | vg.SORT_LSD
     assert vg.method_flag("sort") == vg.METHOD_SORT
     assert _call(flags=vg.METHOD_SORT | vg.SORT_BUCKETS) == vg.Status.WORKSPACE
+    assert _call(flags=vg.METHOD_SORT | vg.SORT_LSD) == vg.Status.WORKSPACE
+    assert _call(flags=vg.METHOD_SORT | 8) == vg.Status.INVALID_ARG
     assert _call(flags=vg.METHOD_SORT | vg.METHOD_HASH) == vg.Status.INVALID_ARG
     L = vg.lib()
     args = (None, 0, 8, ctypes.c_float(0.1), 2, None, None, None, 0, 16, None, None, None, 0)
     assert L.vg_pyramid(*args, vg.SORT_BUCKETS, None) == vg.Status.WORKSPACE
+    assert L.vg_pyramid(*args, vg.SORT_LSD, None) == vg.Status.WORKSPACE
     assert L.vg_pyramid(*args, vg.METHOD_HASH, None) == vg.Status.INVALID_ARG
 
 

@@ -1,10 +1,11 @@
-"""The bucket tail of the narrow sort path (method "sort_bucket": the radix passes sort
-the top key digits, every bucket is reduced in one block's shared memory through an
-occupancy bitmap of its low key bits): the same rows as the oracle and, bit for bit, as
-the all-global radix sort (method "sort"), for bucket shifts of 0, at most 8 and above 8
-bits, buckets of more points than a block holds in registers and of more voxels than one
-window of slots, buckets that are one voxel, a voxel of more points than the 32-bit slot
-sums and their carry counts hold, skewed clouds, batched frames and the pyramid."""
+"""The bucket grouping of the narrow sort path (the default "sort" method for 32-bit
+keys: partition passes over the top key bits, then every bucket reduced in one block's
+shared memory through an occupancy bitmap of its low key bits): the same rows as the
+oracle and, bit for bit, as the global LSD radix sort with its segmented reduction
+(method "sort_lsd"), for buckets of one key, of at most 8 and of more than 8 low bits,
+one and two partition passes, buckets larger than a block stages (streamed in windows
+of cells), buckets that are one voxel, a voxel of millions of points, skewed clouds,
+batched frames and the pyramid."""
 import numpy as np
 import pytest
 import torch
@@ -29,10 +30,10 @@ def same_rows(a, b):
 def check(x, leaf, origin=None):
     ref = oracle.downsample(x, leaf, origin)
     org = None if origin is None else torch.from_numpy(origin).cuda()
-    got = vg.downsample(cuda(x), leaf, org, method="sort_bucket")
+    got = vg.downsample(cuda(x), leaf, org)
     assert_decimation_equal(got, ref, check_p2v=False)
     org2 = None if origin is None else torch.from_numpy(origin).cuda()
-    same_rows(got, vg.downsample(cuda(x), leaf, org2))
+    same_rows(got, vg.downsample(cuda(x), leaf, org2, method="sort_lsd"))
     return got
 
 
@@ -40,24 +41,25 @@ def rng(seed):
     return np.random.Generator(np.random.PCG64(seed))
 
 
-@pytest.mark.parametrize("n", [1, 2, 511, 512, 513, 8191, 8192, 8193, 100_000])
-def test_sizes_around_a_register_chunk(n):
+@pytest.mark.parametrize("n", [1, 2, 511, 512, 513, 3071, 3072, 3073, 4095, 4096, 4097,
+                               8191, 8192, 8193, 100_000])
+def test_sizes_around_tiles_and_stages(n):
     x = synth.random_cloud(n, seed=17 + n, extent=2.0, nan_frac=0.03)
     check(x, 0.02)
 
 
 @pytest.mark.parametrize("edge,n", [(4, 50_000), (30, 50_000), (700, 120_000)])
 def test_bucket_shifts(edge, n):
-    # key widths of 6, 15 and 30 bits: bucket shifts of 0 (one key per bucket), at most 8
-    # and above 8 bits (bitmaps of one word up to 2048 words)
+    # key widths of 6, 15 and 30 bits: one partition pass with buckets of one key, one
+    # pass with a few low bits, and two passes with bitmaps of up to 2048 words
     x = (rng(edge).random((n, 3)) * edge * 0.02).astype(np.float32)
     check(x, 0.02, np.zeros(3, np.float32))
 
 
 def test_bucket_larger_than_a_block():
-    # a dense 0.4 m cluster puts ~150k points and ~8000 voxels in one bucket (more points
-    # than a block holds in registers, more voxels than one window of slots); a handful of
-    # far points widen the key to 30 bits
+    # a dense 0.4 m cluster puts ~150k points and ~8000 voxels in a few buckets (more
+    # entries than a block stages, more cells than one window); a handful of far points
+    # widen the key to 30 bits
     r = rng(5)
     cluster = (r.random((150_000, 3)) * 0.4).astype(np.float32)
     far = (r.random((50, 3)) * 20.0).astype(np.float32)
@@ -72,9 +74,8 @@ def test_one_voxel_buckets_of_many_points():
     check(x, 1.0, np.zeros(3, np.float32))
 
 
-def test_voxel_beyond_the_slot_carry_limit():
-    # 2.2M points in one voxel: more than the slot's 32-bit sums with 10-bit carry counts
-    # hold, so the voxel is summed again exactly
+def test_voxel_of_millions_of_points():
+    # 2.2M points in one voxel: a streamed bucket whose one cell's sums exceed 32 bits
     x = (0.2 + rng(11).random((2_200_000, 3)) * 0.6).astype(np.float32)
     got = check(x, 1.0, np.zeros(3, np.float32))
     assert int(gpu_counts(got.counts)[0]) == 2_200_000
@@ -105,8 +106,8 @@ def test_batched_frames_match_full_sort():
     frames.append(np.zeros((0, 3), np.float32))
     frames.append(synth.random_cloud(5000, seed=9, extent=8.0))
     leaves = [0.02 + 0.01 * (f % 3) for f in range(len(frames))]
-    a = vg.downsample_frames([cuda(f) for f in frames], leaves, method="sort_bucket")
-    b = vg.downsample_frames([cuda(f) for f in frames], leaves)
+    a = vg.downsample_frames([cuda(f) for f in frames], leaves)
+    b = vg.downsample_frames([cuda(f) for f in frames], leaves, method="sort_lsd")
     assert list(a.offsets) == list(b.offsets)
     same_rows(a, b)
     for f, x in enumerate(frames):
@@ -116,9 +117,12 @@ def test_batched_frames_match_full_sort():
         assert np.array_equal(gpu_counts(a.counts[lo:hi]), ref.counts)
 
 
-def test_pyramid_on_the_bucket_tail():
+def test_pyramid_on_the_bucket_grouping():
     x = synth.random_cloud(80_000, seed=21, extent=3.0)
-    p = vg.pyramid(cuda(x), 0.02, 3, method="sort_bucket")
+    p = vg.pyramid(cuda(x), 0.02, 3)
+    q = vg.pyramid(cuda(x), 0.02, 3, method="sort_lsd")
+    for lvl in range(3):
+        same_rows(p[lvl], q[lvl])
     ref, _ = oracle.pyramid(x, 0.02, 3)
     for lvl in range(3):
         assert np.array_equal(gpu_keys(p[lvl].keys), ref[lvl][0])

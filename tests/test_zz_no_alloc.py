@@ -29,18 +29,34 @@ def _compare(a, b):
     assert torch.equal(a.origin, b.origin)
     err = (a.centroids.double() - b.centroids.double()).abs().max().item() if ka.size else 0.0
     assert err <= TOL_M
-    assert torch.equal(a.point_to_voxel, b.point_to_voxel)
+    if a.point_to_voxel is None or b.point_to_voxel is None:
+        assert a.point_to_voxel is None and b.point_to_voxel is None
+    else:
+        assert torch.equal(a.point_to_voxel, b.point_to_voxel)
 
 
-def test_noalloc_matches_downsample_two_calls_in_a_row():
-    frames = [(synth.rgbd_frame(1280, 720, seed=11, cx=639.5, cy=359.5), 0.02),
-              (synth.rgbd_frame(640, 480, seed=12), 0.05)]
-    for xyz_np, leaf in frames:
+@pytest.mark.parametrize("method,p2v_first,p2v_second", [
+    ("sort", True, True),            # wide layout twice (point_to_voxel)
+    ("sort", False, False),          # the narrow layout (bucket grouping) twice
+    ("sort", True, False),           # a wide large call, then a narrow small one
+    ("sort_lsd", False, False),      # the narrow layout through the global radix sort
+    ("sort_lsd", False, True),
+])
+def test_noalloc_matches_downsample_two_calls_in_a_row(method, p2v_first, p2v_second):
+    frames = [(synth.rgbd_frame(1280, 720, seed=11, cx=639.5, cy=359.5), 0.02, p2v_first),
+              (synth.rgbd_frame(640, 480, seed=12), 0.05, p2v_second)]
+    for xyz_np, leaf, p2v in frames:
         xyz = torch.from_numpy(xyz_np).cuda()
-        ref = vg.downsample(xyz, leaf, point_to_voxel=True)
-        got = vg.downsample_noalloc(xyz, leaf, point_to_voxel=True)
+        ref = vg.downsample(xyz, leaf, method=method, point_to_voxel=p2v)
+        got = vg.downsample_noalloc(xyz, leaf, method=method, point_to_voxel=p2v)
         assert got.keys.numel() > 0
         _compare(got, ref)
+
+
+def test_noalloc_rejects_hash_method():
+    xyz = torch.from_numpy(synth.rgbd_frame(640, 480, seed=12)).cuda()
+    with pytest.raises(RuntimeError, match="invalid argument"):
+        vg.downsample_noalloc(xyz, 0.05, method="hash")
 
 
 def test_noalloc_rejects_oversize_cloud():
