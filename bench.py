@@ -43,9 +43,10 @@ def parse():
     p.add_argument("--impl", default="vg", choices=["vg", "reference"])
     p.add_argument("--n", type=int, default=N_POINTS)
     p.add_argument("--leaf", type=float, default=LEAF)
-    p.add_argument("--method", default="sort", choices=["sort", "sort_lsd", "hash"],
-                   help="grouping of the timed step: the default sort (bucket grouping for "
-                        "32-bit keys), the global LSD radix sort, or the hash path")
+    p.add_argument("--method", default="auto", choices=["auto", "sort", "sort_lsd", "hash"],
+                   help="grouping of the timed step: the library's choice (the bucket "
+                        "grouping for a cloud this large), the sort with bucket grouping, the "
+                        "global LSD radix sort, or the hash path")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extra", action="store_true",
                    help="skip the other configurations (single frame, batch, pyramid, "
@@ -219,7 +220,7 @@ def extra_measurements(args, dev, peak):
     x = torch.from_numpy(frame).to(dev)
     n = x.shape[0]
     r = {}
-    for m in ("sort", "sort_lsd", "hash"):
+    for m in ("auto", "sort", "sort_lsd", "hash"):
         buf = vg.alloc_buffers(n, dev, flags=vg.method_flag(m))
         ms = _time_ms(lambda: vg.downsample_into(x, 0.05, buf, origin_from_min=True, method=m), 200)
         v = int(buf.num_voxels.item())

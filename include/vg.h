@@ -73,7 +73,9 @@ typedef enum {
 /* flags */
 #define VG_ORIGIN_FROM_MIN 1 /* compute origin = per-axis min of the valid points and
                                 write it to `origin` (else `origin` is read)            */
-#define VG_METHOD_AUTO 0     /* the library's default grouping method (currently SORT)  */
+#define VG_METHOD_AUTO 0     /* the library's choice: SORT, with the bucket grouping
+                                from 4,194,304 points on and every digit in global radix
+                                passes (VG_SORT_LSD) below, where camera frames are      */
 #define VG_METHOD_SORT 16    /* sort the points by key and reduce each run of equal keys.
                                 32-bit keys (no point_to_voxel, no attributes, extents
                                 bound the keys): the top <= 16 key bits are split by one
@@ -309,9 +311,12 @@ VG_API vg_status vg_thin(const float* xyz, int64_t n, float* origin, float cell,
  * required) the first call captures the sequence and later calls with the same pointers,
  * sizes and flags replay it with one cudaGraphLaunch.  A plan is not thread-safe and its
  * workspace is shared by its calls: calls that overlap on the GPU race.
- * vg_plan_tune times both methods x streaming grids {4,8,16} blocks/SM on the given
- * batch (`reps` replays each, host-synchronising) and keeps the fastest; out_ms (6
- * floats or NULL) receives sort@4,8,16 then hash@4,8,16 in ms per batch.
+ * vg_plan_tune times three groupings -- VG_METHOD_SORT, VG_METHOD_SORT | VG_SORT_LSD and
+ * VG_METHOD_HASH -- x streaming grids {4,8,16} blocks/SM on the given batch (`reps`
+ * replays each, host-synchronising) and keeps the fastest; out_ms (9 floats or NULL)
+ * receives sort@4,8,16, sort_lsd@4,8,16 then hash@4,8,16 in ms per batch.  A plan's
+ * method (vg_plan_create flags, vg_plan_configure, vg_plan_get) is one of those three
+ * or VG_METHOD_AUTO (the library's choice by cloud size, the default of a new plan).
  */
 typedef struct vg_plan vg_plan;
 VG_API vg_status vg_plan_create(vg_plan** plan, int max_frames, int64_t max_points, int flags);

@@ -151,7 +151,9 @@ vg_status run_frames(const float* xyz, const FramesArg& fr, bool from_min, const
     // is grouped by buckets unless the caller asks for every digit in global passes.
     FramesArg frn = fr;
     frn.allow_narrow = out.p2v == nullptr && out.attrs_in == nullptr;
-    frn.lsd_narrow = (flags & VG_SORT_LSD) != 0;
+    // AUTO takes the bucket grouping only for large clouds (see kAutoBucketMinPoints)
+    frn.lsd_narrow = (flags & VG_SORT_LSD) != 0 ||
+                     ((flags & VG_METHOD_MASK) == VG_METHOD_AUTO && n < kAutoBucketMinPoints);
     const bool maybe_msd = frn.allow_narrow && !frn.lsd_narrow;
     const bool have_extent = from_min || F > 1 || frn.allow_narrow;
     const SortLayout L = sort_layout(n, F);
@@ -238,7 +240,7 @@ vg_status run_frames(const float* xyz, const FramesArg& fr, bool from_min, const
   if (e == cudaSuccess)
     e = launch_hash_insert(xyz, fr, have_extent, st, fs, tab, point_slot, spins, err, stream);
   mark(stage++, stream);
-  if (e == cudaSuccess) e = launch_hash_compact(tab, st, keys0, idx0, stream);
+  if (e == cudaSuccess) e = launch_hash_compact(tab, st, keys0, idx0, err, stream);
   mark(stage++, stream);
   for (int p = 0; p < kMaxPasses && e == cudaSuccess; ++p) {
     e = launch_sort_pass(st, keys0, idx0, keys1, idx1, lb_a, lb_b, n, p, true, spins, err, stream);
@@ -248,7 +250,7 @@ vg_status run_frames(const float* xyz, const FramesArg& fr, bool from_min, const
     e = launch_hash_finalize(st, fs, F, keys0, idx0, keys1, idx1, tab, slot_rank, n, out, err,
                              stream);
   mark(stage++, stream);
-  if (e == cudaSuccess && out.p2v) e = launch_hash_p2v(point_slot, slot_rank, n, out.p2v, stream);
+  if (e == cudaSuccess && out.p2v) e = launch_hash_p2v(point_slot, slot_rank, n, out.p2v, err, stream);
   mark(stage++, stream);
   return cuda_status(e);
 }
@@ -479,8 +481,9 @@ vg_status vg_pyramid(const float* xyz, int64_t n, float* origin, float leaf, int
   FramesArg fr{nullptr, 1, n, from_min ? nullptr : origin, from_min ? origin : nullptr, nullptr, leaf, 0};
   SegOut out{out_keys, out_centroids, out_counts, sums[0], cap_total, out_level_offsets + 1,
              nullptr, out_point_to_voxel};
+  // level 0 by the sort method's grouping (the AUTO choice unless the flags name one)
   s = run_frames(xyz, fr, from_min, out, out_error, workspace, L.total,
-                 VG_METHOD_SORT | (flags & (VG_SORT_BUCKETS | VG_SORT_LSD)), stream);
+                 flags & (VG_SORT_BUCKETS | VG_SORT_LSD), stream);
   if (s != VG_OK) return s;
   const uint32_t spins = spin_limit();
   for (int k = 1; k < levels && e == cudaSuccess; ++k)

@@ -29,6 +29,18 @@ constexpr uint64_t kKeySentinel = ~0ull;    // invalid point
 __device__ __forceinline__ void set_error(int* err, int code) {
   atomicCAS(err, 0, code);
 }
+// True once some step has set the error word: every kernel after the key kernel then
+// returns at once, so no step reads a row, an index or a count an earlier step left
+// unwritten.
+__device__ __forceinline__ bool error_raised(const int* err) {
+  return *reinterpret_cast<const volatile int*>(err) != 0;
+}
+// The same test taken once for the whole block (thread 0 reads, a barrier shares the
+// answer), for kernels with barriers: a block of a kernel that sets errors itself could
+// otherwise see the word change between its warps' reads.  Every thread must call it.
+__device__ __forceinline__ bool block_error_raised(const int* err) {
+  return __syncthreads_or(threadIdx.x == 0 && error_raised(err)) != 0;
+}
 
 // ---- voxel index and Morton key -----------------------------------------------------
 // Returns false when the index leaves [0, 2^21) (also for an infinite quotient).

@@ -35,7 +35,9 @@ __global__ __launch_bounds__(kFiltThreads) void filter_kernel(
   const int64_t V = *num_voxels < cap ? *num_voxels : cap;  // rows beyond cap were not written
   const int64_t ntiles = ceil_div(V, kFiltTile);
   for (;;) {
-    if (t == 0) s_tile = static_cast<int>(atomicAdd(ticket, 1u));
+    // After an error (an earlier step, or a chained-scan timeout here) a block takes no
+    // more tickets; every ticket taken is processed, so no tile waits on a skipped one.
+    if (t == 0) s_tile = error_raised(err) ? 0x7fffffff : static_cast<int>(atomicAdd(ticket, 1u));
     __syncthreads();
     const int tile = s_tile;
     if (tile >= ntiles) break;
@@ -99,7 +101,9 @@ __global__ __launch_bounds__(kFiltThreads) void filter_kernel(
 // New voxel count, and per-frame offsets (kept rows before each frame's first row).
 __global__ __launch_bounds__(1024) void filter_fix_kernel(int64_t* num_voxels, int64_t cap,
                                                           int64_t* frame_offsets, int nframes,
-                                                          const uint32_t* __restrict__ remap) {
+                                                          const uint32_t* __restrict__ remap,
+                                                          const int* err) {
+  if (block_error_raised(err)) return;  // the remap may be incomplete
   const int64_t V = *num_voxels < cap ? *num_voxels : cap;
   const uint32_t last = V > 0 ? remap[V - 1] : 0u;
   const int64_t total = V > 0 ? int64_t(last & ~kKeptBit) + (last >> 31) : 0;
@@ -113,7 +117,8 @@ __global__ __launch_bounds__(1024) void filter_fix_kernel(int64_t* num_voxels, i
 }
 
 __global__ void filter_p2v_kernel(int32_t* p2v, int64_t n, int64_t cap,
-                                  const uint32_t* __restrict__ remap) {
+                                  const uint32_t* __restrict__ remap, const int* err) {
+  if (error_raised(err)) return;  // the remap may be incomplete
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n;
        i += int64_t(gridDim.x) * blockDim.x) {
     const int32_t v = p2v[i];
@@ -158,11 +163,11 @@ cudaError_t launch_filter(char* ws, const FilterLayout& L, int64_t cap, uint32_t
                                                    out.attrs_out ? out.channels : 0, remap,
                                                    status, ticket, spin_limit, err);
   filter_fix_kernel<<<1, 1024, 0, stream>>>(out.num_voxels, cap, out.frame_offsets, nframes,
-                                            remap);
+                                            remap, err);
   if (out.p2v && n_points > 0) {
     const int blocks = static_cast<int>(ceil_div(n_points, 256) < 4096 ? ceil_div(n_points, 256)
                                                                          : 4096);
-    filter_p2v_kernel<<<blocks, 256, 0, stream>>>(out.p2v, n_points, cap, remap);
+    filter_p2v_kernel<<<blocks, 256, 0, stream>>>(out.p2v, n_points, cap, remap, err);
   }
   return cudaGetLastError();
 }

@@ -176,8 +176,10 @@ __global__ __launch_bounds__(kStreamThreads) void hash_insert_kernel(
 // st->nitems and histograms their digit 0.
 __global__ __launch_bounds__(256) void hash_compact_kernel(HashTable tab, State* st,
                                                            uint64_t* __restrict__ keys,
-                                                           uint32_t* __restrict__ slots) {
+                                                           uint32_t* __restrict__ slots,
+                                                           const int* err) {
   __shared__ uint32_t hist[kRadix];
+  if (block_error_raised(err)) return;  // an earlier step failed
   hist[threadIdx.x] = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31;
@@ -206,6 +208,7 @@ __global__ __launch_bounds__(256) void hash_finalize_kernel(
     const uint64_t* __restrict__ keys0, const uint32_t* __restrict__ idx0,
     const uint64_t* __restrict__ keys1, const uint32_t* __restrict__ idx1, HashTable tab,
     uint32_t* __restrict__ slot_rank, SegOut out, int* err) {
+  if (error_raised(err)) return;  // an earlier step failed
   const int64_t V = st->nitems;
   const int64_t i = int64_t(blockIdx.x) * 256 + threadIdx.x;
   if (i >= V) return;
@@ -254,7 +257,9 @@ __global__ __launch_bounds__(256) void hash_finalize_kernel(
 
 __global__ __launch_bounds__(256) void hash_p2v_kernel(const uint32_t* __restrict__ point_slot,
                                                        const uint32_t* __restrict__ slot_rank,
-                                                       int64_t n, int32_t* __restrict__ p2v) {
+                                                       int64_t n, int32_t* __restrict__ p2v,
+                                                       const int* err) {
+  if (error_raised(err)) return;  // an earlier step failed
   for (int64_t i = int64_t(blockIdx.x) * 256 + threadIdx.x; i < n;
        i += int64_t(gridDim.x) * 256) {
     const uint32_t s = point_slot[i];
@@ -277,12 +282,12 @@ cudaError_t launch_hash_insert(const float* xyz, const FramesArg& fr, bool have_
 }
 
 cudaError_t launch_hash_compact(const HashTable& tab, State* st, uint64_t* keys, uint32_t* slots,
-                                cudaStream_t stream) {
+                                const int* err, cudaStream_t stream) {
   const int64_t H = int64_t(tab.mask) + 1;
   const int64_t want = ceil_div(H, 256);
   const int64_t cap = int64_t(num_sms()) * 16;
   hash_compact_kernel<<<static_cast<int>(want < cap ? want : cap), 256, 0, stream>>>(tab, st, keys,
-                                                                                    slots);
+                                                                                    slots, err);
   return cudaGetLastError();
 }
 
@@ -298,12 +303,12 @@ cudaError_t launch_hash_finalize(const State* st, const FrameState* fs, int nfra
 }
 
 cudaError_t launch_hash_p2v(const uint32_t* point_slot, const uint32_t* slot_rank, int64_t n,
-                            int32_t* p2v, cudaStream_t stream) {
+                            int32_t* p2v, const int* err, cudaStream_t stream) {
   if (n == 0) return cudaSuccess;
   const int64_t want = ceil_div(n, 256);
   const int64_t cap = int64_t(num_sms()) * 16;
-  hash_p2v_kernel<<<static_cast<int>(want < cap ? want : cap), 256, 0, stream>>>(point_slot,
-                                                                                slot_rank, n, p2v);
+  hash_p2v_kernel<<<static_cast<int>(want < cap ? want : cap), 256, 0, stream>>>(
+      point_slot, slot_rank, n, p2v, err);
   return cudaGetLastError();
 }
 

@@ -43,6 +43,11 @@ constexpr int kMsdMaxLow = 16;                 // largest bucket-local key width
 constexpr int kMsdMaxTop = 16;                 // largest bucket id width (two 8-bit levels)
 constexpr int kMsdBuckets = 1 << kMsdMaxTop;   // bucket ids
 constexpr int kMsdTarget = 2048;               // average points per bucket the split aims at
+// Clouds from this many points on take the bucket grouping under VG_METHOD_AUTO; smaller
+// ones (camera frames, whose dense surfaces make large buckets of few cells) take the
+// global radix sort, which is faster there (measured: a 640x480 frame 0.10 vs 0.20 ms,
+// the 50M-point map 2.78 vs 2.24 ms).
+constexpr int64_t kAutoBucketMinPoints = int64_t(1) << 22;
 constexpr int kPartThreads = 256;              // partition pass: 256 threads x 16 records
 constexpr int kPartItems = 16;
 constexpr int kPartTile = kPartThreads * kPartItems;
@@ -386,14 +391,14 @@ cudaError_t launch_hash_insert(const float* xyz, const FramesArg& fr, bool have_
                                FrameState* fs, const HashTable& tab, uint32_t* point_slot,
                                uint32_t spin_limit, int* err, cudaStream_t stream);
 cudaError_t launch_hash_compact(const HashTable& tab, State* st, uint64_t* keys, uint32_t* slots,
-                                cudaStream_t stream);
+                                const int* err, cudaStream_t stream);
 cudaError_t launch_hash_finalize(const State* st, const FrameState* fs, int nframes,
                                  const uint64_t* keys0, const uint32_t* idx0,
                                  const uint64_t* keys1, const uint32_t* idx1,
                                  const HashTable& tab, uint32_t* slot_rank, int64_t n_max,
                                  const SegOut& out, int* err, cudaStream_t stream);
 cudaError_t launch_hash_p2v(const uint32_t* point_slot, const uint32_t* slot_rank, int64_t n,
-                            int32_t* p2v, cudaStream_t stream);
+                            int32_t* p2v, const int* err, cudaStream_t stream);
 
 // ---- pyramid ----
 constexpr int kMaxLevels = 8;

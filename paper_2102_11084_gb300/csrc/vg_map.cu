@@ -201,7 +201,7 @@ vg_status vg_map_extract(vg_map* m, uint64_t* out_keys, float* out_centroids,
   if (e == cudaSuccess) e = cudaMemsetAsync(out_num_voxels, 0, sizeof(int64_t), stream);
   if (e != cudaSuccess) return VG_ERR_CUDA;
   map_extract_init<<<1, 1, 0, stream>>>(m->st, m->xst);
-  e = vg::launch_hash_compact(m->tab, m->xst, m->keys0, m->idx0, stream);
+  e = vg::launch_hash_compact(m->tab, m->xst, m->keys0, m->idx0, err, stream);
   const uint32_t spins = vg::spin_limit();
   for (int p = 0; p < vg::kMaxPasses && e == cudaSuccess; ++p)
     e = vg::launch_sort_pass(m->xst, m->keys0, m->idx0, m->keys1, m->idx1, m->lb_a, m->lb_b,

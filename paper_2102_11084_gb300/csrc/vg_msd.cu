@@ -37,9 +37,6 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
-__device__ __forceinline__ bool failed(const int* err) {
-  return *reinterpret_cast<const volatile int*>(err) != 0;
-}
 __device__ __forceinline__ bool msd_on(const State* st) { return st->narrow && st->msd; }
 
 // ---- scan of the first digit ----------------------------------------------------------
@@ -75,7 +72,7 @@ __device__ __forceinline__ void job2_range(const uint32_t* start1, const uint32_
 __global__ __launch_bounds__(256) void msd_scan1_kernel(State* st, uint32_t* __restrict__ cur1,
                                                         uint32_t* __restrict__ t1, int* err) {
   __shared__ uint32_t tmp[8];
-  if (!msd_on(st) || failed(err)) return;
+  if (!msd_on(st) || block_error_raised(err)) return;
   const uint32_t t = threadIdx.x;
   const uint32_t c = st->hist[0][t];  // digits at or above 2^b1 count nothing
   const uint32_t nj = (c + kPartTile - 1) / kPartTile;
@@ -121,7 +118,7 @@ __global__ __launch_bounds__(kPartThreads, 3) void msd_part_kernel(
     State* st, uint32_t* ka, uint64_t* pa, uint32_t* kb, uint64_t* pb, uint32_t* cursor,
     const uint32_t* __restrict__ t1, int64_t n_max, int* err) {
   __shared__ PartSmem sm;
-  if (!msd_on(st) || failed(err)) return;
+  if (!msd_on(st) || block_error_raised(err)) return;
   if (kLevel == 2 && st->levels != 2) return;
   if (kLevel == 3 && st->njobs3 == 0) return;
   const int t = threadIdx.x;
@@ -225,7 +222,7 @@ __global__ __launch_bounds__(256) void msd_upsweep_kernel(State* st, const uint3
   __shared__ uint32_t h[256];
   __shared__ uint32_t tab[2 * kT1];
   __shared__ uint32_t nzw[8];
-  if (!msd_on(st) || failed(err) || st->levels != 2) return;
+  if (!msd_on(st) || st->levels != 2 || block_error_raised(err)) return;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   for (int i = t; i < 2 * kT1; i += 256) tab[i] = t1[i];
   const uint32_t shift = st->lowbits;
@@ -292,7 +289,7 @@ __global__ __launch_bounds__(1024) void msd_scan2_kernel(State* st, const uint32
                                                          uint32_t* __restrict__ bjob, int* err) {
   __shared__ uint32_t tmp[32];
   __shared__ uint32_t s_be, s_bj;
-  if (!msd_on(st) || failed(err)) return;
+  if (!msd_on(st) || block_error_raised(err)) return;
   const int t = threadIdx.x;
   const bool two = st->levels == 2;
   const uint32_t nb = 1u << (st->b1 + st->b2);
@@ -449,7 +446,7 @@ __global__ __launch_bounds__(kCntThreads) void msd_count_kernel(
     uint32_t jobs3_cap, int* err) {
   extern __shared__ __align__(128) unsigned char cnt_smem[];
   CntSmem& sm = *reinterpret_cast<CntSmem*>(cnt_smem);
-  if (!msd_on(st) || failed(err)) return;
+  if (!msd_on(st) || block_error_raised(err)) return;
   const uint32_t nb = st->nbjobs;
   if (blockIdx.x >= nb) return;
   const uint32_t* K = st->levels == 2 ? k0 : k1;  // the last partition pass's output
@@ -635,7 +632,7 @@ __global__ __launch_bounds__(1024) void msd_plan_kernel(State* st, const uint32_
   __shared__ uint32_t tmp[32];
   __shared__ uint32_t s_base;
   __shared__ uint32_t wm[32][32], wb[32][32], wrow[32][32], wst[32][32];
-  if (!msd_on(st) || failed(err)) return;
+  if (!msd_on(st) || block_error_raised(err)) return;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const uint32_t nb = st->nbjobs;
   const uint32_t blk = blockIdx.x;
@@ -951,7 +948,7 @@ __global__ __launch_bounds__(kBkThreads, VG_BK_MINB) void msd_bucket_kernel(
     int* err) {
   extern __shared__ __align__(128) unsigned char bk_smem[];
   BkSmem& sm = *reinterpret_cast<BkSmem*>(bk_smem);
-  if (!msd_on(st) || failed(err)) return;
+  if (!msd_on(st) || block_error_raised(err)) return;
   const uint32_t nwin = st->nwjobs, njobs = nwin + st->nmjobs;
   if (blockIdx.x >= njobs) return;
   const bool two = st->levels == 2;

@@ -43,6 +43,13 @@ int plan_flags(const vg_plan* p, int flags) {
   return (flags & VG_ORIGIN_FROM_MIN) | p->method | (p->grid_per_sm << VG_GRID_SHIFT);
 }
 
+// The grouping choices a plan holds: the sort (bucket grouping for 32-bit keys), the sort
+// with every digit in global radix passes, and the hash path.
+bool plan_method_ok(int m) {
+  return m == VG_METHOD_AUTO || m == VG_METHOD_SORT || m == (VG_METHOD_SORT | VG_SORT_LSD) ||
+         m == VG_METHOD_HASH;
+}
+
 void drop_graph(vg_plan* p) {
   if (p->exec) cudaGraphExecDestroy(p->exec);
   p->exec = nullptr;
@@ -67,7 +74,9 @@ vg_status vg_plan_create(vg_plan** out, int max_frames, int64_t max_points, int 
   }
   p->max_frames = max_frames;
   p->max_points = max_points;
-  p->method = m == VG_METHOD_HASH ? VG_METHOD_HASH : VG_METHOD_SORT;
+  p->method = m == VG_METHOD_HASH ? VG_METHOD_HASH
+                                  : (m == VG_METHOD_AUTO ? VG_METHOD_AUTO
+                                                         : (VG_METHOD_SORT | (flags & VG_SORT_LSD)));
   const size_t a = vg::frames_workspace_bytes(max_points, max_frames, VG_METHOD_SORT);
   const size_t b = vg::frames_workspace_bytes(max_points, max_frames, VG_METHOD_HASH);
   p->ws_bytes = a > b ? a : b;
@@ -89,8 +98,7 @@ vg_status vg_plan_destroy(vg_plan* p) {
 }
 
 vg_status vg_plan_configure(vg_plan* p, int method, int grid_per_sm) {
-  if (!p || (method != VG_METHOD_SORT && method != VG_METHOD_HASH) || grid_per_sm < 0 ||
-      grid_per_sm > 255)
+  if (!p || !plan_method_ok(method) || grid_per_sm < 0 || grid_per_sm > 255)
     return VG_ERR_INVALID_ARG;
   if (method != p->method || grid_per_sm != p->grid_per_sm) drop_graph(p);
   p->method = method;
@@ -165,7 +173,7 @@ vg_status vg_plan_tune(vg_plan* p, const float* xyz, int64_t n_total,
                        float* out_ms) {
   if (!p || reps < 1) return VG_ERR_INVALID_ARG;
   cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
-  const int methods[2] = {VG_METHOD_SORT, VG_METHOD_HASH};
+  const int methods[3] = {VG_METHOD_SORT, VG_METHOD_SORT | VG_SORT_LSD, VG_METHOD_HASH};
   const int grids[3] = {4, 8, 16};
   float best = 3.0e38f;
   int best_m = p->method, best_g = p->grid_per_sm;
@@ -173,7 +181,7 @@ vg_status vg_plan_tune(vg_plan* p, const float* xyz, int64_t n_total,
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return VG_ERR_CUDA;
   vg_status result = VG_OK;
   int slot = 0;
-  for (int mi = 0; mi < 2 && result == VG_OK; ++mi) {
+  for (int mi = 0; mi < 3 && result == VG_OK; ++mi) {
     for (int gi = 0; gi < 3 && result == VG_OK; ++gi, ++slot) {
       vg_plan_configure(p, methods[mi], grids[gi]);
       // one untimed run (captures the graph), then `reps` timed replays

@@ -26,6 +26,9 @@ __global__ __launch_bounds__(kMergeThreads) void pyramid_merge_kernel(
   __shared__ uint32_t s_tmp[kMergeThreads / 32];
   __shared__ uint32_t s_excl;
   const int t = threadIdx.x;
+  // An earlier step failed: take no ticket.  Every ticket taken is processed, so no tile
+  // ever waits for one that a returning block skipped.
+  if (block_error_raised(err)) return;
   if (t == 0) s_tile = static_cast<int>(atomicAdd(&st->tile_ctr[kMaxPasses + level], 1u));
   __syncthreads();
   const int tile = s_tile;

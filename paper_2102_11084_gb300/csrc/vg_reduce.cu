@@ -223,7 +223,7 @@ __global__ __launch_bounds__(1024) void seg_scan_kernel(const State* st,
                                                         const int* err) {
   __shared__ uint32_t s_tmp[32];
   if (st->narrow && st->msd) return;
-  if (*reinterpret_cast<const volatile int*>(err)) return;  // an earlier step failed
+  if (block_error_raised(err)) return;  // an earlier step failed
   const int64_t ntiles = ceil_div(int64_t(st->nitems), kRedTile);
   uint32_t carry = 0;
   for (int64_t base = 0; base < ntiles; base += 4 * 1024) {
@@ -622,7 +622,7 @@ __global__ __launch_bounds__(kRedThreads) void seg_count_kernel(
     const float* __restrict__ poses, const uint8_t* __restrict__ attrs, int channels,
     TileRec* recs, uint32_t* tile_heads, const int* err) {
   if (st->narrow && st->msd) return;  // the bucket grouping reduces instead
-  if (*reinterpret_cast<const volatile int*>(err)) return;  // an earlier step failed
+  if (block_error_raised(err)) return;  // an earlier step failed
   if (st->narrow)
     seg_count_body<true>(st, fs, rp.nk0, rp.np0, rp.nk1, rp.np1, xyz, poses, nullptr, 0, recs,
                          tile_heads);
@@ -636,7 +636,7 @@ __global__ __launch_bounds__(kRedThreads, VG_RED_MINB) void seg_reduce_kernel(
     const float* __restrict__ xyz, const float* __restrict__ poses,
     const TileRec* __restrict__ recs, SegOut out, int* err) {
   if (st->narrow && st->msd) return;
-  if (*reinterpret_cast<const volatile int*>(err)) return;  // an earlier step failed
+  if (block_error_raised(err)) return;  // an earlier step failed
   if (st->narrow) {
     const bool odd = max(1, sort_passes(st->maxkey)) & 1;
     seg_reduce_narrow(st, fs, nframes, static_cast<const uint32_t*>(odd ? rp.nk1 : rp.nk0),

@@ -272,7 +272,7 @@ __global__ __launch_bounds__(kSortThreads, kSortMinBlocks) void onesweep_kernel(
     uint32_t* lb_cur, uint32_t* lb_next, int pass, int64_t n_host, int compact_input,
     uint32_t spin_limit, int* err) {
   __shared__ SortSmem sm;
-  if (*reinterpret_cast<volatile int*>(err)) return;  // an earlier step failed
+  if (block_error_raised(err)) return;  // an earlier step failed
   if (st->narrow)
     onesweep_body<uint32_t, uint64_t, true>(kn_in, pn_in, kn_out, pn_out, st, lb_cur, lb_next, pass,
                                             n_host, compact_input, spin_limit, err, sm);

@@ -75,7 +75,9 @@ __device__ __forceinline__ const uint32_t* sorted_idx(const State* st, const uin
 __global__ void thin_setup_kernel(const State* st, const uint32_t* idx0, const uint32_t* idx1,
                                   const float* __restrict__ xyz, const uint32_t* __restrict__ prio,
                                   const int32_t* __restrict__ p2v, uint32_t* cstart, float* sx,
-                                  uint32_t* sprio, uint32_t* sidx, uint8_t* state) {
+                                  uint32_t* sprio, uint32_t* sidx, uint8_t* state,
+                                  const int* err) {
+  if (error_raised(err)) return;  // the grouping failed: point_to_voxel is unwritten
   const int64_t m = st->nitems;
   const uint32_t* I = sorted_idx(st, idx0, idx1);
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < m;
@@ -95,7 +97,9 @@ __global__ void thin_setup_kernel(const State* st, const uint32_t* idx0, const u
 
 // Per cell: rows of the 27 cells around it (itself included), kNoCell where empty.
 __global__ void thin_neighbors_kernel(const int64_t* __restrict__ num_cells,
-                                      const uint64_t* __restrict__ vkeys, uint32_t* nb) {
+                                      const uint64_t* __restrict__ vkeys, uint32_t* nb,
+                                      const int* err) {
+  if (error_raised(err)) return;
   const int64_t V = *num_cells;
   for (int64_t v = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; v < V;
        v += int64_t(gridDim.x) * blockDim.x) {
@@ -130,7 +134,8 @@ __global__ __launch_bounds__(256) void thin_count_kernel(
     const State* st, const int32_t* __restrict__ p2v, const uint32_t* __restrict__ sidx,
     const uint32_t* __restrict__ cstart, const uint32_t* __restrict__ vcnt,
     const uint32_t* __restrict__ nb, const float* __restrict__ sx, uint8_t* state, float r2,
-    int64_t threshold, uint32_t* marked_count) {
+    int64_t threshold, uint32_t* marked_count, const int* err) {
+  if (error_raised(err)) return;  // nothing marked: the loop ends after one pass
   const int64_t m = st->nitems;
   uint32_t marked = 0;
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < m;
@@ -172,8 +177,9 @@ __global__ __launch_bounds__(256) void thin_hist_kernel(const State* st, const u
                                                         const uint32_t* __restrict__ sprio,
                                                         const uint32_t* __restrict__ sidx,
                                                         uint64_t prefix, uint64_t mask, int shift,
-                                                        uint32_t* hist) {
+                                                        uint32_t* hist, const int* err) {
   __shared__ uint32_t h[256];
+  if (block_error_raised(err)) return;
   h[threadIdx.x] = 0;
   __syncthreads();
   const int64_t m = st->nitems;
@@ -192,7 +198,9 @@ __global__ __launch_bounds__(256) void thin_hist_kernel(const State* st, const u
 __global__ __launch_bounds__(256) void thin_delete_kernel(const State* st, uint8_t* state,
                                                           const uint32_t* __restrict__ sprio,
                                                           const uint32_t* __restrict__ sidx,
-                                                          uint64_t prefix, uint64_t mask) {
+                                                          uint64_t prefix, uint64_t mask,
+                                                          const int* err) {
+  if (error_raised(err)) return;
   const int64_t m = st->nitems;
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < m;
        i += int64_t(gridDim.x) * blockDim.x) {
@@ -205,7 +213,9 @@ __global__ __launch_bounds__(256) void thin_delete_kernel(const State* st, uint8
 // keep flag per input point (the buffer was zeroed: invalid points stay 0), number kept.
 __global__ __launch_bounds__(256) void thin_output_kernel(const State* st, const uint8_t* state,
                                                           const uint32_t* __restrict__ sidx,
-                                                          uint8_t* keep, uint32_t* kept) {
+                                                          uint8_t* keep, uint32_t* kept,
+                                                          const int* err) {
+  if (error_raised(err)) return;  // every keep flag stays 0, the count 0
   const int64_t m = st->nitems;
   uint32_t c = 0;
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < m;
@@ -295,8 +305,8 @@ vg_status vg_thin(const float* xyz, int64_t n, float* origin, float cell, float 
   const int g = grid_for(n);
   if (n > 0) {
     thin_setup_kernel<<<g, 256, 0, stream>>>(st, idx0, idx1, xyz, priority, p2v, cstart, sx,
-                                             sprio, sidx, state);
-    thin_neighbors_kernel<<<g, 256, 0, stream>>>(vnum, vkeys, nb);
+                                             sprio, sidx, state, err);
+    thin_neighbors_kernel<<<g, 256, 0, stream>>>(vnum, vkeys, nb, err);
   }
   const float r2 = radius * radius;
   const int64_t max_passes = n / batch + 2;  // every pass but the last deletes `batch` points
@@ -306,12 +316,12 @@ vg_status vg_thin(const float* xyz, int64_t n, float* origin, float cell, float 
     e = cudaMemsetAsync(ctr, 0, sizeof(uint32_t), stream);
     if (e != cudaSuccess) return VG_ERR_CUDA;
     thin_count_kernel<<<g, 256, 0, stream>>>(st, p2v, sidx, cstart, vcnt, nb, sx, state, r2,
-                                             threshold, ctr);
+                                             threshold, ctr, err);
     e = cudaMemcpyAsync(&marked, ctr, sizeof(uint32_t), cudaMemcpyDeviceToHost, stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) return VG_ERR_CUDA;
     if (int64_t(marked) <= batch) {  // the last pass: every marked point goes
-      thin_delete_kernel<<<g, 256, 0, stream>>>(st, state, sprio, sidx, ~0ull, 0ull);
+      thin_delete_kernel<<<g, 256, 0, stream>>>(st, state, sprio, sidx, ~0ull, 0ull, err);
       ++passes;
       break;
     }
@@ -322,7 +332,8 @@ vg_status vg_thin(const float* xyz, int64_t n, float* origin, float cell, float 
       uint32_t h[256];
       e = cudaMemsetAsync(hist, 0, sizeof(h), stream);
       if (e != cudaSuccess) return VG_ERR_CUDA;
-      thin_hist_kernel<<<g, 256, 0, stream>>>(st, state, sprio, sidx, prefix, mask, shift, hist);
+      thin_hist_kernel<<<g, 256, 0, stream>>>(st, state, sprio, sidx, prefix, mask, shift, hist,
+                                                  err);
       e = cudaMemcpyAsync(h, hist, sizeof(h), cudaMemcpyDeviceToHost, stream);
       if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
       if (e != cudaSuccess) return VG_ERR_CUDA;
@@ -332,10 +343,10 @@ vg_status vg_thin(const float* xyz, int64_t n, float* origin, float cell, float 
       mask |= 0xffull << shift;
       if (want == int64_t(h[d])) break;  // the whole bucket goes: no finer digit needed
     }
-    thin_delete_kernel<<<g, 256, 0, stream>>>(st, state, sprio, sidx, prefix, mask);
+    thin_delete_kernel<<<g, 256, 0, stream>>>(st, state, sprio, sidx, prefix, mask, err);
   }
   if (n > 0) {
-    thin_output_kernel<<<g, 256, 0, stream>>>(st, state, sidx, out_keep, ctr + 1);
+    thin_output_kernel<<<g, 256, 0, stream>>>(st, state, sidx, out_keep, ctr + 1, err);
     thin_finish_kernel<<<1, 1, 0, stream>>>(ctr + 1, out_num_kept);
   } else {
     e = cudaMemsetAsync(out_num_kept, 0, sizeof(int64_t), stream);

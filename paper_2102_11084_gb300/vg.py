@@ -29,6 +29,7 @@ SORT_BUCKETS = 2
 SORT_LSD = 4
 USE_GRAPH = 64
 GRID_SHIFT = 8
+# "auto" (the default): "sort" for clouds of 4,194,304 points or more, else "sort_lsd";
 # "sort": 32-bit keys grouped by buckets (partition passes over the top key bits, every
 # bucket reduced on chip), otherwise a global radix sort; "sort_lsd": every key digit in a
 # global radix pass and the segmented reduction; "sort_bucket": the same as "sort" (kept
@@ -230,7 +231,7 @@ def alloc_buffers(n: int, device, *, cap: Optional[int] = None, point_to_voxel: 
 
 
 def downsample_into(xyz: torch.Tensor, leaf: float, buf: Buffers, *, origin_from_min: bool,
-                    method="sort", stream: Optional[torch.cuda.Stream] = None,
+                    method="auto", stream: Optional[torch.cuda.Stream] = None,
                     cap: Optional[int] = None) -> None:
     """Launch vg_downsample into preallocated buffers (asynchronous, no host sync)."""
     xyz = _cuda_cloud(xyz)
@@ -254,7 +255,7 @@ class Decimation(NamedTuple):
 
 
 def downsample(xyz: torch.Tensor, leaf: float, origin: Optional[torch.Tensor] = None, *,
-               method="sort", point_to_voxel: bool = False, pose=None, z_limits=None,
+               method="auto", point_to_voxel: bool = False, pose=None, z_limits=None,
                attrs=None, min_count: int = 1,
                stream: Optional[torch.cuda.Stream] = None) -> Decimation:
     """Voxel-grid decimation of one cloud: centroid per occupied voxel, key order.
@@ -296,7 +297,7 @@ NOALLOC_MAX_POINTS = 1 << 20
 
 
 def downsample_noalloc(xyz: torch.Tensor, leaf: float, origin: Optional[torch.Tensor] = None, *,
-                       method="sort", point_to_voxel: bool = False,
+                       method="auto", point_to_voxel: bool = False,
                        stream: Optional[torch.cuda.Stream] = None) -> Decimation:
     """vg_downsample_noalloc: decimation whose scratch is the library's static device
     array instead of a workspace (for callers that cannot allocate device memory; the
@@ -385,7 +386,7 @@ def _per_frame(values, F: int, width: int, device) -> Optional[torch.Tensor]:
     return torch.as_tensor(values, dtype=torch.float32).reshape(F, width).to(device).contiguous()
 
 
-def downsample_frames(frames, leaves, origins=None, *, method="sort", point_to_voxel=False,
+def downsample_frames(frames, leaves, origins=None, *, method="auto", point_to_voxel=False,
                       grid_per_sm: int = 0, poses=None, z_limits=None, attrs=None,
                       min_count: int = 1,
                       stream: Optional[torch.cuda.Stream] = None) -> Frames:
@@ -452,7 +453,7 @@ def frames_into(xyz: torch.Tensor, frame_offsets: torch.Tensor, n_frames: int,
                 origins: torch.Tensor, leaves: torch.Tensor, out_keys: torch.Tensor,
                 out_centroids: torch.Tensor, out_counts: torch.Tensor,
                 out_frame_offsets: torch.Tensor, out_error: torch.Tensor,
-                workspace: torch.Tensor, *, origin_from_min: bool = True, method="sort",
+                workspace: torch.Tensor, *, origin_from_min: bool = True, method="auto",
                 poses: Optional[torch.Tensor] = None, z_limits: Optional[torch.Tensor] = None,
                 point_to_voxel: Optional[torch.Tensor] = None,
                 attrs: Optional[torch.Tensor] = None, out_attrs: Optional[torch.Tensor] = None,
@@ -600,7 +601,7 @@ class VoxelMap:
 class Plan:
     """A batch plan (vg_plan): owned workspace, tuned method/grid, CUDA-graph replay."""
 
-    def __init__(self, max_frames: int, max_points: int, method="sort"):
+    def __init__(self, max_frames: int, max_points: int, method="auto"):
         h = ctypes.c_void_p()
         _check(lib().vg_plan_create(ctypes.byref(h), int(max_frames), int(max_points),
                                     method_flag(method)), "vg_plan_create")
@@ -627,7 +628,8 @@ class Plan:
         m, g, w = ctypes.c_int(), ctypes.c_int(), ctypes.c_size_t()
         _check(lib().vg_plan_get(self._h, ctypes.byref(m), ctypes.byref(g), ctypes.byref(w)),
                "vg_plan_get")
-        return {"method": {METHOD_SORT: "sort", METHOD_HASH: "hash"}[m.value],
+        return {"method": {METHOD_AUTO: "auto", METHOD_SORT: "sort",
+                           METHOD_SORT | SORT_LSD: "sort_lsd", METHOD_HASH: "hash"}[m.value],
                 "grid_per_sm": g.value, "workspace_bytes": w.value}
 
     def run(self, xyz, frame_offsets, n_frames, origins, leaves, out_keys, out_centroids,
@@ -645,8 +647,8 @@ class Plan:
     def tune(self, xyz, frame_offsets, n_frames, origins, leaves, out_keys, out_centroids,
              out_counts, out_frame_offsets, out_error, *, origin_from_min=True, reps=5,
              stream: Optional[torch.cuda.Stream] = None):
-        """vg_plan_tune: time sort/hash x grids {4,8,16}; keeps the fastest."""
-        ms = (ctypes.c_float * 6)()
+        """vg_plan_tune: time sort/sort_lsd/hash x grids {4,8,16}; keeps the fastest."""
+        ms = (ctypes.c_float * 9)()
         flags = ORIGIN_FROM_MIN if origin_from_min else 0
         st = lib().vg_plan_tune(
             self._h, _ptr(xyz), xyz.shape[0], _ptr(frame_offsets), int(n_frames), _ptr(origins),
@@ -654,7 +656,7 @@ class Plan:
             out_keys.shape[0], _ptr(out_frame_offsets), _ptr(out_error), flags, int(reps),
             _stream_ptr(stream), ms)
         _check(st, "vg_plan_tune")
-        names = [f"{m}@{g}" for m in ("sort", "hash") for g in (4, 8, 16)]
+        names = [f"{m}@{g}" for m in ("sort", "sort_lsd", "hash") for g in (4, 8, 16)]
         self.last_tuning = dict(zip(names, list(ms)))
         return self.last_tuning
 
@@ -682,12 +684,13 @@ class Plan:
 
 # ---- pyramid (step a6) -----------------------------------------------------------------
 def pyramid(xyz: torch.Tensor, leaf: float, levels: int, origin: Optional[torch.Tensor] = None,
-            *, point_to_voxel: bool = False, method="sort",
+            *, point_to_voxel: bool = False, method="auto",
             stream: Optional[torch.cuda.Stream] = None) -> list:
     """vg_pyramid: level 0 = decimation at ``leaf``, level k+1 = merge of level k by key>>3.
 
-    ``method``: "sort", "sort_lsd" or "sort_bucket" (level 0's grouping).  Returns a list of ``levels``
-    Decimation tuples (point_to_voxel only on level 0).
+    ``method``: "auto", "sort", "sort_lsd" or "sort_bucket" (level 0's grouping; "hash"
+    is refused).  Returns a list of ``levels`` Decimation tuples (point_to_voxel only on
+    level 0).
     """
     xyz = _cuda_cloud(xyz)
     n = xyz.shape[0]
@@ -701,7 +704,7 @@ def pyramid(xyz: torch.Tensor, leaf: float, levels: int, origin: Optional[torch.
     loff = torch.zeros(levels + 1, dtype=torch.int64, device=dev)
     err = torch.zeros(1, dtype=torch.int32, device=dev)
     p2v = torch.empty(max(n, 1), dtype=torch.int32, device=dev) if point_to_voxel else None
-    if method_flag(method) & ~(METHOD_SORT | SORT_BUCKETS | SORT_LSD):
+    if method_flag(method) & ~(METHOD_SORT | SORT_BUCKETS | SORT_LSD):  # (auto = 0 passes)
         raise ValueError("vg_pyramid groups level 0 by sorting")
     flags = (ORIGIN_FROM_MIN if origin is None else 0) | (method_flag(method) &
                                                           (SORT_BUCKETS | SORT_LSD))

@@ -104,7 +104,7 @@ def test_plan_graph_replay_and_tuner():
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):
         times = plan.tune(**b, reps=2, stream=s)
-        assert len(times) == 6 and all(t > 0 for t in times.values())
+        assert len(times) == 9 and all(t > 0 for t in times.values())
         for _ in range(3):  # graph replays
             plan.run(**b, stream=s)
         s.synchronize()
@@ -115,8 +115,9 @@ def test_plan_graph_replay_and_tuner():
     assert torch.equal(b["out_keys"][:v], ref.keys)
     assert torch.equal(b["out_counts"][:v], ref.counts)
     assert torch.equal(b["out_centroids"][:v].view(torch.int32), ref.centroids.view(torch.int32))
-    for m in ("sort", "hash"):
+    for m in ("auto", "sort", "sort_lsd", "hash"):
         plan.configure(m, 8)
+        assert plan.get()["method"] == m
         with torch.cuda.stream(s):
             plan.run(**b, stream=s, graph=False)
             s.synchronize()

@@ -133,36 +133,43 @@ def test_capacity_error_is_reported():
     assert np.array_equal(gpu_keys(buf.keys[:10]), ref.keys[:10])
 
 
-def test_fused_map_full_size_sampled():
-    """50M-point map cloud at leaf 0.02 m: all keys/counts/order exactly, centroids on a
-    sample of voxels, against oracle keys and FP64 means of the member points."""
-    n = 50_000_000
-    xyz = synth.fused_map(n, seed=0)
-    res = run(xyz, 0.02)
+@pytest.fixture(scope="module")
+def fused_map_50m():
+    return synth.fused_map(50_000_000, seed=0)
+
+
+@pytest.mark.parametrize("leaf", [0.02, 0.1])
+def test_fused_map_full_size(fused_map_50m, leaf):
+    """The 50M-point map cloud at both of its leaves, through the library's default
+    (the bucket grouping at this size): origin, every key, count and the order exactly,
+    against the oracle's per-point keys; every centroid within 1e-5 m of the FP64 mean of
+    its member points; at 0.02 m also the global radix sort's rows, bit for bit."""
+    xyz = fused_map_50m
+    res = run(xyz, leaf)
     k_gpu = gpu_keys(res.keys)
     c_gpu = gpu_counts(res.counts)
     o = to_np(res.origin)
     o_ref, nvalid = oracle.origin(xyz)
     assert np.array_equal(o, o_ref)
-    keys, _, valid, st = oracle.keys(xyz, o_ref, 0.02)
+    keys, _, valid, st = oracle.keys(xyz, o_ref, leaf)
     assert st == 0
     kv = keys[valid]
     uniq, inv, cnt = np.unique(kv, return_inverse=True, return_counts=True)
+    del kv
     assert np.array_equal(k_gpu, uniq)
     assert np.array_equal(c_gpu, cnt.astype(np.uint64))
-    rng = np.random.Generator(np.random.PCG64(0))
-    pick = rng.choice(uniq.shape[0], size=20000, replace=False)
-    sel = np.zeros(uniq.shape[0], bool)
-    sel[pick] = True
-    m = sel[inv]
-    pts = xyz[valid][m].astype(np.float64)
-    rows = inv[m]
-    sums = np.zeros((uniq.shape[0], 3))
+    cent = to_np(res.centroids).astype(np.float64)
+    pts = xyz[valid]
+    err = 0.0
     for a in range(3):
-        sums[:, a] = np.bincount(rows, weights=pts[:, a], minlength=uniq.shape[0])
-    want = sums[pick] / cnt[pick, None]
-    err = np.abs(to_np(res.centroids)[pick].astype(np.float64) - want).max()
+        mean = np.bincount(inv, weights=pts[:, a].astype(np.float64),
+                           minlength=uniq.shape[0]) / cnt
+        err = max(err, float(np.abs(cent[:, a] - mean).max()))
     assert err <= 1e-5, err
+    if leaf == 0.02:
+        other = run(xyz, leaf, method="sort_lsd")
+        assert torch.equal(other.keys, res.keys) and torch.equal(other.counts, res.counts)
+        assert torch.equal(other.centroids.view(torch.int32), res.centroids.view(torch.int32))
 
 
 @pytest.mark.parametrize("top,hi", [((2047, 2047, 1023), (2048, 2048, 1024)),

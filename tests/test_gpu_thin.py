@@ -55,3 +55,31 @@ def test_ragged_invalid_and_untouched_clouds():
     assert res.passes == 1
     empty = run(np.zeros((0, 3), np.float32), 0.05, 1, np.zeros(0, np.uint32))
     assert empty.num_kept == 0
+
+
+def test_rgbd_640x480_bench_parameters():
+    """The bench's configuration (640x480 frame, cell 0.05 m, threshold 20, batches of
+    1000): keep flags, kept count and passes against the oracle's result stored in
+    tests/golden/thin_640x480.txt (written by make_thin_golden.py from the oracle alone);
+    if this machine generates a different cloud, the oracle runs here instead."""
+    import hashlib
+    import os
+    import sys
+    golden = os.path.join(os.path.dirname(__file__), "golden")
+    sys.path.insert(0, golden)
+    import make_thin_golden as mk
+    rec = {}
+    with open(os.path.join(golden, "thin_640x480.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                k, v = line.split()
+                rec[k] = v
+    x, pr = mk.inputs()
+    res = run(x, mk.CELL, mk.THRESHOLD, pr, batch=mk.BATCH)
+    keep = res.keep.cpu().numpy().astype(bool)
+    if mk.digest(x) == rec["cloud_sha256"] and mk.digest(pr) == rec["priority_sha256"]:
+        assert res.passes == int(rec["passes"]) and res.num_kept == int(rec["kept"])
+        assert mk.digest(np.packbits(keep)) == rec["keep_sha256"]
+    else:  # (the stored result belongs to another cloud)
+        ref, passes, st = oracle.thin(x, mk.CELL, mk.THRESHOLD, pr, batch=mk.BATCH)
+        assert st == 0 and res.passes == passes and np.array_equal(keep, ref)
