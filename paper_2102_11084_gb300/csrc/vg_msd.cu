@@ -721,38 +721,54 @@ __global__ __launch_bounds__(1024) void msd_plan_kernel(State* st, const uint32_
 constexpr int kBkThreads = VG_BK_THREADS;
 constexpr int kBkWarps = kBkThreads / 32;
 constexpr int kBkItems = kBkStage / kBkThreads;
+constexpr int kBkPer = kBkWords / kBkThreads;  // bitmap words per thread
 constexpr int kSlotMax = 256;  // keys of an oversized window (one coarse range)
+// A cell's first kSumSplit entries are summed in 32 bits (kSumSplit biased 21-bit offsets
+// stay below 2^32).  A job holds at most kBkStage < 2 kSumSplit entries, so at most one of
+// its cells has more; their further entries go into one 64-bit sum per axis.
+constexpr uint32_t kSumSplit = 2048;
 static_assert(kBkStage % kBkThreads == 0, "bucket stage");
 static_assert(kBkWords % kBkThreads == 0, "bucket bitmap");
-static_assert(kBkStage < 65536, "16-bit cell counts and offsets");
-static_assert(kSlotMax <= kBkThreads && 3 * kSlotMax <= kBkStage + 2, "slots fit a buffer");
+static_assert(kBkStage < 2 * int(kSumSplit), "at most one cell per job above the 32-bit sums");
+static_assert(uint64_t(kSumSplit) * 0x1fffffu <= 0xffffffffull, "32-bit sums");
+static_assert(kBkStage < 65536, "16-bit ranks and key offsets");
+static_assert(kSlotMax <= kBkThreads && 6 * kSlotMax <= 3 * kBkStage, "slots fit the sums");
+static_assert(kBkWarps <= 32, "one warp scans the warp totals");
 
-struct BkSmem {
-  uint32_t keys[2][kBkStage + 4];           // staged keys, from a 16-byte boundary
-  unsigned long long pay[2][kBkStage + 2];  // staged payloads, from a 16-byte boundary
-  uint32_t bits[kBkWords];                  // occupancy of the job's key range
-  uint16_t rank[kBkWords];                  // occupied cells before each word
-  uint32_t cnt2[kBkStage / 2];              // entries per cell, two 16-bit counters a word
-  uint16_t vstart[kBkStage];                // first entry of each cell (cell order)
-  uint16_t vkey[kBkStage];                  // key offset of each cell in the job's range
-  uint32_t tmp[kBkWarps];
-  unsigned long long bar[2];
-  Job job[2];
-  uint32_t jid[2];
-};
-static_assert(offsetof(BkSmem, keys) % 16 == 0 && (sizeof(uint32_t) * (kBkStage + 4)) % 16 == 0,
-              "key stage buffers on 16-byte boundaries");
-static_assert(offsetof(BkSmem, pay) % 16 == 0 && (8 * (kBkStage + 2)) % 16 == 0,
-              "payload stage buffers on 16-byte boundaries");
-static_assert(offsetof(BkSmem, bar) % 8 == 0, "mbarrier alignment");
-static_assert((sizeof(BkSmem) + 1024) * VG_BK_MINB <= 228 * 1024, "bucket block shared memory");
-
+// Origin and leaf of a single frame (o1, leaf1), else each row's frame from fs.
 struct RowCtx {
   const FrameState* fs;
   uint32_t key_shift;
   float o1[3];
   float leaf1;
 };
+
+struct BkSmem {
+  uint32_t keys[kBkStage + 4];           // staged keys, from a 16-byte boundary
+  unsigned long long pay[kBkStage + 2];  // staged payloads, from a 16-byte boundary
+  unsigned long long big[4];             // 64-bit sums past kSumSplit entries (kept zero)
+  uint32_t bits[2][kBkWords];            // occupancy bitmaps of alternate jobs (kept clean)
+  uint32_t cnt[kBkStage];                // entries per cell (kept zero)
+  uint32_t sum[3][kBkStage];             // biased offset sums per cell and axis (kept zero)
+  uint16_t rank[kBkWords];               // occupied cells before each word
+  uint16_t vkey[kBkStage];               // key offset of each cell in the job's range
+  uint32_t tmp[kBkWarps];
+  unsigned long long bar[2];             // [0] key copies, [1] payload copies
+  Job job[2];                            // this job and the next (alternating slots)
+  Job ahd;                               // the one after (copied in asynchronously)
+  uint32_t jid[2];
+  RowCtx rc;
+};
+static_assert(offsetof(BkSmem, keys) % 16 == 0 && (sizeof(uint32_t) * (kBkStage + 4)) % 16 == 0,
+              "key stage buffer on a 16-byte boundary");
+static_assert(offsetof(BkSmem, pay) % 16 == 0 && (8 * (kBkStage + 2)) % 16 == 0,
+              "payload stage buffer on a 16-byte boundary");
+static_assert(offsetof(BkSmem, sum) % 8 == 0, "oversized windows sum in 64 bits there");
+static_assert(offsetof(BkSmem, bar) % 8 == 0, "mbarrier alignment");
+static_assert(offsetof(BkSmem, job) % 16 == 0 && offsetof(BkSmem, ahd) % 16 == 0 &&
+                  sizeof(Job) == 32,
+              "descriptors copied in 16-byte pieces");
+static_assert((sizeof(BkSmem) + 1024) * VG_BK_MINB <= 228 * 1024, "bucket block shared memory");
 
 // Row `cur`: cell `key` (the full sort key) with n entries whose offsets sum to s.
 __device__ __forceinline__ void put_row(const RowCtx& rc, const SegOut& out, uint32_t cur,
@@ -841,6 +857,18 @@ __device__ __forceinline__ Job job_load(uint32_t q, uint32_t nwin, uint32_t njob
   return Job{a.x, a.y, a.z, a.w, b.x, b.y, b.z, 0u};
 }
 
+// The same, copied into *dst asynchronously (complete after cp_async_wait_all).
+__device__ __forceinline__ void job_fetch(Job* dst, uint32_t q, uint32_t nwin, uint32_t njobs,
+                                          const uint32_t* jobsw, const uint32_t* jobsm) {
+  if (q >= njobs) {
+    *dst = Job{0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+    return;
+  }
+  const uint32_t* p = q < nwin ? jobsw + size_t(q) * kJobWords : jobsm + size_t(q - nwin) * kJobWords;
+  cp_async16(dst, p);
+  cp_async16(reinterpret_cast<uint32_t*>(dst) + 4, p + 4);
+}
+
 __device__ __forceinline__ bool staged_by_copy(const Job& j) {
   return j.mw <= uint32_t(kBkStage);
 }
@@ -853,35 +881,36 @@ struct Bufs {
   const uint64_t* PS;
 };
 
-// Bulk copies of a job's keys and payloads into buffer b, from the 16-byte boundaries at
-// or below its first entry, in whole granules.
-__device__ __forceinline__ void issue_stage(BkSmem& sm, int b, const Bufs& bf, const Job& d) {
+
+// Bulk copies of a job's keys (barrier 0) or payloads (barrier 1) into the stage buffer,
+// from the 16-byte boundary at or below its first entry, in whole granules.
+__device__ __forceinline__ void issue_keys(BkSmem& sm, const Bufs& bf, const Job& d) {
   const uint32_t* K = d.scratch ? bf.KS : bf.K;
-  const uint64_t* P = d.scratch ? bf.PS : bf.P;
   const uint32_t kg = ((d.start & 3u) + d.mw + 3u) >> 2;  // 16-byte granules of keys
+  mbar_arrive_expect_tx(&sm.bar[0], 16u * kg);
+  bulk_copy_g2s(sm.keys, K + (d.start & ~3u), 16u * kg, &sm.bar[0]);
+}
+__device__ __forceinline__ void issue_pays(BkSmem& sm, const Bufs& bf, const Job& d) {
+  const uint64_t* P = d.scratch ? bf.PS : bf.P;
   const uint32_t pg = ((d.start & 1u) + d.mw + 1u) >> 1;  // 16-byte granules of payloads
-  mbar_arrive_expect_tx(&sm.bar[b], 16u * (kg + pg));
-  bulk_copy_g2s(sm.keys[b], K + (d.start & ~3u), 16u * kg, &sm.bar[b]);
-  bulk_copy_g2s(sm.pay[b], P + (d.start & ~1u), 16u * pg, &sm.bar[b]);
+  mbar_arrive_expect_tx(&sm.bar[1], 16u * pg);
+  bulk_copy_g2s(sm.pay, P + (d.start & ~1u), 16u * pg, &sm.bar[1]);
 }
 
 // An oversized window: at most kSlotMax keys, any number of entries (contiguous in the
-// job's buffer); one shared-memory slot per key (count, three 64-bit sums), warp sums
-// first when a whole warp meets one key.
-__device__ __forceinline__ void slot_window(BkSmem& sm, int b, const Bufs& bf, const Job& d,
+// job's buffer), read from global memory; one slot per key (the cell counters and, as
+// 64-bit words, the first sums), warp sums first when a whole warp meets one key.  Leaves
+// the slots zero again.
+__device__ __forceinline__ void slot_window(BkSmem& sm, const Bufs& bf, const Job& d,
                                             uint32_t row0, const RowCtx& rc, const SegOut& out,
                                             int* err) {
   const uint32_t* __restrict__ K = d.scratch ? bf.KS : bf.K;
   const uint64_t* __restrict__ P = d.scratch ? bf.PS : bf.P;
   const int t = threadIdx.x, lane = t & 31;
-  uint32_t* wcnt = sm.keys[b];
-  unsigned long long* wsum = sm.pay[b];  // [3][kSlotMax]
-  const uint32_t span = d.span;          // <= kSlotMax
-  if (uint32_t(t) < span) {
-    wcnt[t] = 0;
-    wsum[t] = wsum[kSlotMax + t] = wsum[2 * kSlotMax + t] = 0;
-  }
-  __syncthreads();
+  uint32_t* wcnt = sm.cnt;
+  unsigned long long* wsum = reinterpret_cast<unsigned long long*>(&sm.sum[0][0]);  // [3][256]
+  const uint32_t span = d.span;  // <= kSlotMax
+  __syncthreads();  // the job before has read and cleared the slots
   for (uint32_t i0 = 0; i0 < d.mw; i0 += 4u * kBkThreads) {
     uint32_t k[4];
 #pragma unroll
@@ -924,23 +953,32 @@ __device__ __forceinline__ void slot_window(BkSmem& sm, int b, const Bufs& bf, c
   __syncthreads();
   // rows of the occupied keys, in key order
   const uint32_t n = uint32_t(t) < span ? wcnt[t] : 0u;
+  Acc a;
+  a.n = n;
+  a.s[0] = a.s[1] = a.s[2] = 0;
+  if (uint32_t(t) < span) {
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+      a.s[x] = static_cast<long long>(wsum[x * kSlotMax + t]);
+      wsum[x * kSlotMax + t] = 0;
+    }
+    wcnt[t] = 0;
+  }
   uint32_t unused;
   const uint32_t r = block_excl_scan(n ? 1u : 0u, &unused, sm.tmp);
-  if (n) {
-    Acc a;
-    a.n = n;
-    a.s[0] = static_cast<long long>(wsum[t]);
-    a.s[1] = static_cast<long long>(wsum[kSlotMax + t]);
-    a.s[2] = static_cast<long long>(wsum[2 * kSlotMax + t]);
-    put_row(rc, out, row0 + r, d.key_lo + uint32_t(t), a, err);
-  }
-  fence_proxy_async();  // this thread's accesses of buffer b precede later bulk copies
-  __syncthreads();
+  if (n) put_row(rc, out, row0 + r, d.key_lo + uint32_t(t), a, err);
 }
 
-// Block b runs jobs b, b + G, ... (the windows first: the larger jobs); a job's entries are
-// copied into one buffer while the job before is reduced from the other, and its
-// descriptor is read two jobs ahead.
+// Block b runs jobs b, b + G, ... (the windows first: the larger jobs).  A job's keys are
+// copied in while the job before ranks its entries, and its payloads while the job before
+// writes its rows; descriptors are read two jobs ahead.  Per job:
+//   1. every thread waits for the keys and marks its entries' key offsets in the job's
+//      occupancy bitmap (two bitmaps, alternate jobs: one is cleared while the other fills);
+//   2. the prefix popcounts of the bitmap's words: every cell's rank, in key order;
+//   3. every thread waits for the payloads and adds each entry into its cell's counter and
+//      per-axis sums (shared-memory atomics; integers, so the order does not matter);
+//   4. one thread per cell writes its row and clears its counter and sums.
+// Four barriers a job; counters, sums and bitmaps are left clean for the next one.
 __global__ __launch_bounds__(kBkThreads, VG_BK_MINB) void msd_bucket_kernel(
     State* st, const FrameState* __restrict__ fs, const uint32_t* k0, const uint64_t* p0,
     const uint32_t* k1, const uint64_t* p1, const uint32_t* __restrict__ jobsw,
@@ -955,174 +993,197 @@ __global__ __launch_bounds__(kBkThreads, VG_BK_MINB) void msd_bucket_kernel(
   // the last partition pass's output, and the other buffer (windows of large buckets)
   const Bufs bf{two ? k0 : k1, two ? p0 : p1, two ? k1 : k0, two ? p1 : p0};
   const uint32_t G = gridDim.x;
-  const int t = threadIdx.x;
-  RowCtx rc;
-  rc.fs = fs;
-  rc.key_shift = st->key_shift;
-  rc.o1[0] = fs[0].origin[0];
-  rc.o1[1] = fs[0].origin[1];
-  rc.o1[2] = fs[0].origin[2];
-  rc.leaf1 = fs[0].leaf;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const RowCtx& rc = sm.rc;
 
-  for (int w = t; w < kBkWords; w += kBkThreads) sm.bits[w] = 0;  // kept clean after each job
-  Job ahead{};  // thread 0: the job after the next one
+  for (int i = t; i < kBkStage; i += kBkThreads) {
+    sm.cnt[i] = 0;
+    sm.sum[0][i] = sm.sum[1][i] = sm.sum[2][i] = 0;
+  }
+  for (int w = t; w < 2 * kBkWords; w += kBkThreads) sm.bits[w / kBkWords][w % kBkWords] = 0;
+  if (t < 4) sm.big[t] = 0;
+  // thread 0 keeps the job numbers: slot s holds job jid[s] (this one), slot s ^ 1 the
+  // next (whose copies are issued during this one), ahd the one after (jid qa)
   uint32_t qa = 0;
   if (t == 0) {
+    sm.rc.fs = fs;
+    sm.rc.key_shift = st->key_shift;
+    sm.rc.o1[0] = fs[0].origin[0];
+    sm.rc.o1[1] = fs[0].origin[1];
+    sm.rc.o1[2] = fs[0].origin[2];
+    sm.rc.leaf1 = fs[0].leaf;
     mbar_init(&sm.bar[0], 1);
     mbar_init(&sm.bar[1], 1);
     fence_mbar_init();
-    const uint32_t q = blockIdx.x;
+    const uint32_t q = blockIdx.x, qn = q + G;
     sm.jid[0] = q;
     sm.job[0] = job_load(q, nwin, njobs, jobsw, jobsm);
-    if (staged_by_copy(sm.job[0])) issue_stage(sm, 0, bf, sm.job[0]);
-    qa = q + G;
-    ahead = job_load(qa, nwin, njobs, jobsw, jobsm);
+    if (staged_by_copy(sm.job[0])) {
+      issue_keys(sm, bf, sm.job[0]);
+      issue_pays(sm, bf, sm.job[0]);
+    }
+    sm.jid[1] = qn;
+    sm.job[1] = job_load(qn, nwin, njobs, jobsw, jobsm);
+    qa = qn < njobs ? qn + G : qn;
+    job_fetch(&sm.ahd, qa, nwin, njobs, jobsw, jobsm);
   }
   __syncthreads();
-  uint32_t phase = 0;  // bit b: parity of buffer b's next completion
-  for (int b = 0;; b ^= 1) {
-    const uint32_t q = sm.jid[b];
+  uint32_t par = 0;  // parity of both copy barriers' next completion
+  int jb = 0;        // the bitmap of the next staged job
+  for (int s = 0;; s ^= 1) {
+    const uint32_t q = sm.jid[s];
     if (q >= njobs) break;
-    const Job d = sm.job[b];
+    const Job d = sm.job[s];
     // this job's first row (a window's: its bucket's first row plus its first cell's rank)
     const uint32_t row0 = d.row + (d.bj != kJobRun ? vbase[d.bj] : 0u);
-    // the next job: its descriptor (read one job ago) into the other slot, its copy into
-    // the other buffer (whose reads by this block ended at the last job's final barrier),
-    // and the descriptor of the one after it
-    if (t == 0) {
-      sm.jid[b ^ 1] = qa;
-      sm.job[b ^ 1] = ahead;
-      if (qa < njobs && staged_by_copy(ahead)) {
-        fence_proxy_async();
-        issue_stage(sm, b ^ 1, bf, ahead);
+    const Job& nxt = sm.job[s ^ 1];  // (thread 0 issues its copies)
+    const bool nxt_copy = t == 0 && sm.jid[s ^ 1] < njobs && staged_by_copy(nxt);
+    if (!staged_by_copy(d)) {  // an oversized window: nothing of it is staged
+      if (nxt_copy) {
+        issue_keys(sm, bf, nxt);
+        issue_pays(sm, bf, nxt);
       }
-      qa = qa < njobs ? qa + G : qa;
-      ahead = job_load(qa, nwin, njobs, jobsw, jobsm);
-    }
-    if (!staged_by_copy(d)) {  // an oversized window (nothing was copied for it)
-      slot_window(sm, b, bf, d, row0, rc, out, err);
-      continue;  // (ends on a barrier)
-    }
-    const uint32_t* sk;
-    const unsigned long long* sp;
-    const uint32_t m = d.mw;
-    {
-      bool ok = true;
-      const uint32_t par = (phase >> b) & 1u;
-      if (t < 32) ok = mbar_wait(&sm.bar[b], par, kDefaultSpinLimit);
-      phase ^= 1u << b;
+      slot_window(sm, bf, d, row0, rc, out, err);
+    } else {
+      const uint32_t m = d.mw;
+      const uint32_t* sk = sm.keys + (d.start & 3u);
+      const unsigned long long* sp = sm.pay + (d.start & 1u);
+      uint32_t* bits = sm.bits[jb];
+      const int nw = int((d.span + 31u) >> 5);
+      // (item loops stop at the job's entries: the break is the same in every thread)
+
+      // 1. the keys, and the occupancy bitmap of the job's key range
+      bool ok = mbar_wait(&sm.bar[0], par, kDefaultSpinLimit);
+      uint32_t kl[kBkItems];
+#pragma unroll
+      for (int q2 = 0; q2 < kBkItems; ++q2) {
+        kl[q2] = kFull;
+        if (uint32_t(q2) * kBkThreads >= m) break;
+        const uint32_t i = uint32_t(q2) * kBkThreads + uint32_t(t);
+        kl[q2] = i < m ? sk[i] - d.key_lo : kFull;
+        if (kl[q2] != kFull) atomicOr(&bits[kl[q2] >> 5], 1u << (kl[q2] & 31u));
+      }
+      fence_proxy_async();  // this thread's reads of the key buffer precede the next copy
       if (__syncthreads_or(!ok)) {  // a copy that never completed: report, drain, stop
         if (t == 0) {
           set_error(err, kErrTimeout);
-          mbar_wait(&sm.bar[b], par, kDefaultSpinLimit);
-          if (sm.jid[b ^ 1] < njobs && staged_by_copy(sm.job[b ^ 1]))
-            mbar_wait(&sm.bar[b ^ 1], (phase >> (b ^ 1)) & 1u, kDefaultSpinLimit);
+          mbar_wait(&sm.bar[0], par, kDefaultSpinLimit);
+          mbar_wait(&sm.bar[1], par, kDefaultSpinLimit);
+          cp_async_wait_all();
         }
         return;
       }
-      sk = sm.keys[b] + (d.start & 3u);
-      sp = sm.pay[b] + (d.start & 1u);
-    }
-    unsigned long long* spo = sm.pay[b];  // the payloads in cell order, from entry 0
-    const int nw = int((d.span + 31u) >> 5);
-    // (item loops stop at the job's entries: the break is the same in every thread)
+      if (nxt_copy) issue_keys(sm, bf, nxt);
 
-    // 1. occupancy bitmap of the job's key range (clean since the last job)
-    uint32_t kl[kBkItems];
+      // 2. cells before every word (exclusive prefix of the popcounts) and the cell count
+      uint32_t pc[kBkPer], mine = 0;
 #pragma unroll
-    for (int q2 = 0; q2 < kBkItems; ++q2) {
-      kl[q2] = kFull;
-      if (uint32_t(q2) * kBkThreads >= m) break;
-      const uint32_t i = uint32_t(q2) * kBkThreads + uint32_t(t);
-      kl[q2] = i < m ? sk[i] - d.key_lo : kFull;
-      if (kl[q2] != kFull) atomicOr(&sm.bits[kl[q2] >> 5], 1u << (kl[q2] & 31u));
-    }
-    __syncthreads();
-    // 2. cell ranks and count
-    const uint32_t V = bitmap_popc<kBkThreads>(sm.bits, sm.rank, nw, true, sm.tmp);
-    for (uint32_t i = t; i < (V + 1) / 2; i += kBkThreads) sm.cnt2[i] = 0;
-    __syncthreads();
-    // 3. every entry's cell and its place among the cell's entries (any order)
-    uint32_t rc16[kBkItems];
-#pragma unroll
-    for (int q2 = 0; q2 < kBkItems; ++q2) {
-      rc16[q2] = kFull;
-      if (uint32_t(q2) * kBkThreads >= m) break;
-      if (kl[q2] != kFull) {
-        const uint32_t r = rank_of(sm.bits, sm.rank, kl[q2]);
-        const uint32_t sh = 16u * (r & 1u);
-        const uint32_t old = atomicAdd(&sm.cnt2[r >> 1], 1u << sh);
-        rc16[q2] = (r << 16) | ((old >> sh) & 0xffffu);
+      for (int q2 = 0; q2 < kBkPer; ++q2) {
+        const int w = kBkPer * t + q2;
+        pc[q2] = w < nw ? __popc(bits[w]) : 0u;
+        mine += pc[q2];
       }
-    }
-    __syncthreads();
-    // 4. first entry of every cell: exclusive scan of the counts; thread t takes the cells
-    //    [cpt t, cpt t + cpt), cpt = the cells per thread this job needs
-    {
-      const uint32_t cpt = (V + kBkThreads - 1) / kBkThreads;  // <= kBkItems
-      uint32_t vc[kBkItems], mine = 0;
+      uint32_t inc = mine;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, inc, off);
+        if (lane >= off) inc += y;
+      }
+      if (lane == 31) sm.tmp[warp] = inc;
+      __syncthreads();
+      uint32_t wt = lane < kBkWarps ? sm.tmp[lane] : 0u;
+#pragma unroll
+      for (int off = 1; off < kBkWarps; off <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, wt, off);
+        if (lane >= off) wt += y;
+      }
+      const uint32_t V = __shfl_sync(kFull, wt, kBkWarps - 1);
+      const uint32_t wex = __shfl_sync(kFull, wt, (warp + 31) & 31);
+      uint32_t run = (warp ? wex : 0u) + inc - mine;
+#pragma unroll
+      for (int q2 = 0; q2 < kBkPer; ++q2) {
+        const int w = kBkPer * t + q2;
+        if (w < nw) sm.rank[w] = static_cast<uint16_t>(run);
+        run += pc[q2];
+      }
+      __syncthreads();
+
+      // 3. the payloads, into their cells' counters and sums
+      ok = mbar_wait(&sm.bar[1], par, kDefaultSpinLimit);
 #pragma unroll
       for (int q2 = 0; q2 < kBkItems; ++q2) {
-        vc[q2] = 0;
-        if (uint32_t(q2) >= cpt) break;
-        const uint32_t r = cpt * uint32_t(t) + uint32_t(q2);
-        vc[q2] = r < V ? (sm.cnt2[r >> 1] >> (16u * (r & 1u))) & 0xffffu : 0u;
-        mine += vc[q2];
-      }
-      uint32_t unused;
-      uint32_t run = block_excl_scan(mine, &unused, sm.tmp);
+        if (uint32_t(q2) * kBkThreads >= m) break;
+        if (kl[q2] != kFull) {
+          const uint32_t i = uint32_t(q2) * kBkThreads + uint32_t(t);
+          const uint32_t r = rank_of(bits, sm.rank, kl[q2]);
+          const uint64_t p = sp[i];
+          const uint32_t f[3] = {uint32_t(p) & 0x1fffffu, uint32_t(p >> 21) & 0x1fffffu,
+                                 uint32_t(p >> 42) & 0x1fffffu};
+          const uint32_t old = atomicAdd(&sm.cnt[r], 1u);
+          if (old < kSumSplit) {
 #pragma unroll
-      for (int q2 = 0; q2 < kBkItems; ++q2) {
-        if (uint32_t(q2) >= cpt) break;
-        const uint32_t r = cpt * uint32_t(t) + uint32_t(q2);
-        if (r < V) sm.vstart[r] = static_cast<uint16_t>(run);
-        run += vc[q2];
-      }
-    }
-    // 5. payloads into cell order, in place
-    unsigned long long pv[kBkItems];
+            for (int a = 0; a < 3; ++a) atomicAdd(&sm.sum[a][r], f[a]);
+          } else {
 #pragma unroll
-    for (int q2 = 0; q2 < kBkItems; ++q2) {
-      pv[q2] = 0ull;
-      if (uint32_t(q2) * kBkThreads >= m) break;
-      const uint32_t i = uint32_t(q2) * kBkThreads + uint32_t(t);
-      pv[q2] = i < m ? sp[i] : 0ull;
-    }
-    __syncthreads();
+            for (int a = 0; a < 3; ++a) atomicAdd(&sm.big[a], static_cast<unsigned long long>(f[a]));
+          }
+          if (old == 0) sm.vkey[r] = static_cast<uint16_t>(kl[q2]);
+        }
+      }
+      fence_proxy_async();  // this thread's reads of the payload buffer precede the next copy
+      if (__syncthreads_or(!ok)) {
+        if (t == 0) {
+          set_error(err, kErrTimeout);
+          mbar_wait(&sm.bar[1], par, kDefaultSpinLimit);
+          if (nxt_copy) mbar_wait(&sm.bar[0], par ^ 1u, kDefaultSpinLimit);
+          cp_async_wait_all();
+        }
+        return;
+      }
+      if (nxt_copy) issue_pays(sm, bf, nxt);
+      par ^= 1u;
+
+      // 4. one row per cell (biased sums, the bias removed once); clean up for the next job
+      for (uint32_t r = t; r < V; r += kBkThreads) {
+        const uint32_t n = sm.cnt[r];
+        unsigned long long b[3];
 #pragma unroll
-    for (int q2 = 0; q2 < kBkItems; ++q2) {
-      if (uint32_t(q2) * kBkThreads >= m) break;
-      if (rc16[q2] != kFull) {
-        const uint32_t r = rc16[q2] >> 16, c = rc16[q2] & 0xffffu;
-        spo[sm.vstart[r] + c] = pv[q2];
-        if (c == 0) sm.vkey[r] = static_cast<uint16_t>(kl[q2]);
+        for (int a = 0; a < 3; ++a) {
+          b[a] = sm.sum[a][r];
+          sm.sum[a][r] = 0;
+        }
+        sm.cnt[r] = 0;
+        if (n > kSumSplit) {
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            b[a] += sm.big[a];
+            sm.big[a] = 0;
+          }
+        }
+        const long long bias = static_cast<long long>(n) * kQMin;
+        const long long sums[3] = {static_cast<long long>(b[0]) + bias,
+                                   static_cast<long long>(b[1]) + bias,
+                                   static_cast<long long>(b[2]) + bias};
+        put_row32(rc, out, row0 + r, d.key_lo + sm.vkey[r], n, sums, err);
       }
-    }
-    __syncthreads();
-    // 6. one row per cell
-    for (uint32_t r = t; r < V; r += kBkThreads) {
-      const uint32_t e0 = sm.vstart[r];
-      const uint32_t n = (sm.cnt2[r >> 1] >> (16u * (r & 1u))) & 0xffffu;
-      // biased offsets summed in 64 bits (at most kBkStage of 21 bits), bias removed once
-      unsigned long long b[3] = {0, 0, 0};
-      for (uint32_t e = e0; e < e0 + n; ++e) {
-        const uint64_t w = spo[e];
-        b[0] += w & 0x1fffffu;
-        b[1] += (w >> 21) & 0x1fffffu;
-        b[2] += (w >> 42) & 0x1fffffu;
+#pragma unroll
+      for (int q2 = 0; q2 < kBkPer; ++q2) {
+        const int w = kBkPer * t + q2;
+        if (w < nw) bits[w] = 0;
       }
-      const long long bias = static_cast<long long>(n) * kQMin;
-      const long long sums[3] = {static_cast<long long>(b[0]) + bias,
-                                 static_cast<long long>(b[1]) + bias,
-                                 static_cast<long long>(b[2]) + bias};
-      put_row32(rc, out, row0 + r, d.key_lo + sm.vkey[r], n, sums, err);
+      jb ^= 1;
     }
-    // the bitmap clean for the next job (nothing reads it after step 3)
-    for (int w = t; w < nw; w += kBkThreads) sm.bits[w] = 0;
-    fence_proxy_async();  // this thread's accesses of buffer b precede later bulk copies
-    __syncthreads();
+    if (t == 0) {  // slot s takes the job after the next; every thread has read this one
+      cp_async_wait_all();
+      sm.jid[s] = qa;
+      sm.job[s] = sm.ahd;
+      qa = qa < njobs ? qa + G : qa;
+      job_fetch(&sm.ahd, qa, nwin, njobs, jobsw, jobsm);
+    }
   }
+  if (t == 0) cp_async_wait_all();  // (nothing is in flight: the jobs past the last are empty)
 }
+
 
 constexpr size_t kBkSmem = sizeof(BkSmem);
 
