@@ -42,7 +42,10 @@ constexpr int kSortMinBlocks = VG_SORT_MINB;
 constexpr int kMsdMaxLow = 16;                 // largest bucket-local key width
 constexpr int kMsdMaxTop = 16;                 // largest bucket id width (two 8-bit levels)
 constexpr int kMsdBuckets = 1 << kMsdMaxTop;   // bucket ids
-constexpr int kMsdTarget = 2048;               // average points per bucket the split aims at
+#ifndef VG_MSD_TARGET
+#define VG_MSD_TARGET 2048
+#endif
+constexpr int kMsdTarget = VG_MSD_TARGET;               // average points per bucket the split aims at
 // Clouds from this many points on take the bucket grouping under VG_METHOD_AUTO; smaller
 // ones (camera frames, whose dense surfaces make large buckets of few cells) take the
 // global radix sort, which is faster there (measured: a 640x480 frame 0.10 vs 0.20 ms,

@@ -802,11 +802,11 @@ __device__ __forceinline__ void put_row(const RowCtx& rc, const SegOut& out, uin
 }
 
 // Row `cur` of a 32-bit key: the same operations as put_row (acc_centroid), with the
-// key's indices de-interleaved in 32-bit words and the offset sums converted from 32-bit
-// integers when they fit (the same integers, so the same floats).
+// key's indices de-interleaved in 32-bit words; sf = the offset sums, already converted
+// to binary32 (round to nearest, as acc_centroid converts them).
 __device__ __forceinline__ void put_row32(const RowCtx& rc, const SegOut& out, uint32_t cur,
-                                          uint32_t key, uint32_t n, const long long s[3],
-                                          int* err) {
+                                          uint32_t key, uint32_t n, const float sf[3],
+                                          const long long* s64, int* err) {
   if (int64_t(cur) >= out.cap) {
     set_error(err, kErrCapacity);
     return;
@@ -826,13 +826,11 @@ __device__ __forceinline__ void put_row32(const RowCtx& rc, const SegOut& out, u
     scale = __fmul_rn(leaf, __int_as_float((127 - 20 - (__ffs(int(n)) - 1)) << 23));
   else
     scale = __fdiv_rn(leaf, __fmul_rn(__uint2float_rn(n), kQuantScale));
-  const bool fits = n <= 1024u;  // |sum| < 1024 * 1.5 * 2^20 < 2^31
   float c[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     const float corner = __fadd_rn(o[a], __fmul_rn(__uint2float_rn(compact3_32(local >> a)), leaf));
-    const float sf = fits ? __int2float_rn(int(s[a])) : __ll2float_rn(s[a]);
-    c[a] = __fadd_rn(corner, __fmul_rn(sf, scale));
+    c[a] = __fadd_rn(corner, __fmul_rn(sf[a], scale));
   }
   out.keys[cur] = local;
   out.counts[cur] = n;
@@ -840,9 +838,9 @@ __device__ __forceinline__ void put_row32(const RowCtx& rc, const SegOut& out, u
   out.centroids[3 * size_t(cur) + 1] = c[1];
   out.centroids[3 * size_t(cur) + 2] = c[2];
   if (out.sums) {
-    out.sums[3 * size_t(cur)] = s[0];
-    out.sums[3 * size_t(cur) + 1] = s[1];
-    out.sums[3 * size_t(cur) + 2] = s[2];
+    out.sums[3 * size_t(cur)] = s64[0];
+    out.sums[3 * size_t(cur) + 1] = s64[1];
+    out.sums[3 * size_t(cur) + 2] = s64[2];
   }
 }
 
@@ -1143,28 +1141,40 @@ __global__ __launch_bounds__(kBkThreads, VG_BK_MINB) void msd_bucket_kernel(
       if (nxt_copy) issue_pays(sm, bf, nxt);
       par ^= 1u;
 
-      // 4. one row per cell (biased sums, the bias removed once); clean up for the next job
+      // 4. one row per cell (biased sums, the bias n * kQMin removed once); clean up for
+      //    the next job.  Up to 1024 entries the unbiased sum fits 32 bits (|s| < 1.5 2^30),
+      //    and the 32-bit difference of the biased sum and n 2^19 is that exact integer.
       for (uint32_t r = t; r < V; r += kBkThreads) {
         const uint32_t n = sm.cnt[r];
-        unsigned long long b[3];
+        uint32_t b[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
           b[a] = sm.sum[a][r];
           sm.sum[a][r] = 0;
         }
         sm.cnt[r] = 0;
-        if (n > kSumSplit) {
+        float sf[3];
+        long long s64[3];
+        if (n <= 1024u) {
 #pragma unroll
           for (int a = 0; a < 3; ++a) {
-            b[a] += sm.big[a];
-            sm.big[a] = 0;
+            const int s32 = static_cast<int>(b[a] - (n << 19));
+            sf[a] = __int2float_rn(s32);
+            s64[a] = s32;
+          }
+        } else {
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            unsigned long long bb = b[a];
+            if (n > kSumSplit) {
+              bb += sm.big[a];
+              sm.big[a] = 0;
+            }
+            s64[a] = static_cast<long long>(bb) + static_cast<long long>(n) * kQMin;
+            sf[a] = __ll2float_rn(s64[a]);
           }
         }
-        const long long bias = static_cast<long long>(n) * kQMin;
-        const long long sums[3] = {static_cast<long long>(b[0]) + bias,
-                                   static_cast<long long>(b[1]) + bias,
-                                   static_cast<long long>(b[2]) + bias};
-        put_row32(rc, out, row0 + r, d.key_lo + sm.vkey[r], n, sums, err);
+        put_row32(rc, out, row0 + r, d.key_lo + sm.vkey[r], n, sf, s64, err);
       }
 #pragma unroll
       for (int q2 = 0; q2 < kBkPer; ++q2) {

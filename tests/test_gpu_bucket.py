@@ -1,6 +1,7 @@
-"""The bucket grouping of the narrow sort path (the default "sort" method for 32-bit
-keys: partition passes over the top key bits, then every bucket reduced in one block's
-shared memory through an occupancy bitmap of its low key bits): the same rows as the
+"""The bucket grouping of the narrow sort path (method "sort" for 32-bit keys, and "auto"
+from 2^22 points: partition passes over the top key bits, then every bucket reduced in
+one block's shared memory through an occupancy bitmap of its low key bits): the same
+rows as the
 oracle and, bit for bit, as the global LSD radix sort with its segmented reduction
 (method "sort_lsd"), for buckets of one key, of at most 8 and of more than 8 low bits,
 one and two partition passes, buckets larger than a block stages (streamed in windows
@@ -30,7 +31,7 @@ def same_rows(a, b):
 def check(x, leaf, origin=None):
     ref = oracle.downsample(x, leaf, origin)
     org = None if origin is None else torch.from_numpy(origin).cuda()
-    got = vg.downsample(cuda(x), leaf, org)
+    got = vg.downsample(cuda(x), leaf, org, method="sort")
     assert_decimation_equal(got, ref, check_p2v=False)
     org2 = None if origin is None else torch.from_numpy(origin).cuda()
     same_rows(got, vg.downsample(cuda(x), leaf, org2, method="sort_lsd"))
@@ -106,7 +107,7 @@ def test_batched_frames_match_full_sort():
     frames.append(np.zeros((0, 3), np.float32))
     frames.append(synth.random_cloud(5000, seed=9, extent=8.0))
     leaves = [0.02 + 0.01 * (f % 3) for f in range(len(frames))]
-    a = vg.downsample_frames([cuda(f) for f in frames], leaves)
+    a = vg.downsample_frames([cuda(f) for f in frames], leaves, method="sort")
     b = vg.downsample_frames([cuda(f) for f in frames], leaves, method="sort_lsd")
     assert list(a.offsets) == list(b.offsets)
     same_rows(a, b)
@@ -119,7 +120,7 @@ def test_batched_frames_match_full_sort():
 
 def test_pyramid_on_the_bucket_grouping():
     x = synth.random_cloud(80_000, seed=21, extent=3.0)
-    p = vg.pyramid(cuda(x), 0.02, 3)
+    p = vg.pyramid(cuda(x), 0.02, 3, method="sort")
     q = vg.pyramid(cuda(x), 0.02, 3, method="sort_lsd")
     for lvl in range(3):
         same_rows(p[lvl], q[lvl])
@@ -127,3 +128,31 @@ def test_pyramid_on_the_bucket_grouping():
     for lvl in range(3):
         assert np.array_equal(gpu_keys(p[lvl].keys), ref[lvl][0])
         assert np.array_equal(gpu_counts(p[lvl].counts), ref[lvl][2])
+
+
+def test_frames_straddling_partition_tiles():
+    # frames of 1 to 5000 points: the key kernel's chunks and the partition passes' tiles
+    # of 4096 entries hold many frames
+    r = rng(31)
+    sizes = [1, 2, 3, 4095, 4097, 1, 0, 5000, 7, 4096, 13, 2049, 1, 1, 1]
+    frames = [(r.random((m, 3)) * 3.0).astype(np.float32) for m in sizes]
+    leaves = [0.05 + 0.01 * (f % 4) for f in range(len(frames))]
+    a = vg.downsample_frames([cuda(f) for f in frames], leaves, method="sort")
+    b = vg.downsample_frames([cuda(f) for f in frames], leaves, method="sort_lsd")
+    assert list(a.offsets) == list(b.offsets)
+    same_rows(a, b)
+    for f, x in enumerate(frames):
+        ref = oracle.downsample(x, leaves[f])
+        lo, hi = int(a.offsets[f]), int(a.offsets[f + 1])
+        assert np.array_equal(gpu_keys(a.keys[lo:hi]), ref.keys)
+        assert np.array_equal(gpu_counts(a.counts[lo:hi]), ref.counts)
+
+
+@pytest.mark.parametrize("n", [307_200, 4_500_000])
+def test_auto_picks_by_size_and_matches_both_groupings(n):
+    # "auto" takes the global radix sort below 2^22 points and the bucket grouping from
+    # there: its rows are bit-identical to both
+    x = synth.fused_map(n, seed=41)
+    auto = vg.downsample(cuda(x), 0.02)
+    same_rows(auto, vg.downsample(cuda(x), 0.02, method="sort"))
+    same_rows(auto, vg.downsample(cuda(x), 0.02, method="sort_lsd"))
