@@ -91,6 +91,15 @@ typedef enum {
                                 radix pass, then the segmented reduction, instead of the
                                 bucket grouping (same rows; for comparison)              */
 #define VG_USE_GRAPH 64      /* vg_downsample_batch: capture / replay a CUDA graph      */
+#define VG_SORT_FRAME 128    /* SORT for one camera frame (vg_downsample, or a batch of
+                                one frame): the keys are counted into bins of 2^12
+                                consecutive keys, scattered once, and every bin is reduced
+                                in one block's shared memory -- five kernels, for clouds
+                                whose launches cost more than their bytes.  Needs 32-bit
+                                keys (the Morton code of the frame's per-axis maximum
+                                index below 2^32 - 1), else the call records
+                                VG_ERR_RANGE.  Several frames, point_to_voxel or
+                                attributes take the plain SORT path.  Same rows as SORT */
 #define VG_GRID_SHIFT 8      /* vg_downsample_frames: blocks per SM of the streaming    */
 #define VG_GRID_MASK (0xff << VG_GRID_SHIFT) /* kernels (0 = default 8)                */
 
@@ -390,8 +399,9 @@ VG_API vg_status vg_downsample_backward(const float* grad_centroids, const uint3
  * process exits.  The call allocates nothing.
  *   * n > VG_NOALLOC_MAX_POINTS is rejected with VG_ERR_INVALID_ARG before any launch.
  *   * Only the sort method runs here (VG_METHOD_AUTO, VG_METHOD_SORT, with or without
- *     VG_SORT_BUCKETS): the array holds the sort path's workspace, so VG_METHOD_HASH is
- *     rejected with VG_ERR_INVALID_ARG before any launch.
+ *     VG_SORT_BUCKETS or VG_SORT_LSD): the array holds the sort path's workspace, so
+ *     VG_METHOD_HASH and VG_SORT_FRAME are rejected with VG_ERR_INVALID_ARG before any
+ *     launch.
  *   * The device address of the array is cached per device; cudaDeviceReset invalidates
  *     it, so do not call this entry point after resetting the device.
  *   * The first call on a device looks up the array's device address (once per device,

@@ -59,6 +59,7 @@ void warm_launch_config() {
   warm_reduce_config();
   warm_filter_config();
   warm_msd_config();
+  warm_frame_config();
 }
 
 int persistent_grid(const void* kernel, int threads, size_t dyn_smem, int64_t work_tiles) {
@@ -115,8 +116,9 @@ int method_of(int flags) {
 
 size_t frames_workspace_bytes(int64_t n, int frames, int flags) {
   if (n < 0 || frames < 1) return 0;
-  return method_of(flags) == VG_METHOD_HASH ? hash_layout(n, frames).total
-                                            : sort_layout(n, frames).total;
+  if (method_of(flags) == VG_METHOD_HASH) return hash_layout(n, frames).total;
+  const size_t base = sort_layout(n, frames).total;
+  return (flags & VG_SORT_FRAME) != 0 ? frame_layout(n, base).total : base;
 }
 
 vg_status check_outputs(int64_t n, const float* xyz, uint64_t* out_keys, float* out_centroids,
@@ -155,6 +157,8 @@ vg_status run_frames(const float* xyz, const FramesArg& fr, bool from_min, const
     frn.lsd_narrow = (flags & VG_SORT_LSD) != 0 ||
                      ((flags & VG_METHOD_MASK) == VG_METHOD_AUTO && n < kAutoBucketMinPoints);
     const bool maybe_msd = frn.allow_narrow && !frn.lsd_narrow;
+    // VG_SORT_FRAME: one frame, no point_to_voxel or attributes (else the plain sort path)
+    const bool frame_path = (flags & VG_SORT_FRAME) != 0 && F == 1 && frn.allow_narrow && n > 0;
     const bool have_extent = from_min || F > 1 || frn.allow_narrow;
     const SortLayout L = sort_layout(n, F);
     State* st = reinterpret_cast<State*>(ws + L.state);
@@ -173,24 +177,42 @@ vg_status run_frames(const float* xyz, const FramesArg& fr, bool from_min, const
     uint64_t* pay_1 = reinterpret_cast<uint64_t*>(ws + L.idx0);
     int* err = out_error ? reinterpret_cast<int*>(out_error) : &st->error;
 
-    cudaError_t e = cudaMemsetAsync(ws, 0, L.zero_bytes, stream);
-    if (e == cudaSuccess && maybe_msd)  // points per bucket
+    // (the frame path needs only the state and frame state cleared: its last kernel
+    // writes the voxel count and the frame offsets)
+    cudaError_t e = cudaMemsetAsync(ws, 0, frame_path ? L.lb_a : L.zero_bytes, stream);
+    if (e == cudaSuccess && maybe_msd && !frame_path)  // points per bucket
       e = cudaMemsetAsync(ws + L.mhist, 0, L.mvcnt - L.mhist, stream);
     if (e == cudaSuccess && out_error) e = cudaMemsetAsync(out_error, 0, sizeof(int32_t), stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(out.num_voxels, 0, sizeof(int64_t), stream);
-    if (e == cudaSuccess && out.frame_offsets)
+    if (e == cudaSuccess && !frame_path)
+      e = cudaMemsetAsync(out.num_voxels, 0, sizeof(int64_t), stream);
+    if (e == cudaSuccess && out.frame_offsets && !frame_path)
       e = cudaMemsetAsync(out.frame_offsets, 0, size_t(F + 1) * sizeof(int64_t), stream);
     if (e == cudaSuccess && out.p2v && n > 0)
       e = cudaMemsetAsync(out.p2v, 0xff, size_t(n) * sizeof(int32_t), stream);
     mark(stage++, stream);
-    if (e == cudaSuccess && have_extent) e = launch_origin(xyz, frn, st, fs, err, stream);
+    if (e == cudaSuccess && have_extent) {
+      if (frame_path) {
+        const FrameLayout FL = frame_layout(n, L.total);
+        e = launch_origin(xyz, frn, st, fs, err, stream, ws + FL.zero, FL.zero_bytes);
+      } else {
+        e = launch_origin(xyz, frn, st, fs, err, stream);
+      }
+    }
     mark(stage++, stream);
-    if (e == cudaSuccess)
+    if (e == cudaSuccess && !frame_path)
       e = launch_keys_any(xyz, frn, have_extent, st, fs, keys0, k32_0, pay_0, err, stream);
-    mark(stage++, stream);
+    if (!frame_path) mark(stage++, stream);
     // The layout and the grouping are chosen on the device (they depend on the largest
     // key); the kernels of the ones not chosen return at once.
     const NarrowBuffers nb{k32_0, pay_0, k32_1, pay_1};
+    if (frame_path) {
+      // one camera frame: bins of 2^12 keys (vg_frame.cu); the extent kernel clears the
+      // bin counts
+      const FrameLayout FL = frame_layout(n, L.total);
+      if (e == cudaSuccess) e = launch_frame(xyz, frn, st, fs, nb, ws, FL, out, spins, err, stream);
+      for (int k = 0; k < 1 + 3 + kMaxPasses + 1; ++k) mark(stage++, stream);
+      return cuda_status(e);
+    }
     if (maybe_msd) {
       if (e == cudaSuccess)
         e = launch_msd(st, fs, F, nb, ws, L, n, out, spins, err, stream, stage, mark);
@@ -338,9 +360,12 @@ vg_status vg_downsample(const float* xyz, int64_t n, float* origin, float leaf,
                         int32_t* out_error, void* workspace, size_t workspace_bytes, int flags,
                         vg_stream_t stream) {
   if (!(leaf > 0.0f) || !std::isfinite(leaf)) return VG_ERR_INVALID_ARG;
-  if ((flags & ~(VG_ORIGIN_FROM_MIN | VG_METHOD_MASK | VG_SORT_BUCKETS | VG_SORT_LSD)) != 0)
+  if ((flags & ~(VG_ORIGIN_FROM_MIN | VG_METHOD_MASK | VG_SORT_BUCKETS | VG_SORT_LSD |
+                 VG_SORT_FRAME)) != 0)
     return VG_ERR_INVALID_ARG;
   if ((flags & VG_METHOD_MASK) == VG_METHOD_MASK) return VG_ERR_INVALID_ARG;
+  if ((flags & VG_SORT_FRAME) != 0 && (flags & VG_METHOD_MASK) != VG_METHOD_SORT)
+    return VG_ERR_INVALID_ARG;
   if (!origin || !out_num_voxels) return VG_ERR_INVALID_ARG;
   vg_status s = check_outputs(n, xyz, out_keys, out_centroids, out_counts, cap, out_num_voxels,
                               out_point_to_voxel, out_error, workspace);
@@ -407,9 +432,11 @@ vg_status vg_downsample_frames_ex(const float* xyz, int64_t n_total,
   }
   const bool filtered = extras && extras->min_count > 1;
   if ((flags & ~(VG_ORIGIN_FROM_MIN | VG_METHOD_MASK | VG_GRID_MASK | VG_SORT_BUCKETS |
-                 VG_SORT_LSD)) != 0)
+                 VG_SORT_LSD | VG_SORT_FRAME)) != 0)
     return VG_ERR_INVALID_ARG;
   if ((flags & VG_METHOD_MASK) == VG_METHOD_MASK) return VG_ERR_INVALID_ARG;
+  if ((flags & VG_SORT_FRAME) != 0 && (flags & VG_METHOD_MASK) != VG_METHOD_SORT)
+    return VG_ERR_INVALID_ARG;
   if (!frame_offsets || !origins || !leaves || !out_frame_offsets) return VG_ERR_INVALID_ARG;
   vg_status s = check_outputs(n_total, xyz, out_keys, out_centroids, out_counts, cap,
                               out_frame_offsets, out_point_to_voxel, out_error, workspace);

@@ -128,6 +128,8 @@ struct alignas(256) State {
   uint32_t nwjobs;            // bucket-kernel jobs of windows of large buckets
   uint32_t nbig;              // buckets of more than kBkStage entries
   uint32_t njobs3;            // chunks of large buckets the third partition pass splits
+  uint32_t fspan;             // single-frame bins: bin = key >> fspan (vg_frame.cu)
+  uint32_t ftop;              // single-frame bins: 2^ftop bins
   uint32_t ctot[64];          // entries of every 1024 consecutive buckets
   uint32_t nztot[64];         // non-empty buckets of every 1024 consecutive buckets
   uint32_t vtot[64];          // cells of every 1024 consecutive non-empty buckets
@@ -254,6 +256,44 @@ constexpr SortLayout sort_layout(int64_t n, int frames = 1) {
   return L;
 }
 
+// The single-frame bin grouping (VG_SORT_FRAME, vg_frame.cu): the sort layout's key
+// arrays, then the runs of equal keys and their places in their bins, the zeroed bin
+// counts and scan status words, the bins' first entries and cells.
+constexpr int kFrSpanBits = 12;  // a bin holds 2^12 consecutive keys
+constexpr int kFrMaxTop = 20;    // at most 2^20 bins (32-bit keys)
+constexpr int kFrMaxUnitBits = 12;  // at most 2^12 look-back units of bins
+constexpr int kFrScanBins = 4096;   // bins per tile of the bin-count scan
+struct FrameLayout {
+  size_t pos, rin, rout, zero, hist, ustat, pstat, tick, start, vcnt, zero_bytes, total;
+};
+constexpr FrameLayout frame_layout(int64_t n, size_t base) {
+  FrameLayout L{};
+  const int64_t nn = n < 1 ? 1 : n;
+  size_t off = align_up(base, 256);
+  L.pos = off;  // each run's place in its bin (at its last point)
+  off = align_up(off + size_t(nn) * sizeof(uint32_t), 256);
+  L.rin = off;  // runs (three offset sums and the points) at their last point
+  off = align_up(off + size_t(nn) * 4 * sizeof(uint32_t), 256);
+  L.rout = off;  // the runs grouped by bin
+  off = align_up(off + size_t(nn) * 4 * sizeof(uint32_t), 256);
+  L.zero = off;
+  L.hist = off;
+  off = align_up(off + (size_t(1) << kFrMaxTop) * sizeof(uint32_t), 256);
+  L.ustat = off;
+  off = align_up(off + (size_t(1) << kFrMaxUnitBits) * sizeof(uint32_t), 256);
+  L.pstat = off;
+  off = align_up(off + ((size_t(1) << kFrMaxTop) / kFrScanBins) * sizeof(uint32_t), 256);
+  L.tick = off;
+  off = align_up(off + 4 * sizeof(uint32_t), 256);
+  L.zero_bytes = off - L.zero;
+  L.start = off;
+  off = align_up(off + ((size_t(1) << kFrMaxTop) + 1) * sizeof(uint32_t), 256);
+  L.vcnt = off;  // cells of every bin
+  off = align_up(off + (size_t(1) << kFrMaxTop) * sizeof(uint32_t), 256);
+  L.total = off;
+  return L;
+}
+
 int num_sms();
 uint32_t spin_limit();
 // Grid of a persistent kernel: all its blocks resident at once (occupancy x SMs), at most
@@ -267,8 +307,10 @@ void warm_reduce_config();
 
 // Launchers (all asynchronous on `stream`).
 // a1: per-frame min (and max) of the valid points into FrameState.
+// `zero`/`zero_bytes` (16-byte multiple, or 0): a region the kernel also clears.
 cudaError_t launch_origin(const float* xyz, const FramesArg& fr, State* st, FrameState* fs,
-                          int* err, cudaStream_t stream);
+                          int* err, cudaStream_t stream, void* zero = nullptr,
+                          size_t zero_bytes = 0);
 // a2: per-point sort keys (frame id above a key_shift-bit Morton field; ~0 = invalid).
 cudaError_t launch_keys(const float* xyz, const FramesArg& fr, bool have_extent, State* st,
                         FrameState* fs, uint64_t* keys, int* err, cudaStream_t stream);
@@ -314,6 +356,12 @@ cudaError_t launch_msd(State* st, const FrameState* fs, int nframes, const Narro
                        uint32_t spin_limit, int* err, cudaStream_t stream, int stage0,
                        void (*mark)(int, cudaStream_t));
 void warm_msd_config();
+// The single-frame bin grouping after the extent kernel (which cleared the layout's zero
+// region): keys and bin places, bin starts, the scatter into bins, and the rows.
+cudaError_t launch_frame(const float* xyz, const FramesArg& fr, State* st, FrameState* fs,
+                         const NarrowBuffers& nb, char* ws, const FrameLayout& FL,
+                         const SegOut& out, uint32_t spin_limit, int* err, cudaStream_t stream);
+void warm_frame_config();
 // Minimum-count filter (vg_filter.cu): its scratch follows the grouping method's layout.
 struct FilterLayout {
   size_t ticket, status, remap, zero_bytes, total;

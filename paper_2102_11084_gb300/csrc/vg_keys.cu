@@ -58,7 +58,8 @@ __device__ __forceinline__ void flush_extent(float mn[3], float mx[3], FrameStat
 template <bool kPosed>
 __global__ __launch_bounds__(kStreamThreads) void origin_kernel(const float* __restrict__ xyz,
                                                                 FramesArg fr, FrameState* fs,
-                                                                int* err) {
+                                                                int* err, uint4* zero,
+                                                                size_t zero16) {
   // only the frame/chunk map (no per-frame origin or leaf is needed here)
   __shared__ struct {
     int64_t off[kMaxFrames + 1];
@@ -66,6 +67,9 @@ __global__ __launch_bounds__(kStreamThreads) void origin_kernel(const float* __r
     uint32_t tmp[kStreamThreads / 32];
   } sm;
   __shared__ float red[kStreamThreads / 32][6];
+  for (size_t i = size_t(blockIdx.x) * kStreamThreads + threadIdx.x; i < zero16;
+       i += size_t(gridDim.x) * kStreamThreads)
+    zero[i] = make_uint4(0u, 0u, 0u, 0u);
   const uint32_t T = build_chunk_map(fr, sm.off, sm.cstart, sm.tmp, err);
   uint32_t c0, c1;
   block_range(T, &c0, &c1);
@@ -164,32 +168,24 @@ __device__ __forceinline__ void key_loop(const float* __restrict__ xyz, const Fr
     uint64_t pay[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      uint32_t ijk[3];
-      const bool ok = point_index(v[3 * j], v[3 * j + 1], v[3 * j + 2], o, leaf, rleaf, ijk,
-                                  &range_bad);
+      bool ok;
+      pay[j] = kPayloadInvalid;
       if (kNarrow) {
-        // the indices have at most 11 bits: the interleave runs on 32-bit words
-        const uint32_t local = spread3_32(ijk[0]) | (spread3_32(ijk[1]) << 1) |
-                               (spread3_32(ijk[2]) << 2);
-        k[j] = ok ? static_cast<KeyT>(key_compose(static_cast<uint32_t>(f), local, key_shift))
-                  : static_cast<KeyT>(kKeySentinel);
+        uint32_t k32 = 0;
+        ok = narrow_entry(v[3 * j], v[3 * j + 1], v[3 * j + 2], o, leaf, rleaf, inv_unit,
+                          static_cast<uint32_t>(f), key_shift, &k32, &pay[j], &range_bad);
+        k[j] = ok ? static_cast<KeyT>(k32) : static_cast<KeyT>(kKeySentinel);
       } else {
+        uint32_t ijk[3];
+        ok = point_index(v[3 * j], v[3 * j + 1], v[3 * j + 2], o, leaf, rleaf, ijk, &range_bad);
         k[j] = ok ? key_compose(static_cast<uint32_t>(f), morton3(ijk[0], ijk[1], ijk[2]),
                                 key_shift)
                   : kKeySentinel;
       }
-      pay[j] = kPayloadInvalid;
       if (ok) {
         ++nvalid;
         kmax = k[j] > kmax ? k[j] : kmax;
         atomicAdd(&hist[uint32_t(k[j] >> hshift) & (kRadix - 1)], 1u);
-        if (kNarrow) {
-          int qq[3];
-#pragma unroll
-          for (int a = 0; a < 3; ++a)
-            qq[a] = quant_offset(v[3 * j + a], voxel_corner(ijk[a], o[a], leaf), inv_unit);
-          pay[j] = pack_offsets(qq[0], qq[1], qq[2]);
-        }
       }
     }
     if (kNarrow) {
@@ -291,13 +287,17 @@ int stream_grid(const FramesArg& fr) {
 }
 
 cudaError_t launch_origin(const float* xyz, const FramesArg& fr, State* st, FrameState* fs,
-                          int* err, cudaStream_t stream) {
+                          int* err, cudaStream_t stream, void* zero, size_t zero_bytes) {
   (void)st;
-  if (fr.n == 0) return cudaSuccess;
+  if (fr.n == 0) {
+    return zero_bytes ? cudaMemsetAsync(zero, 0, zero_bytes, stream) : cudaSuccess;
+  }
+  uint4* z = static_cast<uint4*>(zero);
+  const size_t z16 = zero ? zero_bytes / 16 : 0;
   if (posed(fr))
-    origin_kernel<true><<<stream_grid(fr), kStreamThreads, 0, stream>>>(xyz, fr, fs, err);
+    origin_kernel<true><<<stream_grid(fr), kStreamThreads, 0, stream>>>(xyz, fr, fs, err, z, z16);
   else
-    origin_kernel<false><<<stream_grid(fr), kStreamThreads, 0, stream>>>(xyz, fr, fs, err);
+    origin_kernel<false><<<stream_grid(fr), kStreamThreads, 0, stream>>>(xyz, fr, fs, err, z, z16);
   return cudaGetLastError();
 }
 

@@ -51,8 +51,10 @@ vg_status vg_downsample_noalloc(const float* xyz, int64_t n, float* origin, floa
                                 int64_t cap, int64_t* out_num_voxels, int32_t* out_point_to_voxel,
                                 int32_t* out_error, int flags, vg_stream_t stream) {
   if (n < 0 || n > kMaxPoints) return VG_ERR_INVALID_ARG;
-  // The array is sized for the sort path's workspace; the hash path needs far more.
-  if ((flags & VG_METHOD_MASK) == VG_METHOD_HASH) return VG_ERR_INVALID_ARG;
+  // The array is sized for the sort path's workspace; the hash path and the single-frame
+  // bin grouping need more.
+  if ((flags & VG_METHOD_MASK) == VG_METHOD_HASH || (flags & VG_SORT_FRAME) != 0)
+    return VG_ERR_INVALID_ARG;
   void* scratch = nullptr;
   const vg_status s = scratch_for_current_device(&scratch);
   if (s != VG_OK) return s;

@@ -44,10 +44,11 @@ int plan_flags(const vg_plan* p, int flags) {
 }
 
 // The grouping choices a plan holds: the sort (bucket grouping for 32-bit keys), the sort
-// with every digit in global radix passes, and the hash path.
+// with every digit in global radix passes, the single-frame bin grouping, and the hash
+// path.
 bool plan_method_ok(int m) {
   return m == VG_METHOD_AUTO || m == VG_METHOD_SORT || m == (VG_METHOD_SORT | VG_SORT_LSD) ||
-         m == VG_METHOD_HASH;
+         m == (VG_METHOD_SORT | VG_SORT_FRAME) || m == VG_METHOD_HASH;
 }
 
 void drop_graph(vg_plan* p) {
@@ -74,10 +75,16 @@ vg_status vg_plan_create(vg_plan** out, int max_frames, int64_t max_points, int 
   }
   p->max_frames = max_frames;
   p->max_points = max_points;
-  p->method = m == VG_METHOD_HASH ? VG_METHOD_HASH
-                                  : (m == VG_METHOD_AUTO ? VG_METHOD_AUTO
-                                                         : (VG_METHOD_SORT | (flags & VG_SORT_LSD)));
-  const size_t a = vg::frames_workspace_bytes(max_points, max_frames, VG_METHOD_SORT);
+  p->method = m == VG_METHOD_HASH
+                  ? VG_METHOD_HASH
+                  : (m == VG_METHOD_AUTO ? VG_METHOD_AUTO
+                                         : (VG_METHOD_SORT | (flags & (VG_SORT_LSD | VG_SORT_FRAME))));
+  if (p->method == (VG_METHOD_SORT | VG_SORT_LSD | VG_SORT_FRAME)) {
+    delete p;
+    return VG_ERR_INVALID_ARG;
+  }
+  // room for every grouping a later configure may pick
+  const size_t a = vg::frames_workspace_bytes(max_points, max_frames, VG_METHOD_SORT | VG_SORT_FRAME);
   const size_t b = vg::frames_workspace_bytes(max_points, max_frames, VG_METHOD_HASH);
   p->ws_bytes = a > b ? a : b;
   if (cudaMalloc(&p->ws, p->ws_bytes) != cudaSuccess) {

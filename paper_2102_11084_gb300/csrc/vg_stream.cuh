@@ -53,6 +53,27 @@ __device__ __forceinline__ void pose_point(const Pose& P, float& x, float& y, fl
   z = keep ? g[2] : NAN;
 }
 
+// Key (the narrow layout's 32 bits) and packed corner offsets of one point of frame f;
+// false for an invalid or out-of-range point (*range_bad set for the latter).  The key
+// kernel and the single-frame bin grouping both call this, so they agree bit for bit.
+__device__ __forceinline__ bool narrow_entry(float x, float y, float z, const float o[3],
+                                             float leaf, float rleaf, float inv_unit,
+                                             uint32_t f, uint32_t key_shift, uint32_t* key,
+                                             uint64_t* pay, bool* range_bad) {
+  uint32_t ijk[3];
+  if (!point_index(x, y, z, o, leaf, rleaf, ijk, range_bad)) return false;
+  // the indices have at most 11 bits: the interleave runs on 32-bit words
+  const uint32_t local =
+      spread3_32(ijk[0]) | (spread3_32(ijk[1]) << 1) | (spread3_32(ijk[2]) << 2);
+  *key = static_cast<uint32_t>(key_compose(f, local, key_shift));
+  const float v[3] = {x, y, z};
+  int qq[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) qq[a] = quant_offset(v[a], voxel_corner(ijk[a], o[a], leaf), inv_unit);
+  *pay = pack_offsets(qq[0], qq[1], qq[2]);
+  return true;
+}
+
 // Contiguous chunk range of this block.
 __device__ __forceinline__ void block_range(uint32_t T, uint32_t* c0, uint32_t* c1) {
   *c0 = static_cast<uint32_t>((uint64_t(T) * blockIdx.x) / gridDim.x);
@@ -67,7 +88,8 @@ __device__ __forceinline__ uint32_t frame_prologue(const FramesArg& fr, bool hav
                                                    State* st, FrameState* fs, uint32_t T,
                                                    ChunkSmem& sm, int* err,
                                                    bool* narrow = nullptr,
-                                                   uint32_t* bshift = nullptr) {
+                                                   uint32_t* bshift = nullptr,
+                                                   uint32_t* kbits = nullptr) {
   const int F = fr.nframes;
   // per-frame origin and leaf; bits of the largest key of each frame
   uint32_t bits = 0;
@@ -167,6 +189,7 @@ __device__ __forceinline__ uint32_t frame_prologue(const FramesArg& fr, bool hav
   }
   // the key kernel histograms the first partition pass's digit
   if (bshift) *bshift = mmode ? low + b2 : 0u;
+  if (kbits) *kbits = kb;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     st->key_shift = key_shift;
     st->nframes = F;

@@ -28,15 +28,18 @@ METHOD_HASH = 32
 SORT_BUCKETS = 2
 SORT_LSD = 4
 USE_GRAPH = 64
+SORT_FRAME = 128
 GRID_SHIFT = 8
 # "auto" (the default): "sort" for clouds of 4,194,304 points or more, else "sort_lsd";
 # "sort": 32-bit keys grouped by buckets (partition passes over the top key bits, every
 # bucket reduced on chip), otherwise a global radix sort; "sort_lsd": every key digit in a
 # global radix pass and the segmented reduction; "sort_bucket": the same as "sort" (kept
-# for compatibility); "hash": hash-table accumulation.  All give identical rows.
+# for compatibility); "frame": one camera frame counted into bins of 2^12 keys and reduced
+# bin by bin (five kernels; 32-bit keys); "hash": hash-table accumulation.  All give
+# identical rows.
 _METHODS = {"auto": METHOD_AUTO, "sort": METHOD_SORT,
             "sort_bucket": METHOD_SORT | SORT_BUCKETS, "sort_lsd": METHOD_SORT | SORT_LSD,
-            "hash": METHOD_HASH}
+            "frame": METHOD_SORT | SORT_FRAME, "hash": METHOD_HASH}
 MAX_POINTS = (1 << 30) - 1
 MAX_FRAMES = 1024
 MAX_LEVELS = 8
@@ -629,7 +632,8 @@ class Plan:
         _check(lib().vg_plan_get(self._h, ctypes.byref(m), ctypes.byref(g), ctypes.byref(w)),
                "vg_plan_get")
         return {"method": {METHOD_AUTO: "auto", METHOD_SORT: "sort",
-                           METHOD_SORT | SORT_LSD: "sort_lsd", METHOD_HASH: "hash"}[m.value],
+                           METHOD_SORT | SORT_LSD: "sort_lsd",
+                           METHOD_SORT | SORT_FRAME: "frame", METHOD_HASH: "hash"}[m.value],
                 "grid_per_sm": g.value, "workspace_bytes": w.value}
 
     def run(self, xyz, frame_offsets, n_frames, origins, leaves, out_keys, out_centroids,

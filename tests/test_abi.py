@@ -86,11 +86,18 @@ def test_grouping_flags():
     assert _call(flags=vg.METHOD_SORT | vg.SORT_LSD) == vg.Status.WORKSPACE
     assert _call(flags=vg.METHOD_SORT | 8) == vg.Status.INVALID_ARG
     assert _call(flags=vg.METHOD_SORT | vg.METHOD_HASH) == vg.Status.INVALID_ARG
+    # the single-frame bin grouping: a flag of the sort method only, with its own workspace
+    assert vg.method_flag("frame") == vg.METHOD_SORT | vg.SORT_FRAME
+    assert _call(flags=vg.METHOD_SORT | vg.SORT_FRAME) == vg.Status.WORKSPACE
+    assert _call(flags=vg.SORT_FRAME) == vg.Status.INVALID_ARG
+    assert _call(flags=vg.METHOD_HASH | vg.SORT_FRAME) == vg.Status.INVALID_ARG
+    assert vg.workspace_bytes(1000, vg.METHOD_SORT | vg.SORT_FRAME) > vg.workspace_bytes(1000)
     L = vg.lib()
     args = (None, 0, 8, ctypes.c_float(0.1), 2, None, None, None, 0, 16, None, None, None, 0)
     assert L.vg_pyramid(*args, vg.SORT_BUCKETS, None) == vg.Status.WORKSPACE
     assert L.vg_pyramid(*args, vg.SORT_LSD, None) == vg.Status.WORKSPACE
     assert L.vg_pyramid(*args, vg.METHOD_HASH, None) == vg.Status.INVALID_ARG
+    assert L.vg_pyramid(*args, vg.SORT_FRAME, None) == vg.Status.INVALID_ARG
 
 
 def test_no_cpu_fallback():
