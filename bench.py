@@ -215,18 +215,38 @@ def extra_measurements(args, dev, peak):
     out = {}
     stream = torch.cuda.current_stream(dev)
 
-    # 640x480 RGB-D frame, leaf 0.05 m: one plain call (sort and hash) and a 1-frame graph
+    # 640x480 RGB-D frame, leaf 0.05 m: one plain call per grouping, and the one-frame plan
+    # (CUDA-graph replay) with the single-frame bin grouping
     frame = synth.rgbd_frame(640, 480, seed=0)
     x = torch.from_numpy(frame).to(dev)
     n = x.shape[0]
     r = {}
-    for m in ("auto", "sort", "sort_lsd", "hash"):
+    for m in ("auto", "frame", "sort", "sort_lsd", "hash"):
         buf = vg.alloc_buffers(n, dev, flags=vg.method_flag(m))
         ms = _time_ms(lambda: vg.downsample_into(x, 0.05, buf, origin_from_min=True, method=m), 200)
+        if int(buf.error.item()):
+            raise vg.VGError(int(buf.error.item()), "640x480 " + m)
         v = int(buf.num_voxels.item())
         r[m] = {"ms": ms, "points_per_s": n / (ms / 1e3),
                 "roofline_frac": (12.0 * n + 16.0 * v) / (ms / 1e3) / 1e9 / peak}
+    side1 = torch.cuda.Stream(dev)
+    fb = dict(xyz=x, frame_offsets=torch.tensor([0, n], dtype=torch.int64, device=dev),
+              n_frames=1, origins=torch.zeros((1, 3), dtype=torch.float32, device=dev),
+              leaves=torch.full((1,), 0.05, dtype=torch.float32, device=dev),
+              out_keys=torch.empty(n, dtype=torch.int64, device=dev),
+              out_centroids=torch.empty((n, 3), dtype=torch.float32, device=dev),
+              out_counts=torch.empty(n, dtype=torch.int32, device=dev),
+              out_frame_offsets=torch.zeros(2, dtype=torch.int64, device=dev),
+              out_error=torch.zeros(1, dtype=torch.int32, device=dev))
+    for m in ("frame", "sort_lsd"):
+        plan1 = vg.Plan(1, n, method=m)
+        with torch.cuda.stream(side1):
+            ms = _time_ms(lambda: plan1.run(**fb, graph=True, stream=side1), 200, stream=side1)
+        plan1.close()
+        r["plan_graph_" + m] = {"ms": ms, "points_per_s": n / (ms / 1e3),
+                                "roofline_frac": (12.0 * n + 16.0 * v) / (ms / 1e3) / 1e9 / peak}
     r["voxels"] = v
+    r["auto_choice"] = "sort_lsd (radix sort: fewer than 2^22 points)"
     out["rgbd_640x480_leaf0.05"] = r
 
     # 64 frames of uneven size: 64 plain calls vs one batched call (plan, tuned, graph)
@@ -315,11 +335,18 @@ def extra_measurements(args, dev, peak):
     hd = torch.from_numpy(synth.rgbd_frame(1280, 720, seed=0, cx=639.5, cy=359.5)).to(dev)
     out["pyramid_1280x720_4_levels_ms"] = _time_ms(lambda: vg.pyramid(hd, 0.01, 4), 20)
     sweep = {}
-    hb = vg.alloc_buffers(hd.shape[0], dev)
-    for lf in (0.01, 0.02, 0.05, 0.1):
-        ms = _time_ms(lambda: vg.downsample_into(hd, lf, hb, origin_from_min=True), 50)
-        sweep[str(lf)] = {"ms": ms, "points_per_s": hd.shape[0] / (ms / 1e3),
-                          "voxels": int(hb.num_voxels.item())}
+    nhd = hd.shape[0]
+    for m in ("auto", "frame"):
+        hb = vg.alloc_buffers(nhd, dev, flags=vg.method_flag(m))
+        for lf in (0.01, 0.02, 0.05, 0.1):
+            ms = _time_ms(lambda: vg.downsample_into(hd, lf, hb, origin_from_min=True, method=m),
+                          50)
+            if int(hb.error.item()):
+                raise vg.VGError(int(hb.error.item()), "1280x720 " + m)
+            vh = int(hb.num_voxels.item())
+            sweep.setdefault(str(lf), {"voxels": vh})[m] = {
+                "ms": ms, "points_per_s": nhd / (ms / 1e3),
+                "roofline_frac": (12.0 * nhd + 16.0 * vh) / (ms / 1e3) / 1e9 / peak}
     out["rgbd_1280x720_sweep"] = sweep
 
     # voxel extras on the same frame at 0.02 m: RGB means per voxel and/or min 2 points
@@ -370,19 +397,26 @@ def extra_measurements(args, dev, peak):
     # serving: 16 sensor streams x 30 Hz Poisson arrivals of 640x480 frames, leaf 0.05 m
     pool = [synth.rgbd_frame(640, 480, seed=3000 + k) for k in range(64)]
     trace = synth.serving_trace(16, 30.0, args.serve_seconds, len(pool), seed=5)
-    srv = serve.Server(max_points=16 * 307_200, max_frames=16, n_slots=2)
+    srv = serve.Server(max_points=16 * 307_200, max_frames=16, n_slots=3, record_timeline=True)
     results, wall = serve.replay(srv, trace, pool, 0.05)
+    tl = srv.timeline()
     srv.close()
     st = serve.latency_stats(results)
+    st["copy_overlap"] = serve.copy_overlap(tl)
     st["points_per_s"] = len(results) * 307_200 / wall
     st["wall_s"] = wall
     st["batches"] = srv.batches
     sat_trace = [r._replace(arrival_s=0.0) for r in trace[:2000]]
-    srv = serve.Server(max_points=16 * 307_200, max_frames=16, n_slots=2)
+    srv = serve.Server(max_points=16 * 307_200, max_frames=16, n_slots=3, record_timeline=True)
     sat, sat_wall = serve.replay(srv, sat_trace, pool, 0.05, realtime=False)
+    sat_tl = srv.timeline()
     srv.close()
     st["saturation_points_per_s"] = len(sat) * 307_200 / sat_wall
     st["saturation_p99_ms"] = serve.latency_stats(sat)["p99_ms"]
+    st["saturation_copy_overlap"] = serve.copy_overlap(sat_tl)
+    st["copy_overlap_definition"] = ("copy time (pinned host <-> device, in and out) that ran "
+                                     "while another batch was decimated, over all copy time; "
+                                     "CUDA event timestamps")
     out["serving_16x30Hz_640x480"] = st
     return out
 
@@ -638,15 +672,18 @@ def run_vg(args, rank, world, local):
     # copy in and decimation run while step k's rows are copied back
     del keys_h, cent_h, cnt_h
     from paper_2102_11084_gb300 import serve
-    pipe = serve.CloudPipeline(n, args.leaf, depth=3, method=args.method, device=dev)
+    pipe = serve.CloudPipeline(n, args.leaf, depth=3, method=args.method, device=dev,
+                               record_timeline=True)
     for _ in pipe.run([xyz_host] * 3):  # untimed: first touch of the slots' buffers
         pass
     torch.cuda.synchronize()
+    n_warm_tl = len(pipe.timeline())
     t0 = time.perf_counter()
     d2h_pipe = 0
     for k_, c_, n_ in pipe.run([xyz_host] * e2e_steps):
         d2h_pipe = 8 + k_.shape[0] * (8 + 12 + 4)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
+    pipe_overlap = serve.copy_overlap(pipe.timeline()[n_warm_tl:])
     del pipe
     e2e_s = max_over_ranks(e2e_s, dev)
     e2e_seq_s = max_over_ranks(e2e_seq_s, dev)
@@ -708,6 +745,7 @@ def run_vg(args, rank, world, local):
                 "d2h_bytes_per_step": d2h_pipe, "ms_per_step": e2e_s * 1e3,
                 "api": "serve.CloudPipeline (depth 3: copies of neighbouring steps overlapped)",
                 "steps": e2e_steps, "warmup": 3,
+                "copy_overlap": pipe_overlap,
                 "sequential": {"value": total_points / e2e_seq_s, "ms_per_step": e2e_seq_s * 1e3,
                                "api": "vg.downsample_into + torch copies, one step at a time",
                                "h2d_ms": h2d_ms, "d2h_ms": d2h_ms,

@@ -320,12 +320,15 @@ VG_API vg_status vg_thin(const float* xyz, int64_t n, float* origin, float cell,
  * required) the first call captures the sequence and later calls with the same pointers,
  * sizes and flags replay it with one cudaGraphLaunch.  A plan is not thread-safe and its
  * workspace is shared by its calls: calls that overlap on the GPU race.
- * vg_plan_tune times three groupings -- VG_METHOD_SORT, VG_METHOD_SORT | VG_SORT_LSD and
- * VG_METHOD_HASH -- x streaming grids {4,8,16} blocks/SM on the given batch (`reps`
- * replays each, host-synchronising) and keeps the fastest; out_ms (9 floats or NULL)
- * receives sort@4,8,16, sort_lsd@4,8,16 then hash@4,8,16 in ms per batch.  A plan's
- * method (vg_plan_create flags, vg_plan_configure, vg_plan_get) is one of those three
- * or VG_METHOD_AUTO (the library's choice by cloud size, the default of a new plan).
+ * vg_plan_tune times four groupings -- VG_METHOD_SORT, VG_METHOD_SORT | VG_SORT_LSD,
+ * VG_METHOD_SORT | VG_SORT_FRAME (one-frame batches only) and VG_METHOD_HASH -- x
+ * streaming grids {4,8,16} blocks/SM on the given batch (`reps` replays each,
+ * host-synchronising) and keeps the fastest; out_ms (12 floats or NULL) receives
+ * sort@4,8,16, sort_lsd@4,8,16, frame@4,8,16 then hash@4,8,16 in ms per batch, -1 for a
+ * grouping not timed (frame with several frames) or one whose runs recorded a device
+ * error (frame with keys wider than 32 bits; the error word is cleared again).  A plan's
+ * method (vg_plan_create flags, vg_plan_configure, vg_plan_get) is one of those four or
+ * VG_METHOD_AUTO (the library's choice by cloud size, the default of a new plan).
  */
 typedef struct vg_plan vg_plan;
 VG_API vg_status vg_plan_create(vg_plan** plan, int max_frames, int64_t max_points, int flags);

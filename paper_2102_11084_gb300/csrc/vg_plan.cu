@@ -180,16 +180,24 @@ vg_status vg_plan_tune(vg_plan* p, const float* xyz, int64_t n_total,
                        float* out_ms) {
   if (!p || reps < 1) return VG_ERR_INVALID_ARG;
   cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
-  const int methods[3] = {VG_METHOD_SORT, VG_METHOD_SORT | VG_SORT_LSD, VG_METHOD_HASH};
+  const int methods[4] = {VG_METHOD_SORT, VG_METHOD_SORT | VG_SORT_LSD,
+                          VG_METHOD_SORT | VG_SORT_FRAME, VG_METHOD_HASH};
   const int grids[3] = {4, 8, 16};
+  // the device error word of the tuning runs: a grouping that records an error (the bin
+  // grouping of keys wider than 32 bits) is not a candidate
+  const int32_t* errw = out_error ? out_error : &reinterpret_cast<const vg::State*>(p->ws)->error;
   float best = 3.0e38f;
   int best_m = p->method, best_g = p->grid_per_sm;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return VG_ERR_CUDA;
   vg_status result = VG_OK;
   int slot = 0;
-  for (int mi = 0; mi < 3 && result == VG_OK; ++mi) {
+  for (int mi = 0; mi < 4 && result == VG_OK; ++mi) {
     for (int gi = 0; gi < 3 && result == VG_OK; ++gi, ++slot) {
+      if ((methods[mi] & VG_SORT_FRAME) != 0 && n_frames != 1) {  // several frames: SORT
+        if (out_ms) out_ms[slot] = -1.0f;
+        continue;
+      }
       vg_plan_configure(p, methods[mi], grids[gi]);
       // one untimed run (captures the graph), then `reps` timed replays
       result = vg_downsample_batch(p, xyz, n_total, frame_offsets, n_frames, origins, leaves,
@@ -209,7 +217,20 @@ vg_status vg_plan_tune(vg_plan* p, const float* xyz, int64_t n_total,
       float ms = 0.0f;
       cudaEventElapsedTime(&ms, e0, e1);
       ms /= float(reps);
+      int32_t werr = 0;
+      if (cudaMemcpy(&werr, errw, sizeof(werr), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        result = VG_ERR_CUDA;
+        break;
+      }
+      if (werr != 0) {  // not a candidate; the next runs start from a clear word
+        ms = -1.0f;
+        if (cudaMemset(const_cast<int32_t*>(errw), 0, sizeof(int32_t)) != cudaSuccess) {
+          result = VG_ERR_CUDA;
+          break;
+        }
+      }
       if (out_ms) out_ms[slot] = ms;
+      if (ms < 0.0f) continue;
       if (ms < best) {
         best = ms;
         best_m = methods[mi];

@@ -12,6 +12,11 @@ another's decimation (the decimations themselves run one after another).
 A completion pass copies each finished batch's rows back and resolves every request's
 future with its own voxels and its latency (arrival -> result on the host).
 
+With ``record_timeline=True`` every batch records CUDA events around its copy in, its
+decimation and its copy out; ``Server.timeline()`` turns them into intervals on one
+device clock and ``copy_overlap()`` measures how much copy time ran under another
+batch's decimation.
+
 Every frame of a batch is decimated exactly as it would be alone (same keys, counts
 and centroid bits), so a result does not depend on what it was batched with.
 """
@@ -77,19 +82,30 @@ class _Slot:
         self.h_error = torch.zeros(1, dtype=torch.int32).pin_memory()
         self.done = torch.cuda.Event()
         self.decimated = torch.cuda.Event()
+        self.copied = torch.cuda.Event()
         self.batch: list = []
         self.busy = False
+        self.copying = False
 
     def device_bytes(self) -> int:
         ts = [self.xyz, self.offsets, self.leaves, self.origins, self.keys, self.centroids,
               self.counts, self.out_offsets, self.error, self.workspace]
         return sum(t.numel() * t.element_size() for t in ts)
 
-    def launch(self, batch: list, after: Optional[torch.cuda.Event] = None):
+    def launch(self, batch: list, after: Optional[torch.cuda.Event] = None,
+               timeline: Optional[list] = None):
         """H2D of the admitted clouds, one batched decimation (behind the event `after`,
-        the previous decimation of any slot), D2H of the small tables."""
+        the previous decimation of any slot), D2H of the small tables.  `timeline`: a list
+        that receives this batch's timing events."""
         self.batch = batch
         self.busy = True
+        ev = None
+        if timeline is not None:
+            ev = {k: torch.cuda.Event(enable_timing=True)
+                  for k in ("h2d0", "h2d1", "dec0", "dec1", "d2h0", "d2h1")}
+            timeline.append({"frames": len(batch), "ev": ev, "done": False})
+            self.tl_entry = timeline[-1]
+        self.ev = ev
         sizes = [r.xyz.shape[0] for r in batch]
         offs = np.zeros(len(batch) + 1, np.int64)
         np.cumsum(sizes, out=offs[1:])
@@ -101,11 +117,17 @@ class _Slot:
         self.h_off_in.numpy()[:F + 1] = offs
         self.h_leaf_in.numpy()[:F] = [r.leaf for r in batch]
         with torch.cuda.stream(self.stream):
+            if ev:
+                ev["h2d0"].record(self.stream)
             self.xyz[:n].copy_(self.h_xyz[:n], non_blocking=True)
             self.offsets[:F + 1].copy_(self.h_off_in[:F + 1], non_blocking=True)
             self.leaves[:F].copy_(self.h_leaf_in[:F], non_blocking=True)
+            if ev:
+                ev["h2d1"].record(self.stream)
             if after is not None:
                 self.stream.wait_event(after)
+            if ev:
+                ev["dec0"].record(self.stream)
             st = vg.lib().vg_downsample_frames(
                 vg._ptr(self.xyz), n, vg._ptr(self.offsets), F, vg._ptr(self.origins),
                 vg._ptr(self.leaves), vg._ptr(self.keys), vg._ptr(self.centroids),
@@ -115,23 +137,42 @@ class _Slot:
             if st != 0:
                 raise vg.VGError(st, "vg_downsample_frames")
             self.decimated.record(self.stream)
+            if ev:
+                ev["dec1"].record(self.stream)
             self.h_offsets[:F + 1].copy_(self.out_offsets[:F + 1], non_blocking=True)
             self.h_origins[:F].copy_(self.origins[:F], non_blocking=True)
             self.h_error.copy_(self.error, non_blocking=True)
             self.done.record(self.stream)
         self.n_frames = F
 
-    def finish(self):
-        """Copies the rows back and splits them per request (after `done` fired)."""
+    def copy_back(self):
+        """Issues the copy of the rows back (after `done` fired) and returns at once;
+        `copied` fires when they are on the host."""
         F = self.n_frames
-        err = int(self.h_error[0])
-        offs = self.h_offsets[:F + 1].numpy().copy()
-        v = int(offs[-1])
+        self.err = int(self.h_error[0])
+        self.offs = self.h_offsets[:F + 1].numpy().copy()
+        v = int(self.offs[-1])
+        ev = self.ev
         with torch.cuda.stream(self.stream):
+            if ev:
+                ev["d2h0"].record(self.stream)
             self.h_keys[:v].copy_(self.keys[:v], non_blocking=True)
             self.h_centroids[:v].copy_(self.centroids[:v], non_blocking=True)
             self.h_counts[:v].copy_(self.counts[:v], non_blocking=True)
-        self.stream.synchronize()
+            if ev:
+                ev["d2h1"].record(self.stream)
+            self.copied.record(self.stream)
+        self.copying = True
+
+    def finish(self):
+        """Splits the copied rows per request and resolves the futures (after `copied`)."""
+        self.copied.synchronize()
+        if self.ev:
+            self.tl_entry["done"] = True
+        F = self.n_frames
+        err = self.err
+        offs = self.offs
+        v = int(offs[-1])
         keys = self.h_keys.numpy()[:v].view(np.uint64)
         cents = self.h_centroids.numpy()[:v]
         counts = self.h_counts.numpy()[:v].view(np.uint32)
@@ -146,6 +187,7 @@ class _Slot:
                                        origins[f].copy(), now - r.arrival, F))
         self.batch = []
         self.busy = False
+        self.copying = False
 
 
 def admit(queue: collections.deque, max_points: int, max_frames: int) -> list:
@@ -167,13 +209,21 @@ class Server:
 
     max_points   point budget of one batch (per slot); a request larger than it is refused.
     max_frames   most requests in one batch.
-    n_slots      device slots (>= 2 lets a batch's copies overlap another's decimation).
+    n_slots      device slots (>= 2 lets a batch's copies overlap another's decimation; with
+                 3, one batch can be copied in and another copied out while a third runs).
     mem_budget   device bytes the slots may hold; fewer slots are made if needed.
     """
 
-    def __init__(self, *, max_points: int = 8 * 307_200, max_frames: int = 16, n_slots: int = 2,
-                 method: str = "auto", device="cuda", mem_budget: Optional[int] = None):
+    def __init__(self, *, max_points: int = 8 * 307_200, max_frames: int = 16, n_slots: int = 3,
+                 method: str = "auto", device="cuda", mem_budget: Optional[int] = None,
+                 record_timeline: bool = False):
         dev = torch.device(device)
+        self._timeline: Optional[list] = [] if record_timeline else None
+        self._t0 = None
+        if record_timeline:  # the common origin of every batch's event times
+            self._t0 = torch.cuda.Event(enable_timing=True)
+            self._t0.record(torch.cuda.current_stream(dev))
+            self._t0.synchronize()
         self.slots = []
         used = 0
         for _ in range(max(1, n_slots)):
@@ -215,6 +265,13 @@ class Server:
             self._cv.notify()
         self._thread.join()
 
+    def timeline(self) -> list:
+        """Per finished batch (record_timeline=True): ms from the server's start on the
+        device clock of its copy in, decimation and copy out, as (start, end) pairs."""
+        if self._timeline is None:
+            raise ValueError("the server was made without record_timeline")
+        return _intervals(self._timeline, self._t0)
+
     def _admit(self) -> list:
         return admit(self._q, self.max_points, self.max_frames)
 
@@ -223,7 +280,10 @@ class Server:
         while True:
             progressed = False
             for s in self.slots:
-                if s.busy and s.done.query():
+                if s.busy and not s.copying and s.done.query():
+                    s.copy_back()  # the rows travel back while other batches run
+                    progressed = True
+                if s.copying and s.copied.query():
                     s.finish()
                     progressed = True
             with self._cv:
@@ -239,7 +299,7 @@ class Server:
                     # batches copy in and out concurrently, but decimate one at a time: two
                     # GPU-filling persistent grids of chained-scan kernels at once make each
                     # other's blocks wait on tiles that cannot get an SM
-                    free[0].launch(batch, self._last_decimated)
+                    free[0].launch(batch, self._last_decimated, self._timeline)
                     self._last_decimated = free[0].decimated
                     self.batches += 1
                     self.points += sum(r.xyz.shape[0] for r in batch)
@@ -264,6 +324,44 @@ def replay(server: Server, trace, pool, leaf: float, *, realtime: bool = True):
         futs.append((r, server.submit(r.stream, pool[r.frame], leaf)))
     out = [(r, f.result()) for r, f in futs]
     return out, time.perf_counter() - t0
+
+
+def _intervals(timeline: list, t0) -> list:
+    out = []
+    for b in list(timeline):
+        if not b["done"]:
+            continue  # not finished (or failed before its events were recorded)
+        t = {k: t0.elapsed_time(e) for k, e in b["ev"].items()}
+        out.append({"frames": b["frames"], "h2d": (t["h2d0"], t["h2d1"]),
+                    "decimate": (t["dec0"], t["dec1"]), "d2h": (t["d2h0"], t["d2h1"])})
+    return out
+
+
+def _union_overlap(a: tuple, spans: list) -> float:
+    """Length of interval a covered by the union of spans."""
+    lo, hi = a
+    cut = sorted((max(lo, s), min(hi, e)) for s, e in spans if min(hi, e) > max(lo, s))
+    total, end = 0.0, lo
+    for s, e in cut:
+        s = max(s, end)
+        if e > s:
+            total += e - s
+            end = e
+    return total
+
+
+def copy_overlap(timeline: list) -> dict:
+    """How much of the batches' copy time (in and out) ran while another batch was being
+    decimated: overlapped ms / copy ms, from Server.timeline()."""
+    copy_ms = over_ms = 0.0
+    for i, b in enumerate(timeline):
+        others = [o["decimate"] for j, o in enumerate(timeline) if j != i]
+        for key in ("h2d", "d2h"):
+            s, e = b[key]
+            copy_ms += max(0.0, e - s)
+            over_ms += _union_overlap((s, e), others)
+    return {"batches": len(timeline), "copy_ms": copy_ms, "overlapped_ms": over_ms,
+            "fraction": over_ms / copy_ms if copy_ms > 0 else 0.0}
 
 
 def latency_stats(results) -> dict:
@@ -298,8 +396,14 @@ class CloudPipeline:
     """
 
     def __init__(self, max_points: int, leaf: float, *, depth: int = 3, method: str = "auto",
-                 device="cuda"):
+                 device="cuda", record_timeline: bool = False):
         self.leaf = float(leaf)
+        self._timeline: Optional[list] = [] if record_timeline else None
+        self._t0 = None
+        if record_timeline:  # the common origin of every cloud's event times
+            self._t0 = torch.cuda.Event(enable_timing=True)
+            self._t0.record(torch.cuda.current_stream(torch.device(device)))
+            self._t0.synchronize()
         self.method = method
         self.max_points = int(max_points)
         dev = torch.device(device)
@@ -318,20 +422,35 @@ class CloudPipeline:
                  "nv": torch.zeros(1, dtype=torch.int64).pin_memory(),
                  "err": torch.zeros(1, dtype=torch.int32).pin_memory(),
                  "counted": torch.cuda.Event(), "done": torch.cuda.Event(), "v": 0,
-                 "state": "free"}
+                 "state": "free", "ev": None}
             self.slots.append(s)
 
     def _launch(self, s, host: torch.Tensor):
         n = host.shape[0]
         if n > self.max_points:
             raise ValueError("cloud larger than the pipeline's max_points")
+        ev = None
+        if self._timeline is not None:
+            ev = {k: torch.cuda.Event(enable_timing=True)
+                  for k in ("h2d0", "h2d1", "dec0", "dec1", "d2h0", "d2h1")}
+            self._timeline.append({"frames": 1, "ev": ev, "done": False})
+            s["tl"] = self._timeline[-1]
+        s["ev"] = ev
         with torch.cuda.stream(s["stream"]):
+            if ev:
+                ev["h2d0"].record(s["stream"])
             s["xyz"][:n].copy_(host, non_blocking=True)
+            if ev:
+                ev["h2d1"].record(s["stream"])
             if self._last_decimated is not None:  # one decimation on the device at a time
                 s["stream"].wait_event(self._last_decimated)
+            if ev:
+                ev["dec0"].record(s["stream"])
             vg.downsample_into(s["xyz"][:n], self.leaf, s["buf"], origin_from_min=True,
                                method=self.method, stream=s["stream"])
             s["decimated"].record(s["stream"])
+            if ev:
+                ev["dec1"].record(s["stream"])
             self._last_decimated = s["decimated"]
             s["nv"].copy_(s["buf"].num_voxels, non_blocking=True)
             s["err"].copy_(s["buf"].error, non_blocking=True)
@@ -345,19 +464,33 @@ class CloudPipeline:
         v = int(s["nv"][0])
         s["v"] = v
         b = s["buf"]
+        ev = s["ev"]
         with torch.cuda.stream(s["stream"]):
+            if ev:
+                ev["d2h0"].record(s["stream"])
             s["keys"][:v].copy_(b.keys[:v], non_blocking=True)
             s["cents"][:v].copy_(b.centroids[:v], non_blocking=True)
             s["counts"][:v].copy_(b.counts[:v], non_blocking=True)
+            if ev:
+                ev["d2h1"].record(s["stream"])
             s["done"].record(s["stream"])
         s["state"] = "copying"
 
     def _result(self, s):
         s["done"].synchronize()
+        if s["ev"]:
+            s["tl"]["done"] = True
         v = s["v"]
         s["state"] = "free"
         return (s["keys"].numpy()[:v].view(np.uint64), s["cents"].numpy()[:v],
                 s["counts"].numpy()[:v].view(np.uint32))
+
+    def timeline(self) -> list:
+        """Per cloud handed out (record_timeline=True): ms from the pipeline's start on the
+        device clock of its copy in, decimation and copy out, as (start, end) pairs."""
+        if self._timeline is None:
+            raise ValueError("the pipeline was made without record_timeline")
+        return _intervals(self._timeline, self._t0)
 
     def run(self, clouds):
         """clouds: iterable of float32 [N, 3] CPU tensors (pinned for overlap)."""

@@ -651,8 +651,9 @@ class Plan:
     def tune(self, xyz, frame_offsets, n_frames, origins, leaves, out_keys, out_centroids,
              out_counts, out_frame_offsets, out_error, *, origin_from_min=True, reps=5,
              stream: Optional[torch.cuda.Stream] = None):
-        """vg_plan_tune: time sort/sort_lsd/hash x grids {4,8,16}; keeps the fastest."""
-        ms = (ctypes.c_float * 9)()
+        """vg_plan_tune: time sort/sort_lsd/frame/hash x grids {4,8,16}; keeps the fastest
+        (-1: not timed, or the grouping recorded a device error)."""
+        ms = (ctypes.c_float * 12)()
         flags = ORIGIN_FROM_MIN if origin_from_min else 0
         st = lib().vg_plan_tune(
             self._h, _ptr(xyz), xyz.shape[0], _ptr(frame_offsets), int(n_frames), _ptr(origins),
@@ -660,7 +661,7 @@ class Plan:
             out_keys.shape[0], _ptr(out_frame_offsets), _ptr(out_error), flags, int(reps),
             _stream_ptr(stream), ms)
         _check(st, "vg_plan_tune")
-        names = [f"{m}@{g}" for m in ("sort", "sort_lsd", "hash") for g in (4, 8, 16)]
+        names = [f"{m}@{g}" for m in ("sort", "sort_lsd", "frame", "hash") for g in (4, 8, 16)]
         self.last_tuning = dict(zip(names, list(ms)))
         return self.last_tuning
 

@@ -104,7 +104,9 @@ def test_plan_graph_replay_and_tuner():
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):
         times = plan.tune(**b, reps=2, stream=s)
-        assert len(times) == 9 and all(t > 0 for t in times.values())
+        assert len(times) == 12
+        assert all(t > 0 for k, t in times.items() if not k.startswith("frame"))
+        assert all(times[f"frame@{g}"] == -1 for g in (4, 8, 16))  # several frames: not timed
         for _ in range(3):  # graph replays
             plan.run(**b, stream=s)
         s.synchronize()
@@ -115,13 +117,37 @@ def test_plan_graph_replay_and_tuner():
     assert torch.equal(b["out_keys"][:v], ref.keys)
     assert torch.equal(b["out_counts"][:v], ref.counts)
     assert torch.equal(b["out_centroids"][:v].view(torch.int32), ref.centroids.view(torch.int32))
-    for m in ("auto", "sort", "sort_lsd", "hash"):
+    for m in ("auto", "sort", "sort_lsd", "frame", "hash"):
         plan.configure(m, 8)
         assert plan.get()["method"] == m
         with torch.cuda.stream(s):
             plan.run(**b, stream=s, graph=False)
             s.synchronize()
         assert torch.equal(b["out_keys"][:v], ref.keys)
+    plan.close()
+
+
+def test_one_frame_tuning_times_the_bin_grouping():
+    frame = synth.rgbd_frame(640, 480, seed=12)
+    b = _plan_buffers([frame], [0.05])
+    plan = vg.Plan(1, b["xyz"].shape[0])
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        times = plan.tune(**b, reps=2, stream=s)
+    assert all(t > 0 for t in times.values())
+    best = min(times, key=times.get).split("@")[0]
+    assert plan.get()["method"] == best
+    plan.close()
+    # keys wider than 32 bits: the bin grouping records an error, so it is not a candidate
+    wide = np.array([[0, 0, 0], [30.0, 30.0, 30.0], [1, 2, 3]] * 100, np.float32)
+    b = _plan_buffers([wide], [0.01])
+    plan = vg.Plan(1, b["xyz"].shape[0])
+    with torch.cuda.stream(s):
+        times = plan.tune(**b, reps=1, stream=s)
+        s.synchronize()
+    assert all(times[f"frame@{g}"] == -1 for g in (4, 8, 16))
+    assert plan.get()["method"] != "frame"
+    assert int(b["out_error"].item()) == 0
     plan.close()
 
 

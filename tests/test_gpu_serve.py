@@ -82,3 +82,55 @@ def test_failed_batch_fails_its_requests_and_server_keeps_serving(monkeypatch):
     solo = vg.downsample(torch.from_numpy(frame).cuda(), 0.05)
     for r in results:
         assert np.array_equal(r.keys, solo.keys.cpu().numpy().view(np.uint64))
+
+
+def test_server_timeline_and_results_unchanged():
+    # a burst of 640x480 frames in batches of four: every result is its solo call's, the
+    # batches' decimations never overlap one another, and the copy overlap is measured
+    # (small here: packing a batch into pinned memory on the host takes longer than its
+    # decimation, so the device mostly waits)
+    pool = [synth.rgbd_frame(640, 480, seed=700 + k) for k in range(5)]
+    leaf = 0.05
+    solo = []
+    for x in pool:
+        r = vg.downsample(torch.from_numpy(x).cuda(), leaf)
+        solo.append((r.keys.cpu().numpy().view(np.uint64), r.centroids.cpu().numpy(),
+                     r.counts.cpu().numpy().view(np.uint32)))
+    srv = serve.Server(max_points=4 * 307_200, max_frames=4, n_slots=3, record_timeline=True)
+    futs = [(i % len(pool), srv.submit(i % 16, pool[i % len(pool)], leaf)) for i in range(48)]
+    results = [(k, f.result(timeout=120)) for k, f in futs]
+    tl = srv.timeline()
+    srv.close()
+    for k, res in results:
+        keys, cents, counts = solo[k]
+        assert np.array_equal(res.keys, keys) and np.array_equal(res.counts, counts)
+        assert np.array_equal(res.centroids.view(np.int32), cents.view(np.int32))
+    assert len(tl) >= 6 and sum(b["frames"] for b in tl) == 48
+    dec = sorted(b["decimate"] for b in tl)
+    assert all(a[1] <= b[0] + 1e-3 for a, b in zip(dec, dec[1:]))
+    ov = serve.copy_overlap(tl)
+    assert 0.0 <= ov["fraction"] <= 1.0 and ov["copy_ms"] > 0
+
+
+def test_pipeline_copies_overlap_decimation_and_results_unchanged():
+    # 5M-point clouds through the three-slot pipeline: while one cloud is decimated, the
+    # next is copied in and the last one's rows copied out
+    n = 5_000_000
+    clouds = [torch.from_numpy(synth.fused_map(n, seed=40 + k)).pin_memory() for k in range(2)]
+    leaf = 0.02
+    solo = []
+    for c in clouds:
+        r = vg.downsample(c.cuda(), leaf)
+        solo.append((r.keys.cpu().numpy().view(np.uint64), r.centroids.cpu().numpy(),
+                     r.counts.cpu().numpy().view(np.uint32)))
+    pipe = serve.CloudPipeline(n, leaf, depth=3, record_timeline=True)
+    order = [k % 2 for k in range(8)]
+    for k, (keys, cents, counts) in zip(order, pipe.run(clouds[k] for k in order)):
+        assert np.array_equal(keys, solo[k][0]) and np.array_equal(counts, solo[k][2])
+        assert np.array_equal(cents.view(np.int32), solo[k][1].view(np.int32))
+    tl = pipe.timeline()
+    assert len(tl) == 8
+    dec = sorted(b["decimate"] for b in tl)
+    assert all(a[1] <= b[0] + 1e-3 for a, b in zip(dec, dec[1:]))
+    ov = serve.copy_overlap(tl)
+    assert ov["fraction"] > 0.3, ov
