@@ -165,10 +165,12 @@ __global__ __launch_bounds__(kPartThreads, 3) void msd_part_kernel(
     sm.cnt[t] = 0;
     __syncthreads();
     uint32_t k[kPartItems], slot[kPartItems];
+    unsigned long long p[kPartItems];  // loaded with the keys: both latencies overlap
 #pragma unroll
     for (int j = 0; j < kPartItems; ++j) {
       const uint32_t i = uint32_t(j) * kPartThreads + uint32_t(t);
       k[j] = i < m ? __ldcs(kin + base + i) : kFull;
+      p[j] = i < m ? __ldcs(pin + base + i) : 0ull;
     }
 #pragma unroll
     for (int j = 0; j < kPartItems; ++j) {
@@ -189,12 +191,6 @@ __global__ __launch_bounds__(kPartThreads, 3) void msd_part_kernel(
         slot[j] += sm.loff[((k[j] & kmask) >> shift) & mask];
         sm.keys[slot[j]] = k[j];
       }
-    unsigned long long p[kPartItems];
-#pragma unroll
-    for (int j = 0; j < kPartItems; ++j) {
-      const uint32_t i = uint32_t(j) * kPartThreads + uint32_t(t);
-      p[j] = slot[j] != kFull ? __ldcs(pin + base + i) : 0ull;
-    }
 #pragma unroll
     for (int j = 0; j < kPartItems; ++j)
       if (slot[j] != kFull) sm.pay[slot[j]] = p[j];
