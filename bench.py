@@ -162,7 +162,7 @@ class ClockSampler:
 
 # the sources of the kernels the bench step launches (their traffic is profiled)
 STEP_KERNEL_SOURCES = ("vg_device.cuh", "vg_internal.h", "vg_keys.cu", "vg_msd.cu",
-                       "vg_reduce.cu", "vg_sort.cu", "vg_stream.cuh")
+                       "vg_reduce.cu", "vg_rows.cuh", "vg_sort.cu", "vg_stream.cuh")
 
 
 def kernel_source_hash():

@@ -300,11 +300,13 @@ __global__ __launch_bounds__(256) void frame_count_kernel(const State* st,
 }
 
 // ---- rows ---------------------------------------------------------------------------------
-struct FrSmem {
-  // biased offset sums of every key of the bin, 64 bits as two 32-bit words per axis: an
-  // addition (below 2^31) that wraps the low word carries one into the high word
+struct alignas(16) FrSmem {
+  // biased offset sums of every key of the bin, 64 bits a sum: a 32-bit low word per axis,
+  // and the three axes' carries (an addition below 2^31 that wraps a low word adds one)
+  // packed 21 bits apart in one 64-bit word (fewer than 2^32 points keep every carry
+  // count below 2^21, so no field overflows into the next)
   uint32_t lo[3][kFrSpan];
-  uint32_t hi[3][kFrSpan];
+  unsigned long long hi[kFrSpan];
   uint32_t cnt[kFrSpan];               // entries of every key of the bin
   uint32_t bits[2][kFrWords];          // occupancy of alternate bins (kept clean)
   uint16_t wrank[kFrWords];            // occupied keys before every word
@@ -356,7 +358,7 @@ __device__ __forceinline__ void frame_accumulate(FrSmem& sm, uint32_t* bits,
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
           const uint32_t old = atomicAdd(&sm.lo[a][o], v[a + 1]);
-          if (old + v[a + 1] < old) atomicAdd(&sm.hi[a][o], 1u);
+          if (old + v[a + 1] < old) atomicAdd(&sm.hi[o], 1ull << (21 * a));
         }
       }
     }
@@ -404,15 +406,15 @@ __device__ __forceinline__ void frame_rows(FrSmem& sm, const uint32_t* bits, uin
     const uint32_t r = uint32_t(sm.wrank[w]) + __popc(bits[w] & ((1u << (off & 31u)) - 1u));
     float sf[3];
     long long s64[3];
+    const unsigned long long carries = sm.hi[off];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      const unsigned long long b =
-          (static_cast<unsigned long long>(sm.hi[a][off]) << 32) | sm.lo[a][off];
+      const unsigned long long b = (((carries >> (21 * a)) & 0x1fffffull) << 32) | sm.lo[a][off];
       s64[a] = static_cast<long long>(b) + static_cast<long long>(n) * kQMin;
       sf[a] = __ll2float_rn(s64[a]);
       sm.lo[a][off] = 0;
-      sm.hi[a][off] = 0;
     }
+    sm.hi[off] = 0;
     sm.cnt[off] = 0;
     put_row32(rc, out, row0 + r, key0 + off, n, sf, s64, err);
   }
@@ -467,8 +469,9 @@ __global__ __launch_bounds__(kFrThreads) void frame_bin_kernel(
   rc.leaf1 = fs[0].leaf;
   for (uint32_t i = t; i < kFrSpan; i += kFrThreads) {
     sm.cnt[i] = 0;
+    sm.hi[i] = 0;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) sm.lo[a][i] = sm.hi[a][i] = 0;
+    for (int a = 0; a < 3; ++a) sm.lo[a][i] = 0;
   }
   for (int w = t; w < 2 * kFrWords; w += kFrThreads) sm.bits[w / kFrWords][w % kFrWords] = 0;
   int jb = 0;
