@@ -92,10 +92,14 @@ typedef enum {
                                 bucket grouping (same rows; for comparison)              */
 #define VG_USE_GRAPH 64      /* vg_downsample_batch: capture / replay a CUDA graph      */
 #define VG_SORT_FRAME 128    /* SORT for one camera frame (vg_downsample, or a batch of
-                                one frame): the keys are counted into bins of 2^12
-                                consecutive keys, scattered once, and every bin is reduced
-                                in one block's shared memory -- five kernels, for clouds
-                                whose launches cost more than their bytes.  Needs 32-bit
+                                one frame), for clouds whose launches cost more than their
+                                bytes.  A frame of up to vg_frame_one_launch_points()
+                                points is grouped by ONE cooperative launch: an occupancy
+                                bitmap over the keys ranks the cells in key order and the
+                                cells' sums are added at their rows.  A larger frame is
+                                counted into bins of 2^12 consecutive keys, scattered
+                                once, and every bin reduced in one block's shared memory
+                                (five kernels after the extent kernel).  Needs 32-bit
                                 keys (the Morton code of the frame's per-axis maximum
                                 index below 2^32 - 1), else the call records
                                 VG_ERR_RANGE.  Several frames, point_to_voxel or
@@ -119,6 +123,12 @@ VG_API int vg_version(void);
 /* Bytes of device workspace vg_downsample needs for a cloud of n_points with `flags`.
  * Pure host function; returns 0 for a negative n_points. */
 VG_API size_t vg_downsample_workspace_bytes(int64_t n_points, int flags);
+
+/* Largest frame, in points, that VG_SORT_FRAME groups in one cooperative launch on the
+ * current device (its grid -- one block of 1024 threads per SM -- holding 8 points a
+ * thread); 0 when the device cannot run that launch.  posed != 0 asks for calls with a pose
+ * or height limits.  Larger frames take the bin grouping.  Reads device attributes only. */
+VG_API int64_t vg_frame_one_launch_points(int posed);
 
 /*
  * vg_downsample -- steps a1..a5: origin (optional), voxel key per point, grouping by

@@ -117,8 +117,11 @@ int method_of(int flags) {
 size_t frames_workspace_bytes(int64_t n, int frames, int flags) {
   if (n < 0 || frames < 1) return 0;
   if (method_of(flags) == VG_METHOD_HASH) return hash_layout(n, frames).total;
-  const size_t base = sort_layout(n, frames).total;
-  return (flags & VG_SORT_FRAME) != 0 ? frame_layout(n, base).total : base;
+  const SortLayout L = sort_layout(n, frames);
+  if ((flags & VG_SORT_FRAME) == 0) return L.total;
+  // the bin grouping after the sort layout, or the one-launch grouping after the frame state
+  const size_t a = frame_layout(n, L.total).total, b = fused_layout(n, L.lb_a).total;
+  return a > b ? a : b;
 }
 
 vg_status check_outputs(int64_t n, const float* xyz, uint64_t* out_keys, float* out_centroids,
@@ -159,6 +162,8 @@ vg_status run_frames(const float* xyz, const FramesArg& fr, bool from_min, const
     const bool maybe_msd = frn.allow_narrow && !frn.lsd_narrow;
     // VG_SORT_FRAME: one frame, no point_to_voxel or attributes (else the plain sort path)
     const bool frame_path = (flags & VG_SORT_FRAME) != 0 && F == 1 && frn.allow_narrow && n > 0;
+    // a frame that one cooperative launch holds: that launch alone (it finds the extents)
+    const bool fused = frame_path && frame_fused_fits(n, posed(frn));
     const bool have_extent = from_min || F > 1 || frn.allow_narrow;
     const SortLayout L = sort_layout(n, F);
     State* st = reinterpret_cast<State*>(ws + L.state);
@@ -182,7 +187,8 @@ vg_status run_frames(const float* xyz, const FramesArg& fr, bool from_min, const
     cudaError_t e = cudaMemsetAsync(ws, 0, frame_path ? L.lb_a : L.zero_bytes, stream);
     if (e == cudaSuccess && maybe_msd && !frame_path)  // points per bucket
       e = cudaMemsetAsync(ws + L.mhist, 0, L.mvcnt - L.mhist, stream);
-    if (e == cudaSuccess && out_error) e = cudaMemsetAsync(out_error, 0, sizeof(int32_t), stream);
+    if (e == cudaSuccess && out_error && !fused)  // (the one-launch kernel clears it)
+      e = cudaMemsetAsync(out_error, 0, sizeof(int32_t), stream);
     if (e == cudaSuccess && !frame_path)
       e = cudaMemsetAsync(out.num_voxels, 0, sizeof(int64_t), stream);
     if (e == cudaSuccess && out.frame_offsets && !frame_path)
@@ -190,6 +196,13 @@ vg_status run_frames(const float* xyz, const FramesArg& fr, bool from_min, const
     if (e == cudaSuccess && out.p2v && n > 0)
       e = cudaMemsetAsync(out.p2v, 0xff, size_t(n) * sizeof(int32_t), stream);
     mark(stage++, stream);
+    if (fused) {
+      if (e == cudaSuccess)
+        e = launch_frame_fused(xyz, frn, st, fs, ws, fused_layout(n, L.lb_a), out, spins, err,
+                               stream);
+      for (int k = 0; k < 1 + 1 + 3 + kMaxPasses + 1; ++k) mark(stage++, stream);
+      return cuda_status(e);
+    }
     if (e == cudaSuccess && have_extent) {
       if (frame_path) {
         const FrameLayout FL = frame_layout(n, L.total);
@@ -348,6 +361,8 @@ vg_status vg_debug_wait_timeout(uint32_t* scratch_words, uint32_t limit, int32_t
 size_t vg_downsample_workspace_bytes(int64_t n_points, int flags) {
   return frames_workspace_bytes(n_points, 1, flags);
 }
+
+int64_t vg_frame_one_launch_points(int posed) { return frame_fused_max_points(posed != 0); }
 
 size_t vg_batch_workspace_bytes(int64_t n_total, int n_frames, int flags) {
   if (n_frames < 1 || n_frames > kMaxFrames) return 0;

@@ -39,6 +39,29 @@ constexpr int kFrPer = kFrSpan / kFrThreads;  // keys of a bin per thread
 static_assert(kFrWords <= 4 * 32, "one warp scans a bin's occupancy words, four a lane");
 static_assert(kFrScanBins == 16 * 256, "prefix tile: 16 bins per thread");
 
+// Runs of equal keys among a warp's 32 consecutive points: a segmented scan sums each run's
+// offsets and points (32 offsets of 21 bits fit 32 bits) into v = {x, y, z, points} of
+// its last lane, which returns true (invalid points, key all ones, form no run).
+__device__ __forceinline__ bool warp_run(uint32_t k, uint64_t pw, bool ok, uint32_t v[4]) {
+  const uint32_t lane = threadIdx.x & 31u;
+  v[0] = uint32_t(pw) & 0x1fffffu;
+  v[1] = uint32_t(pw >> 21) & 0x1fffffu;
+  v[2] = uint32_t(pw >> 42) & 0x1fffffu;
+  v[3] = ok ? 1u : 0u;
+  const uint32_t prev = __shfl_up_sync(kFullMask, k, 1);
+  const uint32_t heads = __ballot_sync(kFullMask, lane == 0 || k != prev);
+  const uint32_t head = 31u - __clz(heads & (0xffffffffu >> (31u - lane)));
+#pragma unroll
+  for (uint32_t d = 1; d < 32; d <<= 1) {
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const uint32_t yv = __shfl_up_sync(kFullMask, v[a], d);
+      if (lane >= head + d) v[a] += yv;
+    }
+  }
+  return ok && (lane == 31u || ((heads >> (lane + 1u)) & 1u) != 0u);
+}
+
 // ---- keys, runs and places in bins ---------------------------------------------------------
 // Lane l of warp w takes point start + 256 s + 32 w + l of every chunk (s = 0..3), so a
 // warp holds 32 consecutive points at a time: neighbouring pixels of a camera frame, which
@@ -98,21 +121,8 @@ __global__ __launch_bounds__(kStreamThreads) void frame_key_kernel(
       if (!ok) k = kFullMask;
       nvalid += ok;
       kmax = ok && k > kmax ? k : kmax;
-      // runs of equal keys among the warp's 32 consecutive points
-      uint32_t v[4] = {uint32_t(pw) & 0x1fffffu, uint32_t(pw >> 21) & 0x1fffffu,
-                       uint32_t(pw >> 42) & 0x1fffffu, ok ? 1u : 0u};
-      const uint32_t prev = __shfl_up_sync(kFullMask, k, 1);
-      const uint32_t heads = __ballot_sync(kFullMask, lane == 0 || k != prev);
-      const uint32_t head = 31u - __clz(heads & (0xffffffffu >> (31u - lane)));
-#pragma unroll
-      for (uint32_t d = 1; d < 32; d <<= 1) {
-#pragma unroll
-        for (int a = 0; a < 4; ++a) {
-          const uint32_t yv = __shfl_up_sync(kFullMask, v[a], d);
-          if (lane >= head + d) v[a] += yv;
-        }
-      }
-      const bool emit = ok && (lane == 31u || ((heads >> (lane + 1u)) & 1u) != 0u);
+      uint32_t v[4];
+      const bool emit = warp_run(k, pw, ok, v);
       const uint32_t em = __ballot_sync(kFullMask, emit);
       uint32_t q = 0;
       if (emit) {
@@ -511,13 +521,555 @@ __global__ __launch_bounds__(kFrThreads) void frame_bin_kernel(
   }
 }
 
+// ---- the whole frame in one launch --------------------------------------------------------
+// A cooperative grid (every block resident, one a SM) takes the frame in phases separated
+// by grid barriers, each point held by one thread (point (s G' + w) 32 + lane for step s,
+// w = the warp's index in the grid, G' = the grid's warps, so a warp holds 32 consecutive
+// points a step):
+//   0  extents (the origin kernel's minima and maxima); the bitmap and scan words cleared;
+//   1  key and corner offsets of every point, warp runs of equal keys kept in shared memory,
+//      one bit a run set in the key bitmap -- or, for keys of more than kFzDenseBits bits,
+//      in a bitmap of blocks of 2^kFzBlockBits keys, whose set bits a chained scan numbers
+//      (slots) before each run sets its key's bit in its slot's 16-word bitmap;
+//   2  a chained scan over the bitmap words gives every occupied key its row (keys in
+//      order: the rank of its bit), writes the row's key and clears its sums;
+//   3  every run adds its points and offset sums at its row (global atomics);
+//   4  every row's centroid (put_row32: the other groupings' formula and integer sums, so
+//      the rows are bit-identical to theirs).
+// Every wait is bounded (kErrTimeout after the limit), every index read back from scratch
+// is checked against its buffer, and every block passes every barrier, so an error never
+// leaves a block waiting on another.
+struct FzArgs {
+  const float* xyz;
+  FramesArg fr;
+  State* st;
+  FrameState* fs;
+  uint32_t* bits;      // kFzDenseWords words
+  uint32_t* rank;      // kFzDenseWords words
+  uint32_t* slotmap;   // 2^(32 - kFzBlockBits) words
+  uint32_t* slotbin;   // rows_cap words
+  uint32_t* sbits;     // 16 rows_cap words
+  uint32_t* srank;     // 16 rows_cap words
+  unsigned long long* acc;  // 3 arrays of rows_cap: x sum + (points << 42), y sum, z sum
+  uint32_t* rowkey;    // rows_cap words
+  uint32_t* stat;      // 2 kFzMaxGrid words
+  SegOut out;
+  int64_t rows_cap;    // the frame's points (bounds slots and rows)
+  int per;             // points a thread
+  uint32_t spin_limit;
+  int* err;
+};
+
+constexpr int kFzAccShift = 42;  // points above the x sum (a sum of n < 2^21 offsets < 2^42)
+constexpr unsigned long long kFzAccMask = (1ull << kFzAccShift) - 1ull;
+
+// Grid barrier on an arrival counter the call zeroes; `target` (thread 0's) grows by the
+// grid each barrier.  The wait is bounded.
+__device__ __forceinline__ void fz_grid_sync(uint32_t* ctr, uint32_t& target, uint32_t spin,
+                                             int* err) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    target += gridDim.x;
+    __threadfence();
+    atomicAdd(ctr, 1u);
+    uint32_t spins = 0;
+    while (ld_acquire(ctr) < target) {
+      if (++spins > spin) {
+        set_error(err, kErrTimeout);
+        break;
+      }
+      if (spins > 16) __nanosleep(32);
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+// Ranking the set bits of words [0, nw) in word order takes two steps around a grid
+// barrier: block b takes a contiguous slice of the words and publishes the slice's set
+// bits in agg[b]; after the barrier every block sums its predecessors' totals (all at
+// once, one per thread) for its slice's first rank, and ranks the slice tile by tile
+// (thread t: word t of a tile of kFzThreads consecutive words), so that the 32 words of a
+// warp are consecutive and so are their ranks.
+__device__ __forceinline__ void fz_slice(uint32_t nw, uint32_t* s0, uint32_t* s1) {
+  const uint32_t q = (nw + gridDim.x - 1u) / gridDim.x;
+  *s0 = min(nw, blockIdx.x * q);
+  *s1 = min(nw, *s0 + q);
+}
+
+// Step one: agg[blockIdx.x] = set bits of the block's slice.  Contains __syncthreads.
+__device__ __forceinline__ void fz_count(const uint32_t* w, uint32_t nw, uint32_t* agg,
+                                         uint32_t* tmp) {
+  uint32_t s0, s1;
+  fz_slice(nw, &s0, &s1);
+  uint32_t mine = 0;
+  for (uint32_t i = s0 + threadIdx.x; i < s1; i += kFzThreads) mine += __popc(__ldcg(w + i));
+  uint32_t total;
+  (void)block_excl_scan(mine, &total, tmp);
+  if (threadIdx.x == 0) agg[blockIdx.x] = total;
+}
+
+// Lane-parallel walk over the set bits of a warp's 32 consecutive words: lane i holds word
+// index wi, bits vi and ri = the rank of its first set bit, the ranks consecutive across
+// the lanes (r[i+1] = r[i] + popc(v[i])).  The bits are taken 32 at a time, lane l the
+// (j + l)-th: its word is the last lane whose first rank is at most that (a binary search
+// over the lanes), its position the matching set bit of that word; f(word, position, rank)
+// then runs with consecutive ranks across the lanes, so row writes coalesce.
+template <typename F>
+__device__ __forceinline__ void warp_expand(uint32_t wi, uint32_t vi, uint32_t ri, F f) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t r0 = __shfl_sync(kFullMask, ri, 0);
+  const uint32_t e = ri - r0;
+  const uint32_t total = __shfl_sync(kFullMask, e + __popc(vi), 31);
+  for (uint32_t j = 0; j < total; j += 32) {
+    const uint32_t b = j + lane;
+    uint32_t lo = 0;
+#pragma unroll
+    for (uint32_t step = 16; step; step >>= 1) {
+      const uint32_t ec = __shfl_sync(kFullMask, e, lo + step);
+      if (ec <= b) lo += step;
+    }
+    const uint32_t eo = __shfl_sync(kFullMask, e, lo);
+    const uint32_t vo = __shfl_sync(kFullMask, vi, lo);
+    const uint32_t wo = __shfl_sync(kFullMask, wi, lo);
+    if (b < total) f(wo, __fns(vo, 0u, int(b - eo + 1u)), r0 + b);
+  }
+}
+
+// Step two (after a grid barrier): rk[i] = set bits before word i for the block's slice;
+// with kExpand, f(word, position, rank) for every set bit (warp_expand).  Returns the grand
+// total (in every block).  The grid has at most kFzThreads blocks.  Contains
+// __syncthreads.
+struct FzNoBits {
+  __device__ void operator()(uint32_t, uint32_t, uint32_t) const {}
+};
+
+template <bool kExpand, typename F>
+__device__ __forceinline__ uint32_t fz_rank(const uint32_t* w, uint32_t* rk, uint32_t nw,
+                                            const uint32_t* agg, uint32_t* tmp,
+                                            uint32_t* s_first, F f) {
+  uint32_t s0, s1;
+  fz_slice(nw, &s0, &s1);
+  const uint32_t g = threadIdx.x < gridDim.x ? __ldcg(agg + threadIdx.x) : 0u;
+  uint32_t all;
+  const uint32_t pre = block_excl_scan(g, &all, tmp);
+  if (threadIdx.x == blockIdx.x) *s_first = pre;  // the blocks before this one
+  __syncthreads();
+  uint32_t base = *s_first;
+  for (uint32_t t0 = s0; t0 < s1; t0 += kFzThreads) {  // (the same trips in every thread)
+    const uint32_t i = t0 + threadIdx.x;
+    const uint32_t v = i < s1 ? __ldcg(w + i) : 0u;
+    uint32_t tot;
+    const uint32_t r = base + block_excl_scan(__popc(v), &tot, tmp);
+    if (i < s1) rk[i] = r;
+    if (kExpand) warp_expand(i, v, r, f);
+    base += tot;
+  }
+  return all;
+}
+
+template <bool kPosed>
+__global__ __launch_bounds__(kFzThreads, 1) void frame_fused_kernel(const FzArgs a) {
+  extern __shared__ uint4 fz_runs[];  // [kFzPer][kFzThreads]: key, x, y, z | points << 26
+  __shared__ float red[kFzThreads / 32][6];
+  __shared__ uint32_t tmp[kFzThreads / 32];
+  __shared__ uint32_t s_excl;
+  __shared__ float s_o[3], s_leaf, s_rleaf, s_inv;
+  __shared__ uint32_t s_kb;
+  __shared__ int s_go;
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  const uint32_t gthreads = gridDim.x * kFzThreads;
+  const int64_t n = a.fr.n;
+  const int64_t gwarps = int64_t(gridDim.x) * (kFzThreads / 32);
+  const int64_t gw = int64_t(blockIdx.x) * (kFzThreads / 32) + warp;
+  int* err = a.err;
+  uint32_t target = 0;
+
+  // The call clears the error word here, before the first barrier (no step records an
+  // error before it).  One frame: offsets, when given, must be {0, n}.
+  if (blockIdx.x == 0 && threadIdx.x == 0) *err = 0;
+  const bool bad_offsets =
+      a.fr.offsets && (__ldg(a.fr.offsets) != 0 || __ldg(a.fr.offsets + 1) != n);
+  Pose P;
+  if (kPosed) load_pose(a.fr, 0, P);
+
+  // ---- phase 0: extents; the bitmap's first kFzZeroWords words cleared ----
+  for (uint32_t i = blockIdx.x * kFzThreads + threadIdx.x; i < kFzZeroWords / 4; i += gthreads)
+    reinterpret_cast<uint4*>(a.bits)[i] = make_uint4(0u, 0u, 0u, 0u);
+  {
+    float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+#pragma unroll 2
+    for (int s = 0; s < (bad_offsets ? 0 : a.per); ++s) {
+      const int64_t p = (int64_t(s) * gwarps + gw) * 32 + lane;
+      if (p >= n) continue;
+      float x = __ldg(a.xyz + 3 * p), y = __ldg(a.xyz + 3 * p + 1), z = __ldg(a.xyz + 3 * p + 2);
+      if (kPosed) pose_point(P, x, y, z);
+      if (point_valid(x, y, z)) {
+        mn[0] = fminf(mn[0], x), mx[0] = fmaxf(mx[0], x);
+        mn[1] = fminf(mn[1], y), mx[1] = fmaxf(mx[1], y);
+        mn[2] = fminf(mn[2], z), mx[2] = fmaxf(mx[2], z);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+#pragma unroll
+      for (int off = 16; off; off >>= 1) {
+        mn[c] = fminf(mn[c], __shfl_xor_sync(kFullMask, mn[c], off));
+        mx[c] = fmaxf(mx[c], __shfl_xor_sync(kFullMask, mx[c], off));
+      }
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        red[warp][c] = mn[c];
+        red[warp][3 + c] = mx[c];
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+      const int c = threadIdx.x;
+      float m = INFINITY, M = -INFINITY;
+      for (int w = 0; w < kFzThreads / 32; ++w) {
+        m = fminf(m, red[w][c]);
+        M = fmaxf(M, red[w][3 + c]);
+      }
+      if (m != INFINITY) {
+        atomicMax(&a.fs[0].ord_min_inv[c], ~float_to_ordered(m));
+        atomicMax(&a.fs[0].ord_max[c], float_to_ordered(M));
+      }
+    }
+  }
+  fz_grid_sync(&a.st->fz_bar, target, a.spin_limit, err);
+  if (bad_offsets) {  // (uniform: every block read the same offsets)
+    if (blockIdx.x == 0 && threadIdx.x == 0) set_error(err, kErrInvalidArg);
+    return;
+  }
+
+  // ---- the frame's origin, leaf and key width (the same in every block) ----
+  if (threadIdx.x == 0) {
+    const float leaf = a.fr.leaves ? __ldg(a.fr.leaves) : a.fr.leaf;
+    const bool bad_leaf = !(leaf > 0.0f) || !isfinite(leaf);
+    const bool any = __ldcg(&a.fs[0].ord_min_inv[0]) != 0u;
+    float o[3];
+    for (int c = 0; c < 3; ++c) {
+      if (a.fr.origin_in) {
+        o[c] = __ldg(a.fr.origin_in + c);
+      } else {
+        const uint32_t u = __ldcg(&a.fs[0].ord_min_inv[c]);
+        o[c] = u == 0u ? 0.0f : ordered_to_float(~u);
+      }
+      s_o[c] = o[c];
+    }
+    uint64_t kbound = 0;
+    if (any && !bad_leaf) {
+      uint32_t ii[3];
+      bool ok = true;
+      for (int c = 0; c < 3; ++c)
+        ok = ok && axis_index(ordered_to_float(__ldcg(&a.fs[0].ord_max[c])), o[c], leaf, &ii[c]);
+      kbound = ok ? morton3(ii[0], ii[1], ii[2]) : ~0ull >> 1;
+    }
+    const uint32_t kb = kbound ? 64u - __clzll(static_cast<long long>(kbound)) : 0u;
+    const bool narrow = kb <= 32u && kbound < 0xffffffffull;
+    s_leaf = leaf;
+    s_rleaf = fast_leaf(leaf) ? __fdiv_rn(1.0f, leaf) : 0.0f;
+    s_inv = quant_inv_unit(leaf);
+    s_kb = kb;
+    s_go = !bad_leaf && narrow;
+    if (blockIdx.x == 0) {
+      for (int c = 0; c < 3; ++c) {
+        a.fs[0].origin[c] = o[c];
+        if (!a.fr.origin_in && a.fr.origin_out) a.fr.origin_out[c] = o[c];
+      }
+      a.fs[0].leaf = leaf;
+      a.st->key_shift = 64;
+      a.st->nframes = 1;
+      a.st->narrow = narrow ? 1u : 0u;
+      a.st->maxkey = kbound;
+      if (bad_leaf) set_error(err, kErrInvalidArg);
+      else if (!narrow) set_error(err, kErrRange);  // keys of more than 32 bits
+      if (bad_leaf || !narrow) {
+        *a.out.num_voxels = 0;
+        if (a.out.frame_offsets) a.out.frame_offsets[0] = a.out.frame_offsets[1] = 0;
+      }
+    }
+  }
+  __syncthreads();
+  if (!s_go) return;  // (uniform across the grid)
+  const uint32_t kb = s_kb;
+  const bool dense = kb <= uint32_t(kFzDenseBits);
+  const float o[3] = {s_o[0], s_o[1], s_o[2]};
+  const float leaf = s_leaf, rleaf = s_rleaf, inv_unit = s_inv;
+  if (dense && kb > uint32_t(kFzZeroBits)) {  // the rest of a wider key bitmap (uniform)
+    const uint32_t end = (1u << (kb - 5u)) / 4u;
+    for (uint32_t i = uint32_t(kFzZeroWords / 4) + blockIdx.x * kFzThreads + threadIdx.x; i < end;
+         i += gthreads)
+      reinterpret_cast<uint4*>(a.bits)[i] = make_uint4(0u, 0u, 0u, 0u);
+    fz_grid_sync(&a.st->fz_bar, target, a.spin_limit, err);
+  }
+
+  // ---- phase 1: keys, runs, bitmap ----
+  {
+    bool range_bad = false;
+    float nx[3];  // the next point's coordinates, loaded one step ahead
+    {
+      const int64_t p = gw * 32 + lane;
+      const bool in = p < n;
+      nx[0] = in ? __ldg(a.xyz + 3 * p) : __int_as_float(0x7fc00000);
+      nx[1] = in ? __ldg(a.xyz + 3 * p + 1) : nx[0];
+      nx[2] = in ? __ldg(a.xyz + 3 * p + 2) : nx[0];
+    }
+    for (int s = 0; s < a.per; ++s) {
+      float x = nx[0], y = nx[1], z = nx[2];
+      if (s + 1 < a.per) {
+        const int64_t p = (int64_t(s + 1) * gwarps + gw) * 32 + lane;
+        const bool in = p < n;
+        nx[0] = in ? __ldg(a.xyz + 3 * p) : __int_as_float(0x7fc00000);
+        nx[1] = in ? __ldg(a.xyz + 3 * p + 1) : nx[0];
+        nx[2] = in ? __ldg(a.xyz + 3 * p + 2) : nx[0];
+      }
+      if (kPosed) pose_point(P, x, y, z);
+      uint32_t k = kFullMask;
+      uint64_t pw = 0;
+      const bool ok = narrow_entry(x, y, z, o, leaf, rleaf, inv_unit, 0u, 64u, &k, &pw,
+                                   &range_bad);
+      if (!ok) k = kFullMask;
+      uint32_t v[4];
+      const bool emit = warp_run(k, pw, ok, v);
+      fz_runs[s * kFzThreads + threadIdx.x] =
+          emit ? make_uint4(k, v[0], v[1], v[2] | (v[3] << 26)) : make_uint4(kFullMask, 0u, 0u, 0u);
+      // one atomic a bitmap word among the warp's runs
+      const uint32_t em = __ballot_sync(kFullMask, emit);
+      if (emit) {
+        const uint32_t word = dense ? (k >> 5) : (k >> (kFzBlockBits + 5));
+        const uint32_t bit = 1u << (dense ? (k & 31u) : ((k >> kFzBlockBits) & 31u));
+        const uint32_t peers = __match_any_sync(em, word);
+        const uint32_t orv = __reduce_or_sync(peers, bit);
+        if (int(lane) == __ffs(peers) - 1) atomicOr(a.bits + word, orv);
+      }
+    }
+    if (__any_sync(kFullMask, range_bad) && lane == 0) set_error(err, kErrRange);
+  }
+  fz_grid_sync(&a.st->fz_bar, target, a.spin_limit, err);
+
+  uint32_t* wbits = a.bits;
+  uint32_t* wrank = a.rank;
+  uint32_t nw = kb > 5u ? 1u << (kb - 5u) : 1u;
+  uint32_t nslots = 0;
+  if (!dense) {
+    // ---- phase 1b: occupied blocks numbered (slots); their bitmaps cleared ----
+    const uint32_t nw1 = kb > uint32_t(kFzBlockBits + 5) ? 1u << (kb - kFzBlockBits - 5u) : 1u;
+    fz_count(a.bits, nw1, a.stat, tmp);
+    fz_grid_sync(&a.st->fz_bar, target, a.spin_limit, err);
+    uint32_t* slotmap = a.slotmap;
+    uint32_t* slotbin = a.slotbin;
+    const int64_t cap = a.rows_cap;
+    const uint32_t slots = fz_rank<true>(
+        a.bits, a.rank, nw1, a.stat, tmp, &s_excl,
+        [&](uint32_t i, uint32_t bit, uint32_t slot) {
+          if (slot >= cap) return;  // (more slots than points: reported below)
+          const uint32_t blk = (i << 5) | bit;
+          slotmap[blk] = slot;
+          slotbin[slot] = blk;
+        });
+    nslots = static_cast<uint32_t>(min(int64_t(slots), a.rows_cap));
+    if (slots > nslots && blockIdx.x == 0 && threadIdx.x == 0) set_error(err, kErrInvalidArg);
+    for (uint32_t i = blockIdx.x * kFzThreads + threadIdx.x; i < nslots * 4u; i += gthreads)
+      reinterpret_cast<uint4*>(a.sbits)[i] = make_uint4(0u, 0u, 0u, 0u);
+    fz_grid_sync(&a.st->fz_bar, target, a.spin_limit, err);
+    // ---- phase 1c: every run's bit in its slot's bitmap ----
+    for (int s = 0; s < a.per; ++s) {
+      const uint4 r = fz_runs[s * kFzThreads + threadIdx.x];
+      const bool emit = r.x != kFullMask;
+      const uint32_t em = __ballot_sync(kFullMask, emit);
+      if (emit) {
+        const uint32_t slot = __ldcg(a.slotmap + (r.x >> kFzBlockBits));
+        const bool good = slot < nslots;
+        const uint32_t word = good ? slot * 16u + ((r.x >> 5) & 15u) : ~0u;
+        const uint32_t peers = __match_any_sync(em, word);
+        const uint32_t orv = __reduce_or_sync(peers, 1u << (r.x & 31u));
+        if (!good) set_error(err, kErrInvalidArg);
+        else if (int(lane) == __ffs(peers) - 1) atomicOr(a.sbits + word, orv);
+      }
+    }
+    fz_grid_sync(&a.st->fz_bar, target, a.spin_limit, err);
+    wbits = a.sbits;
+    wrank = a.srank;
+    nw = nslots * 16u;
+  }
+
+  // ---- phase 2: rows in key order (the rank of each occupied key's bit); sums cleared ----
+  fz_count(wbits, nw, a.stat + kFzMaxGrid, tmp);
+  fz_grid_sync(&a.st->fz_bar, target, a.spin_limit, err);
+  const uint32_t rows_all =
+      fz_rank<false>(wbits, wrank, nw, a.stat + kFzMaxGrid, tmp, &s_excl, FzNoBits());
+  const uint32_t rows = static_cast<uint32_t>(min(int64_t(rows_all), a.rows_cap));
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (rows_all > rows) set_error(err, kErrInvalidArg);
+    a.st->fz_rows = rows_all;
+    *a.out.num_voxels = rows_all;
+    if (a.out.frame_offsets) {
+      a.out.frame_offsets[0] = 0;
+      a.out.frame_offsets[1] = rows_all;
+    }
+  }
+  for (uint32_t i = blockIdx.x * kFzThreads + threadIdx.x; i < rows; i += gthreads) {
+    a.acc[i] = 0ull;
+    a.acc[i + a.rows_cap] = 0ull;
+    a.acc[i + 2 * a.rows_cap] = 0ull;
+  }
+  fz_grid_sync(&a.st->fz_bar, target, a.spin_limit, err);
+
+  // ---- phase 3: every run's points and sums at its row ----
+  {
+    // the rows of all the thread's runs first (their loads in flight together), then the
+    // atomics
+    uint32_t rw[kFzPer];
+#pragma unroll
+    for (int s = 0; s < kFzPer; ++s) {
+      rw[s] = ~0u;
+      if (s < a.per) {
+        const uint32_t k = fz_runs[s * kFzThreads + threadIdx.x].x;
+        if (k != kFullMask) {
+          uint32_t word;
+          if (dense) {
+            word = k >> 5;
+          } else {
+            const uint32_t slot = __ldcg(a.slotmap + (k >> kFzBlockBits));
+            word = slot < nslots ? slot * 16u + ((k >> 5) & 15u) : ~0u;
+          }
+          if (word < nw) {
+            rw[s] = __ldcg(wrank + word) + __popc(__ldcg(wbits + word) & ((1u << (k & 31u)) - 1u));
+            if (rw[s] >= rows) rw[s] = ~1u;
+          } else {
+            rw[s] = ~1u;
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int s = 0; s < kFzPer; ++s) {
+      if (rw[s] == ~0u) continue;
+      if (rw[s] == ~1u) {
+        set_error(err, kErrInvalidArg);
+        continue;
+      }
+      const uint4 r = fz_runs[s * kFzThreads + threadIdx.x];
+      a.rowkey[rw[s]] = r.x;  // (every run of the row stores the same key)
+      // (three arrays: a run's three atomics fall in three different lines)
+      unsigned long long* ap = a.acc + rw[s];
+      atomicAdd(ap, (unsigned long long)r.y | ((unsigned long long)(r.w >> 26) << kFzAccShift));
+      atomicAdd(ap + a.rows_cap, (unsigned long long)r.z);
+      atomicAdd(ap + 2 * a.rows_cap, (unsigned long long)(r.w & 0x3ffffffu));
+    }
+  }
+  fz_grid_sync(&a.st->fz_bar, target, a.spin_limit, err);
+
+  // ---- phase 4: rows (a thread a row) ----
+  if (block_error_raised(err)) return;
+  RowCtx rc;
+  rc.fs = a.fs;
+  rc.key_shift = 64;
+  rc.o1[0] = o[0];
+  rc.o1[1] = o[1];
+  rc.o1[2] = o[2];
+  rc.leaf1 = leaf;
+  for (uint32_t row = blockIdx.x * kFzThreads + threadIdx.x; row < rows; row += gthreads) {
+    const unsigned long long* ap = a.acc + row;
+    const unsigned long long ax = __ldcg(ap), ay = __ldcg(ap + a.rows_cap),
+                             az = __ldcg(ap + 2 * a.rows_cap);
+    const uint32_t cnt = static_cast<uint32_t>(ax >> kFzAccShift);
+    const unsigned long long sb[3] = {ax & kFzAccMask, ay, az};
+    float sf[3];
+    long long s64[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      s64[c] = static_cast<long long>(sb[c]) + static_cast<long long>(cnt) * kQMin;
+      sf[c] = __ll2float_rn(s64[c]);
+    }
+    put_row32(rc, a.out, row, __ldcg(a.rowkey + row), cnt, sf, s64, err);
+  }
+}
+
+constexpr size_t kFzSmem = size_t(kFzPer) * kFzThreads * sizeof(uint4);
+static_assert(kFzSmem + 2048 <= 227 * 1024, "one-launch block shared memory");
+
 constexpr size_t kFrSmem = sizeof(FrSmem);
 static_assert(kFrSmem + 1024 <= 227 * 1024, "bin block shared memory");
 
 }  // namespace
 
+namespace {
+// Blocks of the one-launch kernel resident on an SM (0: it cannot run), per device.
+int fused_blocks_per_sm(bool posed) {
+  static int cache[64][2];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+  int& b = cache[dev][posed ? 1 : 0];
+  if (b == 0) {
+    const void* fn = posed ? reinterpret_cast<const void*>(frame_fused_kernel<true>)
+                           : reinterpret_cast<const void*>(frame_fused_kernel<false>);
+    int v = 0;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(kFzSmem)) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, fn, kFzThreads, kFzSmem) != cudaSuccess)
+      v = 0;
+    (void)cudaGetLastError();
+    b = v > 0 ? v : -1;
+  }
+  return b > 0 ? b : 0;
+}
+
+int fused_grid(bool posed) {
+  const int64_t g = int64_t(fused_blocks_per_sm(posed)) * num_sms();
+  return static_cast<int>(g < kFzMaxGrid ? g : kFzMaxGrid);
+}
+}  // namespace
+
 void warm_frame_config() {
   persistent_grid(reinterpret_cast<const void*>(frame_bin_kernel), kFrThreads, kFrSmem, 1);
+  (void)fused_blocks_per_sm(false);
+  (void)fused_blocks_per_sm(true);
+}
+
+int64_t frame_fused_max_points(bool posed) {
+  return int64_t(fused_grid(posed)) * kFzThreads * kFzPer;
+}
+
+bool frame_fused_fits(int64_t n, bool posed) {
+  return n > 0 && n <= frame_fused_max_points(posed);
+}
+
+cudaError_t launch_frame_fused(const float* xyz, const FramesArg& fr, State* st, FrameState* fs,
+                               char* ws, const FusedLayout& ZL, const SegOut& out,
+                               uint32_t spin_limit, int* err, cudaStream_t stream) {
+  const bool ps = posed(fr);
+  const int g = fused_grid(ps);
+  if (g <= 0) return cudaErrorInvalidConfiguration;
+  const int64_t per = ceil_div(fr.n, int64_t(g) * kFzThreads);
+  if (per > kFzPer) return cudaErrorInvalidValue;
+  FzArgs a;
+  a.xyz = xyz;
+  a.fr = fr;
+  a.st = st;
+  a.fs = fs;
+  a.bits = reinterpret_cast<uint32_t*>(ws + ZL.bits);
+  a.rank = reinterpret_cast<uint32_t*>(ws + ZL.rank);
+  a.slotmap = reinterpret_cast<uint32_t*>(ws + ZL.slotmap);
+  a.slotbin = reinterpret_cast<uint32_t*>(ws + ZL.slotbin);
+  a.sbits = reinterpret_cast<uint32_t*>(ws + ZL.sbits);
+  a.srank = reinterpret_cast<uint32_t*>(ws + ZL.srank);
+  a.acc = reinterpret_cast<unsigned long long*>(ws + ZL.acc);
+  a.rowkey = reinterpret_cast<uint32_t*>(ws + ZL.rowkey);
+  a.stat = reinterpret_cast<uint32_t*>(ws + ZL.stat);
+  a.out = out;
+  a.rows_cap = fr.n;
+  a.per = static_cast<int>(per);
+  a.spin_limit = spin_limit;
+  a.err = err;
+  void* args[] = {&a};
+  const void* fn = ps ? reinterpret_cast<const void*>(frame_fused_kernel<true>)
+                      : reinterpret_cast<const void*>(frame_fused_kernel<false>);
+  return cudaLaunchCooperativeKernel(fn, dim3(g), dim3(kFzThreads), args, kFzSmem, stream);
 }
 
 cudaError_t launch_frame(const float* xyz, const FramesArg& fr, State* st, FrameState* fs,

@@ -66,6 +66,7 @@ _SIGS = {
     "vg_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "vg_version": ([], ctypes.c_int),
     "vg_downsample_workspace_bytes": ([ctypes.c_int64, ctypes.c_int], ctypes.c_size_t),
+    "vg_frame_one_launch_points": ([ctypes.c_int], ctypes.c_int64),
     "vg_downsample": ([ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_float,
                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -201,6 +202,11 @@ def method_flag(method) -> int:
 
 def workspace_bytes(n: int, flags: int = 0) -> int:
     return int(lib().vg_downsample_workspace_bytes(int(n), int(flags)))
+
+
+def frame_one_launch_points(posed: bool = False) -> int:
+    """Largest frame method="frame" groups in one cooperative launch on this device (0: none)."""
+    return int(lib().vg_frame_one_launch_points(1 if posed else 0))
 
 
 class Buffers(NamedTuple):

@@ -36,7 +36,7 @@ def clouds():
 
 
 @pytest.mark.parametrize("cloud", ["rgbd", "map"])
-@pytest.mark.parametrize("method", ["auto", "sort", "sort_lsd", "hash"])
+@pytest.mark.parametrize("method", ["auto", "sort", "sort_lsd", "hash", "frame"])
 @pytest.mark.parametrize("extra", [{}, {"point_to_voxel": True}, {"min_count": 2}])
 def test_range_error_stops_later_steps(clouds, cloud, method, extra):
     xyz = clouds[cloud]

@@ -130,3 +130,63 @@ def test_one_frame_plan_graph_replays():
     assert np.array_equal(gpu_keys(bb["out_keys"][:v]), gpu_keys(ref.keys))
     assert np.array_equal(gpu_counts(bb["out_counts"][:v]), gpu_counts(ref.counts))
     assert np.array_equal(to_np(bb["out_centroids"][:v]), to_np(ref.centroids))
+
+
+def test_one_launch_capacity():
+    cap = vg.frame_one_launch_points()
+    assert cap >= 1280 * 720  # one block of 1024 threads an SM, 8 points a thread
+    assert vg.frame_one_launch_points(posed=True) >= 640 * 480
+
+
+@pytest.mark.parametrize("w,h", [(1600, 900), (2048, 1024)])
+def test_frames_beyond_one_launch(w, h):
+    # above the one-launch capacity the bin grouping (five kernels) takes the frame
+    if w * h <= vg.frame_one_launch_points():
+        pytest.skip("this device's one-launch grid holds the frame")
+    check(synth.rgbd_frame(w, h, seed=11, cx=w / 2 - 0.5, cy=h / 2 - 0.5), 0.02)
+
+
+@pytest.mark.parametrize("leaf", [0.005, 0.01])
+def test_wide_keys_one_launch(leaf):
+    # 24-bit keys (the widest single bitmap over every key) and 27-bit keys (bitmaps of the
+    # occupied blocks of 2^9 keys, numbered first)
+    x = synth.rgbd_frame(640, 480, seed=21)
+    got = check(x, leaf)
+    assert got.keys.numel() > 0
+
+
+def test_repeated_calls_same_buffers():
+    # the grid-barrier counter and scan words are reset every call: calls in a row agree
+    x = cuda(synth.rgbd_frame(640, 480, seed=8))
+    b = vg.alloc_buffers(x.shape[0], "cuda", flags=vg.method_flag("frame"))
+    ref = vg.downsample(x, 0.05, method="sort_lsd")
+    for leaf in (0.05, 0.004, 0.05):
+        vg.downsample_into(x, leaf, b, origin_from_min=True, method="frame")
+        assert int(b.error.item()) == 0
+    v = int(b.num_voxels.item())
+    assert v == ref.keys.numel()
+    assert np.array_equal(gpu_keys(b.keys[:v]), gpu_keys(ref.keys))
+    assert np.array_equal(to_np(b.centroids[:v]), to_np(ref.centroids))
+
+
+def test_bad_offsets_one_frame():
+    xyz = cuda(synth.random_cloud(1000, seed=1))
+    with pytest.raises(vg.VGError) as e:
+        vg.downsample_frames((xyz, [0, 999]), [0.1], method="frame")
+    assert e.value.status == vg.Status.INVALID_ARG
+    # the next call with the same method is unaffected
+    x = synth.random_cloud(1000, seed=1)
+    check(x, 0.1)
+
+
+@pytest.mark.parametrize("cells,bits", [((511, 511, 255), 26), ((511, 511, 511), 27)])
+def test_bitmap_widths(cells, bits):
+    # 26-bit keys: the widest single key bitmap (its words past 2^19 cleared after the
+    # extents); 27 bits: bitmaps of the occupied blocks of 2^9 keys
+    r = np.random.Generator(np.random.PCG64(bits))
+    ext = np.float32(cells) * np.float32(0.02)
+    x = (r.random((60_000, 3)) * ext).astype(np.float32)
+    x[0] = ext - np.float32(1e-3)
+    x[1] = 0.0
+    got = check(x, 0.02, np.zeros(3, np.float32))
+    assert int(gpu_keys(got.keys).max()).bit_length() == bits
