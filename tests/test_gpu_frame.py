@@ -148,8 +148,8 @@ def test_frames_beyond_one_launch(w, h):
 
 @pytest.mark.parametrize("leaf", [0.005, 0.01])
 def test_wide_keys_one_launch(leaf):
-    # 24-bit keys (the widest single bitmap over every key) and 27-bit keys (bitmaps of the
-    # occupied blocks of 2^9 keys, numbered first)
+    # 24-bit keys (the bitmap the kernel clears before the extents) and 27-bit keys
+    # (bitmaps of the occupied blocks of 2^9 keys, numbered first)
     x = synth.rgbd_frame(640, 480, seed=21)
     got = check(x, leaf)
     assert got.keys.numel() > 0
@@ -179,10 +179,11 @@ def test_bad_offsets_one_frame():
     check(x, 0.1)
 
 
-@pytest.mark.parametrize("cells,bits", [((511, 511, 255), 26), ((511, 511, 511), 27)])
+@pytest.mark.parametrize("cells,bits", [((511, 511, 255), 26), ((511, 511, 511), 27),
+                                        ((1023, 1023, 511), 29)])
 def test_bitmap_widths(cells, bits):
     # 26-bit keys: the widest single key bitmap (its words past 2^19 cleared after the
-    # extents); 27 bits: bitmaps of the occupied blocks of 2^9 keys
+    # extents); 27 and 29 bits: bitmaps of the occupied blocks of 2^9 keys
     r = np.random.Generator(np.random.PCG64(bits))
     ext = np.float32(cells) * np.float32(0.02)
     x = (r.random((60_000, 3)) * ext).astype(np.float32)
