@@ -215,8 +215,9 @@ def extra_measurements(args, dev, peak):
     out = {}
     stream = torch.cuda.current_stream(dev)
 
-    # 640x480 RGB-D frame, leaf 0.05 m: one plain call per grouping, and the one-frame plan
-    # (CUDA-graph replay) with the single-frame bin grouping
+    # 640x480 RGB-D frame, leaf 0.05 m: one plain call per grouping (host issue is well
+    # under the device time, so back-to-back calls measure the device), and the one-frame
+    # plan (CUDA-graph replay)
     frame = synth.rgbd_frame(640, 480, seed=0)
     x = torch.from_numpy(frame).to(dev)
     n = x.shape[0]
@@ -246,7 +247,8 @@ def extra_measurements(args, dev, peak):
         r["plan_graph_" + m] = {"ms": ms, "points_per_s": n / (ms / 1e3),
                                 "roofline_frac": (12.0 * n + 16.0 * v) / (ms / 1e3) / 1e9 / peak}
     r["voxels"] = v
-    r["auto_choice"] = "sort_lsd (radix sort: fewer than 2^22 points)"
+    r["auto_choice"] = ("sort_lsd (radix sort: fewer than 2^22 points; the one-launch frame "
+                        "grouping needs 32-bit keys, known only on the device)")
     out["rgbd_640x480_leaf0.05"] = r
 
     # 64 frames of uneven size: 64 plain calls vs one batched call (plan, tuned, graph)
