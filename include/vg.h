@@ -103,7 +103,8 @@ typedef enum {
                                 keys (the Morton code of the frame's per-axis maximum
                                 index below 2^32 - 1), else the call records
                                 VG_ERR_RANGE.  Several frames, point_to_voxel or
-                                attributes take the plain SORT path.  Same rows as SORT */
+                                attributes take the global radix sort (as with
+                                VG_SORT_LSD).  Same rows as SORT                          */
 #define VG_GRID_SHIFT 8      /* vg_downsample_frames: blocks per SM of the streaming    */
 #define VG_GRID_MASK (0xff << VG_GRID_SHIFT) /* kernels (0 = default 8)                */
 

@@ -156,8 +156,9 @@ vg_status run_frames(const float* xyz, const FramesArg& fr, bool from_min, const
     // is grouped by buckets unless the caller asks for every digit in global passes.
     FramesArg frn = fr;
     frn.allow_narrow = out.p2v == nullptr && out.attrs_in == nullptr;
-    // AUTO takes the bucket grouping only for large clouds (see kAutoBucketMinPoints)
-    frn.lsd_narrow = (flags & VG_SORT_LSD) != 0 ||
+    // AUTO takes the bucket grouping only for large clouds (see kAutoBucketMinPoints); the
+    // frame method, when the call is not one frame for its own grouping, the radix sort
+    frn.lsd_narrow = (flags & (VG_SORT_LSD | VG_SORT_FRAME)) != 0 ||
                      ((flags & VG_METHOD_MASK) == VG_METHOD_AUTO && n < kAutoBucketMinPoints);
     const bool maybe_msd = frn.allow_narrow && !frn.lsd_narrow;
     // VG_SORT_FRAME: one frame, no point_to_voxel or attributes (else the plain sort path)

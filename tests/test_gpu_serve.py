@@ -10,7 +10,9 @@ from paper_2102_11084_gb300 import serve, synth, vg
 pytestmark = pytest.mark.gpu
 
 
-def test_results_same_alone_and_in_the_mix():
+@pytest.mark.parametrize("method", ["auto", "frame"])
+def test_results_same_alone_and_in_the_mix(method):
+    # "frame": batches of one frame take the one-launch grouping, larger ones the radix sort
     pool = [synth.rgbd_frame(320, 240, seed=900 + k) for k in range(6)]
     leaf = 0.05
     solo = []
@@ -18,7 +20,7 @@ def test_results_same_alone_and_in_the_mix():
         r = vg.downsample(torch.from_numpy(x).cuda(), leaf)
         solo.append((r.keys.cpu().numpy().view(np.uint64), r.centroids.cpu().numpy(),
                      r.counts.cpu().numpy().view(np.uint32)))
-    srv = serve.Server(max_points=4 * 320 * 240, max_frames=8, n_slots=2)
+    srv = serve.Server(max_points=4 * 320 * 240, max_frames=8, n_slots=2, method=method)
     rng = np.random.Generator(np.random.PCG64(3))
     futs = []
     for i in range(90):
