@@ -126,9 +126,10 @@ VG_API int vg_version(void);
 VG_API size_t vg_downsample_workspace_bytes(int64_t n_points, int flags);
 
 /* Largest frame, in points, that VG_SORT_FRAME groups in one cooperative launch on the
- * current device (its grid -- one block of 1024 threads per SM -- holding 8 points a
- * thread); 0 when the device cannot run that launch.  posed != 0 asks for calls with a pose
- * or height limits.  Larger frames take the bin grouping.  Reads device attributes only. */
+ * current device: its grid (one block of 1024 threads per SM) holding 14 points a thread,
+ * and at most 2^21 points (2,097,152: a 1920x1080 frame fits); 0 when the device cannot
+ * run that launch.  posed != 0 asks for calls with a pose or height limits.  Larger frames
+ * take the bin grouping.  Reads device attributes only. */
 VG_API int64_t vg_frame_one_launch_points(int posed);
 
 /*

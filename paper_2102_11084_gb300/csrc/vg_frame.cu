@@ -560,7 +560,8 @@ struct FzArgs {
   int* err;
 };
 
-constexpr int kFzAccShift = 42;  // points above the x sum (a sum of n < 2^21 offsets < 2^42)
+constexpr int kFzAccShift = 42;  // points above the x sum (n <= 2^21 offsets of < 2^21 each)
+static_assert(kFzMaxPointsBits + 21 <= kFzAccShift, "x sum below the points field");
 constexpr unsigned long long kFzAccMask = (1ull << kFzAccShift) - 1ull;
 
 // Grid barrier on an arrival counter the call zeroes; `target` (thread 0's) grows by the
@@ -1032,7 +1033,9 @@ void warm_frame_config() {
 }
 
 int64_t frame_fused_max_points(bool posed) {
-  return int64_t(fused_grid(posed)) * kFzThreads * kFzPer;
+  // (and at most 2^21 points, so a cell's x sum stays below the points field at bit 42)
+  const int64_t g = int64_t(fused_grid(posed)) * kFzThreads * kFzPer;
+  return g < (int64_t(1) << kFzMaxPointsBits) ? g : (int64_t(1) << kFzMaxPointsBits);
 }
 
 bool frame_fused_fits(int64_t n, bool posed) {

@@ -301,7 +301,8 @@ constexpr FrameLayout frame_layout(int64_t n, size_t base) {
 // blocks of 2^kFzBlockBits keys) ranks the cells in key order, and the cells' counts and
 // sums are added at their rows.  Scratch after the sort layout's frame state.
 constexpr int kFzThreads = 1024;   // threads of a block (one block per SM)
-constexpr int kFzPer = 8;          // points a thread holds at most
+constexpr int kFzPer = 14;         // points a thread holds at most
+constexpr int kFzMaxPointsBits = 21;  // a frame of at most 2^21 points
 constexpr int kFzDenseBits = 26;   // keys of up to 26 bits: one bitmap over every key
 constexpr int kFzZeroBits = 24;    // bitmap bits the kernel clears before the extents
 constexpr int kFzBlockBits = 9;    // wider keys: bitmaps of the occupied blocks of 2^9 keys

@@ -134,11 +134,15 @@ def test_one_frame_plan_graph_replays():
 
 def test_one_launch_capacity():
     cap = vg.frame_one_launch_points()
-    assert cap >= 1280 * 720  # one block of 1024 threads an SM, 8 points a thread
+    assert 1920 * 1080 <= cap <= 2 ** 21  # one block of 1024 threads an SM, 14 points a thread
     assert vg.frame_one_launch_points(posed=True) >= 640 * 480
 
 
-@pytest.mark.parametrize("w,h", [(1600, 900), (2048, 1024)])
+def test_full_hd_one_launch():
+    check(synth.rgbd_frame(1920, 1080, seed=12, cx=959.5, cy=539.5), 0.02)
+
+
+@pytest.mark.parametrize("w,h", [(2304, 1296), (2560, 1440)])
 def test_frames_beyond_one_launch(w, h):
     # above the one-launch capacity the bin grouping (five kernels) takes the frame
     if w * h <= vg.frame_one_launch_points():
