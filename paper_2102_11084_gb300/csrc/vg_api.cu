@@ -11,6 +11,7 @@
 #include "../../include/vg.h"
 #include "vg_api_internal.h"
 #include "vg_internal.h"
+#include "vg_frame.h"
 
 namespace vg {
 

@@ -26,6 +26,7 @@
 
 #include "vg_device.cuh"
 #include "vg_internal.h"
+#include "vg_frame.h"
 #include "vg_rows.cuh"
 #include "vg_stream.cuh"
 
