@@ -455,6 +455,13 @@ VG_API int vg_set_stage_events(void** events, int max_events);
 VG_API vg_status vg_debug_wait_timeout(uint32_t* scratch_words, uint32_t limit,
                                        int32_t* out_error, vg_stream_t stream);
 
+/* Test of the grid barrier of the one-launch frame grouping: a two-block cooperative
+ * launch whose barrier waits for one block more than it has, on one device word
+ * (scratch_words, caller-owned, zeroed by the call) with a limit of `limit` polls
+ * (1 .. 2^22); every block's wait gives up and *out_error becomes VG_ERR_TIMEOUT. */
+VG_API vg_status vg_debug_grid_barrier_timeout(uint32_t* scratch_words, uint32_t limit,
+                                               int32_t* out_error, vg_stream_t stream);
+
 /* Test hook: limit of every chained-scan wait in later calls (0 restores the default
  * of about a second).  A wait that reaches it records VG_ERR_TIMEOUT and returns. */
 VG_API void vg_debug_set_spin_limit(uint32_t limit);

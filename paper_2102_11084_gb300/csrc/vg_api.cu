@@ -360,6 +360,19 @@ vg_status vg_debug_wait_timeout(uint32_t* scratch_words, uint32_t limit, int32_t
   return cuda_status(e);
 }
 
+vg_status vg_debug_grid_barrier_timeout(uint32_t* scratch_words, uint32_t limit,
+                                        int32_t* out_error, vg_stream_t stream_) {
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+  if (!scratch_words || !out_error || limit == 0 || limit > kDefaultSpinLimit)
+    return VG_ERR_INVALID_ARG;
+  if (!aligned(scratch_words, 4) || !aligned(out_error, 4)) return VG_ERR_ALIGN;
+  cudaError_t e = cudaMemsetAsync(scratch_words, 0, sizeof(uint32_t), stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(out_error, 0, sizeof(int32_t), stream);
+  if (e == cudaSuccess)
+    e = launch_debug_grid_barrier(scratch_words, limit, reinterpret_cast<int*>(out_error), stream);
+  return cuda_status(e);
+}
+
 size_t vg_downsample_workspace_bytes(int64_t n_points, int flags) {
   return frames_workspace_bytes(n_points, 1, flags);
 }

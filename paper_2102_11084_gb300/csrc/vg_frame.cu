@@ -992,6 +992,13 @@ __global__ __launch_bounds__(kFzThreads, 1) void frame_fused_kernel(const FzArgs
   }
 }
 
+// Test of the grid barrier's bounded wait: the target counts one arrival more than the grid
+// makes, so every block's wait runs out after `limit` polls and records kErrTimeout.
+__global__ void debug_grid_barrier_kernel(uint32_t* ctr, uint32_t limit, int* err) {
+  uint32_t target = 1;
+  fz_grid_sync(ctr, target, limit, err);
+}
+
 constexpr size_t kFzSmem = size_t(kFzPer) * kFzThreads * sizeof(uint4);
 static_assert(kFzSmem + 2048 <= 227 * 1024, "one-launch block shared memory");
 
@@ -1041,6 +1048,13 @@ int64_t frame_fused_max_points(bool posed) {
 
 bool frame_fused_fits(int64_t n, bool posed) {
   return n > 0 && n <= frame_fused_max_points(posed);
+}
+
+cudaError_t launch_debug_grid_barrier(uint32_t* ctr, uint32_t limit, int* err,
+                                      cudaStream_t stream) {
+  void* args[] = {&ctr, &limit, &err};
+  return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(debug_grid_barrier_kernel),
+                                     dim3(2), dim3(32), args, 0, stream);
 }
 
 cudaError_t launch_frame_fused(const float* xyz, const FramesArg& fr, State* st, FrameState* fs,

@@ -100,4 +100,8 @@ int64_t frame_fused_max_points(bool posed);
 cudaError_t launch_frame_fused(const float* xyz, const FramesArg& fr, State* st, FrameState* fs,
                                char* ws, const FusedLayout& ZL, const SegOut& out,
                                uint32_t spin_limit, int* err, cudaStream_t stream);
+// Test of the grid barrier's bounded wait (a two-block cooperative launch whose barrier
+// waits for one block more than it has).
+cudaError_t launch_debug_grid_barrier(uint32_t* ctr, uint32_t limit, int* err,
+                                      cudaStream_t stream);
 }  // namespace vg

@@ -78,6 +78,8 @@ _SIGS = {
                                ctypes.c_void_p], ctypes.c_int),
     "vg_downsample_noalloc_scratch_bytes": ([], ctypes.c_size_t),
     "vg_set_stage_events": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
+    "vg_debug_grid_barrier_timeout": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p,
+                                       ctypes.c_void_p], ctypes.c_int),
     "vg_debug_wait_timeout": ([ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p],
                               ctypes.c_int),
     "vg_batch_workspace_bytes": ([ctypes.c_int64, ctypes.c_int, ctypes.c_int], ctypes.c_size_t),

@@ -195,3 +195,16 @@ def test_bitmap_widths(cells, bits):
     x[1] = 0.0
     got = check(x, 0.02, np.zeros(3, np.float32))
     assert int(gpu_keys(got.keys).max()).bit_length() == bits
+
+
+def test_grid_barrier_wait_times_out():
+    # the one-launch kernel's grid barrier: a wait nobody completes gives up and reports
+    scratch = torch.zeros(4, dtype=torch.int32, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    st = vg.lib().vg_debug_grid_barrier_timeout(vg._ptr(scratch), 1000, vg._ptr(err), None)
+    assert st == 0
+    torch.cuda.synchronize()
+    assert int(err.item()) == vg.Status.TIMEOUT
+    assert int(scratch[0].item()) == 2  # both blocks arrived
+    # the context is usable afterwards
+    check(synth.random_cloud(5000, seed=77), 0.05)
