@@ -551,7 +551,7 @@ struct FzArgs {
   uint32_t* slotbin;   // rows_cap words
   uint32_t* sbits;     // 16 rows_cap words
   uint32_t* srank;     // 16 rows_cap words
-  unsigned long long* acc;  // 3 arrays of rows_cap: x sum + (points << 42), y sum, z sum
+  unsigned long long* acc;  // 3 arrays of rows_cap: A, B and C of every row (see below)
   uint32_t* rowkey;    // rows_cap words
   uint32_t* stat;      // 2 kFzMaxGrid words
   SegOut out;
@@ -561,9 +561,11 @@ struct FzArgs {
   int* err;
 };
 
-constexpr int kFzAccShift = 42;  // points above the x sum (n <= 2^21 offsets of < 2^21 each)
-static_assert(kFzMaxPointsBits + 21 <= kFzAccShift, "x sum below the points field");
-constexpr unsigned long long kFzAccMask = (1ull << kFzAccShift) - 1ull;
+// A cell's three sums and points in two words and a carry word: A = x + y 2^32 and
+// B = z + points 2^32 (mod 2^64), C = the carries out of A's and B's low halves and out of
+// A, 21 bits each.  A frame of at most 2^21 points keeps every sum below 2^42, so each
+// carry count below 2^10.
+static_assert(kFzMaxPointsBits + 21 <= 42 && 42 - 32 < 21, "carry counts fit their fields");
 
 // Grid barrier on an arrival counter the call zeroes; `target` (thread 0's) grows by the
 // grid each barrier.  The wait is bounded.
@@ -948,20 +950,40 @@ __global__ __launch_bounds__(kFzThreads, 1) void frame_fused_kernel(const FzArgs
         }
       }
     }
+    // two atomics a run: A += x | y << 32, B += z | points << 32; the old values they return
+    // tell every carry out of a 32-bit half (x into y, A out of 64 bits, z into points),
+    // counted in a third word (rare: a cell of more than 2^11 points)
+    unsigned long long* accA = a.acc;
+    unsigned long long* accB = a.acc + a.rows_cap;
+    unsigned long long* accC = a.acc + 2 * a.rows_cap;
 #pragma unroll
-    for (int s = 0; s < kFzPer; ++s) {
-      if (rw[s] == ~0u) continue;
-      if (rw[s] == ~1u) {
-        set_error(err, kErrInvalidArg);
-        continue;
+    for (int s0 = 0; s0 < kFzPer; s0 += 2) {
+      unsigned long long oa[2], ob[2], va[2], vb[2];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int s = s0 + q;
+        oa[q] = ob[q] = va[q] = vb[q] = 0ull;
+        if (s >= kFzPer || rw[s] >= ~1u) continue;
+        const uint4 r = fz_runs[s * kFzThreads + threadIdx.x];
+        a.rowkey[rw[s]] = r.x;  // (every run of the row stores the same key)
+        va[q] = (unsigned long long)r.y | ((unsigned long long)r.z << 32);
+        vb[q] = (unsigned long long)(r.w & 0x3ffffffu) | ((unsigned long long)(r.w >> 26) << 32);
+        oa[q] = atomicAdd(accA + rw[s], va[q]);
+        ob[q] = atomicAdd(accB + rw[s], vb[q]);
       }
-      const uint4 r = fz_runs[s * kFzThreads + threadIdx.x];
-      a.rowkey[rw[s]] = r.x;  // (every run of the row stores the same key)
-      // (three arrays: a run's three atomics fall in three different lines)
-      unsigned long long* ap = a.acc + rw[s];
-      atomicAdd(ap, (unsigned long long)r.y | ((unsigned long long)(r.w >> 26) << kFzAccShift));
-      atomicAdd(ap + a.rows_cap, (unsigned long long)r.z);
-      atomicAdd(ap + 2 * a.rows_cap, (unsigned long long)(r.w & 0x3ffffffu));
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int s = s0 + q;
+        if (s >= kFzPer || rw[s] == ~0u) continue;
+        if (rw[s] == ~1u) {
+          set_error(err, kErrInvalidArg);
+          continue;
+        }
+        const unsigned long long cx = ((oa[q] & 0xffffffffull) + (va[q] & 0xffffffffull)) >> 32;
+        const unsigned long long cy = oa[q] + va[q] < oa[q] ? 1ull : 0ull;
+        const unsigned long long cz = ((ob[q] & 0xffffffffull) + (vb[q] & 0xffffffffull)) >> 32;
+        if (cx | cy | cz) atomicAdd(accC + rw[s], cx | (cy << 21) | (cz << 42));
+      }
     }
   }
   fz_grid_sync(&a.st->fz_bar, target, a.spin_limit, err);
@@ -977,10 +999,15 @@ __global__ __launch_bounds__(kFzThreads, 1) void frame_fused_kernel(const FzArgs
   rc.leaf1 = leaf;
   for (uint32_t row = blockIdx.x * kFzThreads + threadIdx.x; row < rows; row += gthreads) {
     const unsigned long long* ap = a.acc + row;
-    const unsigned long long ax = __ldcg(ap), ay = __ldcg(ap + a.rows_cap),
-                             az = __ldcg(ap + 2 * a.rows_cap);
-    const uint32_t cnt = static_cast<uint32_t>(ax >> kFzAccShift);
-    const unsigned long long sb[3] = {ax & kFzAccMask, ay, az};
+    const unsigned long long A = __ldcg(ap), B = __ldcg(ap + a.rows_cap),
+                             C = __ldcg(ap + 2 * a.rows_cap);
+    const unsigned long long cx = C & 0x1fffffull, cy = (C >> 21) & 0x1fffffull, cz = C >> 42;
+    // x = low(A) + cx 2^32; y = high(A) + cy 2^32 - cx; z = low(B) + cz 2^32;
+    // points = high(B) - cz
+    const unsigned long long sb[3] = {(A & 0xffffffffull) + (cx << 32),
+                                      (A >> 32) + (cy << 32) - cx,
+                                      (B & 0xffffffffull) + (cz << 32)};
+    const uint32_t cnt = static_cast<uint32_t>((B >> 32) - cz);
     float sf[3];
     long long s64[3];
 #pragma unroll
@@ -1041,7 +1068,7 @@ void warm_frame_config() {
 }
 
 int64_t frame_fused_max_points(bool posed) {
-  // (and at most 2^21 points, so a cell's x sum stays below the points field at bit 42)
+  // (and at most 2^21 points, so a cell's carry counts fit their fields)
   const int64_t g = int64_t(fused_grid(posed)) * kFzThreads * kFzPer;
   return g < (int64_t(1) << kFzMaxPointsBits) ? g : (int64_t(1) << kFzMaxPointsBits);
 }
