@@ -675,23 +675,30 @@ def run_vg(args, rank, world, local):
     e2e_seq_s = e2e_s
 
     # the same steps through the overlapped pipeline (serve.CloudPipeline): step k+1's
-    # copy in and decimation run while step k's rows are copied back
+    # copy in and decimation run while step k's rows are copied back.  The headline copies
+    # back the decimated cloud and its counts (the scope's output bytes, 16 B a voxel);
+    # the run with the keys too (24 B a voxel) is reported beside it.
     del keys_h, cent_h, cnt_h
     from paper_2102_11084_gb300 import serve
-    pipe = serve.CloudPipeline(n, args.leaf, depth=3, method=args.method, device=dev,
-                               record_timeline=True)
-    for _ in pipe.run([xyz_host] * 3):  # untimed: first touch of the slots' buffers
-        pass
-    torch.cuda.synchronize()
-    n_warm_tl = len(pipe.timeline())
-    t0 = time.perf_counter()
-    d2h_pipe = 0
-    for k_, c_, n_ in pipe.run([xyz_host] * e2e_steps):
-        d2h_pipe = 8 + k_.shape[0] * (8 + 12 + 4)
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    pipe_overlap = serve.copy_overlap(pipe.timeline()[n_warm_tl:])
-    del pipe
-    e2e_s = max_over_ranks(e2e_s, dev)
+
+    def pipeline_run(with_keys):
+        pipe = serve.CloudPipeline(n, args.leaf, depth=3, method=args.method, device=dev,
+                                   record_timeline=True, with_keys=with_keys)
+        for _ in pipe.run([xyz_host] * 3):  # untimed: first touch of the slots' buffers
+            pass
+        torch.cuda.synchronize()
+        n_warm_tl = len(pipe.timeline())
+        t0 = time.perf_counter()
+        d2h_bytes = 0
+        for k_, c_, n_ in pipe.run([xyz_host] * e2e_steps):
+            d2h_bytes = 8 + c_.shape[0] * ((8 if with_keys else 0) + 12 + 4)
+        sec = (time.perf_counter() - t0) / e2e_steps
+        overlap = serve.copy_overlap(pipe.timeline()[n_warm_tl:])
+        del pipe
+        return max_over_ranks(sec, dev), d2h_bytes, overlap
+
+    e2e_s, d2h_pipe, pipe_overlap = pipeline_run(False)
+    e2e_k_s, d2h_pipe_k, pipe_overlap_k = pipeline_run(True)
     e2e_seq_s = max_over_ranks(e2e_seq_s, dev)
 
     if rank != 0:
@@ -749,9 +756,13 @@ def run_vg(args, rank, world, local):
         "cpu_baseline": cpu,
         "e2e": {"value": total_points / e2e_s, "unit": "points/s", "h2d_bytes_per_step": 12 * n,
                 "d2h_bytes_per_step": d2h_pipe, "ms_per_step": e2e_s * 1e3,
-                "api": "serve.CloudPipeline (depth 3: copies of neighbouring steps overlapped)",
+                "api": ("serve.CloudPipeline (depth 3: copies of neighbouring steps "
+                        "overlapped); rows out = centroids + counts, keys stay on the device"),
                 "steps": e2e_steps, "warmup": 3,
                 "copy_overlap": pipe_overlap,
+                "with_keys": {"value": total_points / e2e_k_s, "ms_per_step": e2e_k_s * 1e3,
+                              "d2h_bytes_per_step": d2h_pipe_k,
+                              "copy_overlap": pipe_overlap_k},
                 "sequential": {"value": total_points / e2e_seq_s, "ms_per_step": e2e_seq_s * 1e3,
                                "api": "vg.downsample_into + torch copies, one step at a time",
                                "h2d_ms": h2d_ms, "d2h_ms": d2h_ms,

@@ -390,7 +390,8 @@ class CloudPipeline:
     ``run(clouds)`` yields, in order, (keys uint64 [V], centroids float32 [V, 3],
     counts uint32 [V]) numpy views of pinned host memory; a view stays valid until the
     pipeline takes ``depth`` more clouds.  Every cloud's result is the plain call's,
-    bit for bit.
+    bit for bit.  With ``with_keys=False`` the keys stay on the device (keys is None):
+    the decimated cloud and its point counts, 16 bytes a voxel instead of 24, come back.
 
     The copies of different clouds overlap, their decimations do not: a cloud's
     decimation starts only after the previous cloud's has finished.  Two decimations at
@@ -400,8 +401,9 @@ class CloudPipeline:
     """
 
     def __init__(self, max_points: int, leaf: float, *, depth: int = 3, method: str = "auto",
-                 device="cuda", record_timeline: bool = False):
+                 device="cuda", record_timeline: bool = False, with_keys: bool = True):
         self.leaf = float(leaf)
+        self.with_keys = bool(with_keys)
         self._timeline: Optional[list] = [] if record_timeline else None
         self._t0 = None
         if record_timeline:  # the common origin of every cloud's event times
@@ -420,7 +422,8 @@ class CloudPipeline:
                  "decimated": torch.cuda.Event(),
                  "xyz": torch.empty((self.max_points, 3), dtype=torch.float32, device=dev),
                  "buf": vg.alloc_buffers(self.max_points, dev, flags=flags),
-                 "keys": torch.empty(self.max_points, dtype=torch.int64).pin_memory(),
+                 "keys": (torch.empty(self.max_points, dtype=torch.int64).pin_memory()
+                          if self.with_keys else None),
                  "cents": torch.empty((self.max_points, 3), dtype=torch.float32).pin_memory(),
                  "counts": torch.empty(self.max_points, dtype=torch.int32).pin_memory(),
                  "nv": torch.zeros(1, dtype=torch.int64).pin_memory(),
@@ -472,7 +475,8 @@ class CloudPipeline:
         with torch.cuda.stream(s["stream"]):
             if ev:
                 ev["d2h0"].record(s["stream"])
-            s["keys"][:v].copy_(b.keys[:v], non_blocking=True)
+            if self.with_keys:
+                s["keys"][:v].copy_(b.keys[:v], non_blocking=True)
             s["cents"][:v].copy_(b.centroids[:v], non_blocking=True)
             s["counts"][:v].copy_(b.counts[:v], non_blocking=True)
             if ev:
@@ -486,8 +490,8 @@ class CloudPipeline:
             s["tl"]["done"] = True
         v = s["v"]
         s["state"] = "free"
-        return (s["keys"].numpy()[:v].view(np.uint64), s["cents"].numpy()[:v],
-                s["counts"].numpy()[:v].view(np.uint32))
+        keys = s["keys"].numpy()[:v].view(np.uint64) if self.with_keys else None
+        return keys, s["cents"].numpy()[:v], s["counts"].numpy()[:v].view(np.uint32)
 
     def timeline(self) -> list:
         """Per cloud handed out (record_timeline=True): ms from the pipeline's start on the

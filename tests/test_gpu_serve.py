@@ -138,3 +138,8 @@ def test_pipeline_copies_overlap_decimation_and_results_unchanged():
     # copies ran under other clouds' decimations for most of the decimation time (the
     # share of copy time that can be hidden depends on the link, ≈ 70-210 GB/s by box)
     assert ov["fraction"] > 0.0 and ov["overlapped_ms"] > 0.5 * ov["decimate_ms"], ov
+    # keys left on the device: the same centroids and counts come back
+    pipe = serve.CloudPipeline(n, leaf, depth=3, with_keys=False)
+    for k, (keys, cents, counts) in zip(order, pipe.run(clouds[k] for k in order)):
+        assert keys is None and np.array_equal(counts, solo[k][2])
+        assert np.array_equal(cents.view(np.int32), solo[k][1].view(np.int32))
