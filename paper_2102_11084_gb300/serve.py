@@ -502,26 +502,26 @@ class CloudPipeline:
 
     def run(self, clouds):
         """clouds: iterable of float32 [N, 3] CPU tensors (pinned for overlap)."""
+        # Every free slot takes the next cloud at once (its copy in queued behind the
+        # others'), and a cloud's rows start back as soon as its voxel count is in; the
+        # host waits only when the next cloud needs a slot whose cloud is not handed out.
         order = collections.deque()
         k = 0
         for host in clouds:
             s = self.slots[k % len(self.slots)]
-            if s["state"] != "free":  # the slot's previous cloud must be handed out first
-                while order:
-                    o = order.popleft()
-                    if o["state"] == "counting":
-                        self._copy_back(o)
-                    yield self._result(o)
-                    if o is s:
-                        break
-            self._launch(s, host)
-            # the oldest cloud still counting can now start its copy back
-            for o in order:
+            while s["state"] != "free":  # the slot's previous cloud is handed out first
+                o = order.popleft()
                 if o["state"] == "counting":
                     self._copy_back(o)
-                    break
+                yield self._result(o)
+            self._launch(s, host)
             order.append(s)
             k += 1
+            for o in order:  # copies back of the clouds counted so far, oldest first
+                if o["state"] == "counting":
+                    if not o["counted"].query():
+                        break
+                    self._copy_back(o)
         while order:
             o = order.popleft()
             if o["state"] == "counting":
