@@ -1,11 +1,15 @@
-// Steps a2-a5 for one camera frame (VG_SORT_FRAME): grouping by bins of 2^12 keys.
+// Steps a1-a5 for one camera frame (VG_SORT_FRAME).
 //
 // arXiv 2102.11084 Sec. II-C filters one camera cloud per call (Table I times that call),
-// and a frame's points all fall in a few thousand cells per axis at most, so its 32-bit
-// Morton keys split into bins of 2^12 consecutive keys (a 16-cell cube) with at most
-// 2^20 bins.  Order inside a bin is the only sorting left, and a bin's cells fit one
-// block's shared memory densely (one counter and three sums per key of the bin), so the
-// whole grouping is a counting pass, one scatter and one reduction:
+// and a frame's points all fall in a few thousand cells per axis at most, so its keys fit
+// 32 bits and its cells are few: launches, not bytes, cost the time.  A frame the grid
+// holds (vg_frame_one_launch_points) is grouped by frame_fused_kernel, ONE cooperative
+// launch (below): the rank of each occupied key's bit in an occupancy bitmap over the
+// keys is its row, and every run of points adds its sums at its row.  A larger frame's
+// Morton keys split into bins of 2^12 consecutive keys (a 16-cell cube) with at most 2^20
+// bins; order inside a bin is the only sorting left, and a bin's cells fit one block's
+// shared memory densely (one counter and three sums per key of the bin), so that grouping
+// is a counting pass, one scatter and one reduction:
 //   frame_key_kernel     the key and corner offsets of every point (the key kernel's
 //                        arithmetic); runs of equal keys among 32 consecutive pixels
 //                        summed into one entry, and its place in its bin (one global
@@ -20,8 +24,9 @@
 //                        then shared-memory atomics), an occupancy bitmap ranks its cells,
 //                        and one thread per occupied key writes its row (the centroid
 //                        formula of acc_centroid).
-// Same cells, counts and integer sums as every other grouping: the rows are bit-identical.
-// The extent kernel, which runs first, clears the bin counts and status words.
+// Same cells, counts and integer sums as every other grouping in both: the rows are
+// bit-identical.  Before the bin grouping, the extent kernel clears the bin counts and
+// status words.
 #include <cstddef>
 
 #include "vg_device.cuh"
@@ -527,16 +532,21 @@ __global__ __launch_bounds__(kFrThreads) void frame_bin_kernel(
 // by grid barriers, each point held by one thread (point (s G' + w) 32 + lane for step s,
 // w = the warp's index in the grid, G' = the grid's warps, so a warp holds 32 consecutive
 // points a step):
-//   0  extents (the origin kernel's minima and maxima); the bitmap and scan words cleared;
-//   1  key and corner offsets of every point, warp runs of equal keys kept in shared memory,
-//      one bit a run set in the key bitmap -- or, for keys of more than kFzDenseBits bits,
-//      in a bitmap of blocks of 2^kFzBlockBits keys, whose set bits a chained scan numbers
-//      (slots) before each run sets its key's bit in its slot's 16-word bitmap;
-//   2  a chained scan over the bitmap words gives every occupied key its row (keys in
-//      order: the rank of its bit), writes the row's key and clears its sums;
-//   3  every run adds its points and offset sums at its row (global atomics);
-//   4  every row's centroid (put_row32: the other groupings' formula and integer sums, so
-//      the rows are bit-identical to theirs).
+//   0  extents (the origin kernel's minima and maxima); the key bitmap's first
+//      kFzZeroWords words cleared (the rest, for wider keys, once the extents give the
+//      width);
+//   1  key and corner offsets of every point; runs of equal keys among a warp's 32 points
+//      kept in shared memory; one bit a run in the key bitmap (one atomic a bitmap word of
+//      the warp's step) -- or, for keys of more than kFzDenseBits bits, in a bitmap of
+//      blocks of 2^kFzBlockBits keys, whose set bits are ranked into slots before each run
+//      sets its key's bit in its slot's 16-word bitmap;
+//   2  the bitmap's set bits ranked in word order (counts per block, a barrier, every
+//      block's predecessors summed at once): an occupied key's row is its rank, so rows
+//      come out in key order; the rows' sums cleared;
+//   3  every run adds its points and offset sums at its row (two global atomics and a
+//      rare carry) and stores the row's key;
+//   4  one thread a row: the centroid (put_row32: the other groupings' formula and integer
+//      sums, so the rows are bit-identical to theirs).
 // Every wait is bounded (kErrTimeout after the limit), every index read back from scratch
 // is checked against its buffer, and every block passes every barrier, so an error never
 // leaves a block waiting on another.
@@ -640,14 +650,14 @@ __device__ __forceinline__ void warp_expand(uint32_t wi, uint32_t vi, uint32_t r
   }
 }
 
-// Step two (after a grid barrier): rk[i] = set bits before word i for the block's slice;
-// with kExpand, f(word, position, rank) for every set bit (warp_expand).  Returns the grand
-// total (in every block).  The grid has at most kFzThreads blocks.  Contains
-// __syncthreads.
 struct FzNoBits {
   __device__ void operator()(uint32_t, uint32_t, uint32_t) const {}
 };
 
+// Step two (after a grid barrier): rk[i] = set bits before word i for the block's slice;
+// with kExpand, f(word, position, rank) for every set bit (warp_expand).  Returns the grand
+// total (in every block).  The grid has at most kFzThreads blocks.  Contains
+// __syncthreads.
 template <bool kExpand, typename F>
 __device__ __forceinline__ uint32_t fz_rank(const uint32_t* w, uint32_t* rk, uint32_t nw,
                                             const uint32_t* agg, uint32_t* tmp,
