@@ -186,7 +186,9 @@ vg_status run_frames(const float* xyz, const FramesArg& fr, bool from_min, const
 
     // (the frame path needs only the state and frame state cleared: its last kernel
     // writes the voxel count and the frame offsets)
-    cudaError_t e = cudaMemsetAsync(ws, 0, frame_path ? L.lb_a : L.zero_bytes, stream);
+    // (the one-launch grouping clears the few state words it reads itself)
+    cudaError_t e = fused ? cudaSuccess
+                          : cudaMemsetAsync(ws, 0, frame_path ? L.lb_a : L.zero_bytes, stream);
     if (e == cudaSuccess && maybe_msd && !frame_path)  // points per bucket
       e = cudaMemsetAsync(ws + L.mhist, 0, L.mvcnt - L.mhist, stream);
     if (e == cudaSuccess && out_error && !fused)  // (the one-launch kernel clears it)

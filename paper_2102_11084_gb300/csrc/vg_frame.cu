@@ -1029,6 +1029,17 @@ __global__ __launch_bounds__(kFzThreads, 1) void frame_fused_kernel(const FzArgs
   }
 }
 
+// The only state the one-launch kernel reads before writing it: the barrier's arrival
+// counter and the frame's extent words (atomic maxima).  A one-thread-block kernel costs the
+// stream less than a memset of the state.
+__global__ void fz_clear_kernel(State* st, FrameState* fs) {
+  if (threadIdx.x == 0) st->fz_bar = 0u;
+  if (threadIdx.x < 3) {
+    fs[0].ord_min_inv[threadIdx.x] = 0u;
+    fs[0].ord_max[threadIdx.x] = 0u;
+  }
+}
+
 // Test of the grid barrier's bounded wait: the target counts one arrival more than the grid
 // makes, so every block's wait runs out after `limit` polls and records kErrTimeout.
 __global__ void debug_grid_barrier_kernel(uint32_t* ctr, uint32_t limit, int* err) {
@@ -1121,6 +1132,7 @@ cudaError_t launch_frame_fused(const float* xyz, const FramesArg& fr, State* st,
   a.per = static_cast<int>(per);
   a.spin_limit = spin_limit;
   a.err = err;
+  fz_clear_kernel<<<1, 32, 0, stream>>>(st, fs);
   void* args[] = {&a};
   const void* fn = ps ? reinterpret_cast<const void*>(frame_fused_kernel<true>)
                       : reinterpret_cast<const void*>(frame_fused_kernel<false>);
