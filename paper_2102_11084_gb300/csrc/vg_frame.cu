@@ -919,6 +919,9 @@ __global__ __launch_bounds__(kFzThreads, 1) void frame_fused_kernel(const FzArgs
   const uint32_t rows = static_cast<uint32_t>(min(int64_t(rows_all), a.rows_cap));
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     if (rows_all > rows) set_error(err, kErrInvalidArg);
+    // more cells than output rows: the first out.cap rows are written (phase 4 writes only
+    // those), so the shortfall is recorded once, here, for every block to see alike
+    if (int64_t(rows_all) > a.out.cap) set_error(err, kErrCapacity);
     a.st->fz_rows = rows_all;
     *a.out.num_voxels = rows_all;
     if (a.out.frame_offsets) {
@@ -998,8 +1001,12 @@ __global__ __launch_bounds__(kFzThreads, 1) void frame_fused_kernel(const FzArgs
   }
   fz_grid_sync(&a.st->fz_bar, target, a.spin_limit, err);
 
-  // ---- phase 4: rows (a thread a row) ----
-  if (block_error_raised(err)) return;
+  // ---- phase 4: rows (a thread a row), the first out.cap of them ----
+  // (every error but the capacity one stops it; none is set from here on)
+  if (__syncthreads_or(threadIdx.x == 0 && error_raised(err) &&
+                       *reinterpret_cast<const volatile int*>(err) != kErrCapacity))
+    return;
+  const uint32_t wrows = static_cast<uint32_t>(min(int64_t(rows), a.out.cap));
   RowCtx rc;
   rc.fs = a.fs;
   rc.key_shift = 64;
@@ -1007,7 +1014,7 @@ __global__ __launch_bounds__(kFzThreads, 1) void frame_fused_kernel(const FzArgs
   rc.o1[1] = o[1];
   rc.o1[2] = o[2];
   rc.leaf1 = leaf;
-  for (uint32_t row = blockIdx.x * kFzThreads + threadIdx.x; row < rows; row += gthreads) {
+  for (uint32_t row = blockIdx.x * kFzThreads + threadIdx.x; row < wrows; row += gthreads) {
     const unsigned long long* ap = a.acc + row;
     const unsigned long long A = __ldcg(ap), B = __ldcg(ap + a.rows_cap),
                              C = __ldcg(ap + 2 * a.rows_cap);

@@ -208,3 +208,17 @@ def test_grid_barrier_wait_times_out():
     assert int(scratch[0].item()) == 2  # both blocks arrived
     # the context is usable afterwards
     check(synth.random_cloud(5000, seed=77), 0.05)
+
+
+def test_capacity_short_of_the_voxels():
+    # 100 output rows for 11,489 voxels: the rows that fit are written, V is counted in
+    # full, and the call reports the shortfall
+    x = cuda(synth.rgbd_frame(640, 480, seed=0))
+    b = vg.alloc_buffers(x.shape[0], "cuda", flags=vg.method_flag("frame"))
+    vg.downsample_into(x, 0.05, b, origin_from_min=True, method="frame", cap=100)
+    torch.cuda.synchronize()
+    assert int(b.error.item()) == vg.Status.CAPACITY
+    ref = vg.downsample(x, 0.05, method="sort_lsd")
+    assert int(b.num_voxels.item()) == ref.keys.numel()
+    assert np.array_equal(gpu_keys(b.keys[:100]), gpu_keys(ref.keys[:100]))
+    assert np.array_equal(to_np(b.centroids[:100]), to_np(ref.centroids[:100]))
