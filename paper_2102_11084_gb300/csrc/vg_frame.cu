@@ -684,7 +684,7 @@ __device__ __forceinline__ uint32_t fz_rank(const uint32_t* w, uint32_t* rk, uin
 
 template <bool kPosed>
 __global__ __launch_bounds__(kFzThreads, 1) void frame_fused_kernel(const FzArgs a) {
-  extern __shared__ uint4 fz_runs[];  // [kFzPer][kFzThreads]: key, x, y, z | points << 26
+  extern __shared__ uint4 fz_runs[];  // [per][kFzThreads]: key, x, y, z | points << 26
   __shared__ float red[kFzThreads / 32][6];
   __shared__ uint32_t tmp[kFzThreads / 32];
   __shared__ uint32_t s_excl;
@@ -1143,7 +1143,9 @@ cudaError_t launch_frame_fused(const float* xyz, const FramesArg& fr, State* st,
   void* args[] = {&a};
   const void* fn = ps ? reinterpret_cast<const void*>(frame_fused_kernel<true>)
                       : reinterpret_cast<const void*>(frame_fused_kernel<false>);
-  return cudaLaunchCooperativeKernel(fn, dim3(g), dim3(kFzThreads), args, kFzSmem, stream);
+  // shared memory for the runs of the points a thread holds (the rest stays L1 cache)
+  const size_t smem = size_t(per) * kFzThreads * sizeof(uint4);
+  return cudaLaunchCooperativeKernel(fn, dim3(g), dim3(kFzThreads), args, smem, stream);
 }
 
 cudaError_t launch_frame(const float* xyz, const FramesArg& fr, State* st, FrameState* fs,
