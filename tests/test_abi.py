@@ -86,7 +86,7 @@ def test_grouping_flags():
     assert _call(flags=vg.METHOD_SORT | vg.SORT_LSD) == vg.Status.WORKSPACE
     assert _call(flags=vg.METHOD_SORT | 8) == vg.Status.INVALID_ARG
     assert _call(flags=vg.METHOD_SORT | vg.METHOD_HASH) == vg.Status.INVALID_ARG
-    # the single-frame bin grouping: a flag of the sort method only, with its own workspace
+    # the single-frame grouping: a flag of the sort method only, with its own workspace
     assert vg.method_flag("frame") == vg.METHOD_SORT | vg.SORT_FRAME
     assert _call(flags=vg.METHOD_SORT | vg.SORT_FRAME) == vg.Status.WORKSPACE
     assert _call(flags=vg.SORT_FRAME) == vg.Status.INVALID_ARG
@@ -104,3 +104,23 @@ def test_no_cpu_fallback():
     import torch
     with pytest.raises(TypeError):
         vgpkg.downsample(torch.zeros((4, 3)), 0.1)
+
+
+def test_frame_workspace_holds_the_one_launch_scratch():
+    # the frame method's workspace holds the one-launch grouping's scratch (after the
+    # call's state words: key bitmap and ranks of up to 2^26 keys and the 2^23-entry block
+    # map, 48 MiB, then per point two 16-word slot bitmaps, three row sums, a slot and a
+    # row key, 160 B) and the bin grouping's, growing with the frame
+    frame = vg.METHOD_SORT | vg.SORT_FRAME
+    for n in (1, 307_200, 2_073_600):
+        assert vg.workspace_bytes(n, frame) >= (48 << 20) + 160 * n
+        assert vg.workspace_bytes(n, frame) > vg.workspace_bytes(n)
+    assert vg.workspace_bytes(921_600, frame) > vg.workspace_bytes(307_200, frame)
+
+
+def test_one_launch_capacity_without_a_device():
+    # the capacity query reads device attributes only; with no device it reports none
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    assert vg.frame_one_launch_points() == 0 and vg.frame_one_launch_points(posed=True) == 0
