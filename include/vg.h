@@ -75,7 +75,10 @@ typedef enum {
                                 write it to `origin` (else `origin` is read)            */
 #define VG_METHOD_AUTO 0     /* the library's choice: SORT, with the bucket grouping
                                 from 4,194,304 points on and every digit in global radix
-                                passes (VG_SORT_LSD) below, where camera frames are      */
+                                passes (VG_SORT_LSD) below.  A single camera frame is
+                                fastest with VG_SORT_FRAME, which AUTO does not take: it
+                                needs 32-bit keys, known only on the device, and AUTO
+                                serves every cloud without a host synchronisation        */
 #define VG_METHOD_SORT 16    /* sort the points by key and reduce each run of equal keys.
                                 32-bit keys (no point_to_voxel, no attributes, extents
                                 bound the keys): the top <= 16 key bits are split by one
